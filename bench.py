@@ -1,0 +1,323 @@
+"""Benchmark of the GLS hot path on GB300 (one JSON line on rank 0).
+
+Workload (default): n = 10,000 individuals, p = 4 (intercept + 2 covariates + SNP),
+t = 1 phenotype, FP64, SNPs streamed in blocks of 16,384 -- the block stream of a
+1,000,000-SNP job. One step = one block through the whole per-block path (H2D of the
+dosages for e2e, L^{-1} X_blk fused with the per-SNP reductions, p x p solves).
+The per-cohort setup (M, Cholesky, L^{-1}, Xbar_L, ybar, S_TL, bbar_T) runs once
+before the timed region and is reported as ``setup_ms``.
+
+``value``: SNPs/s with the dosage blocks already resident in HBM (device entry point).
+``e2e``: SNPs/s through ``gwas_solve_block`` from pinned host memory, copies timed.
+``--impl reference``: the CPU oracle on the host cores, same metric and config.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLS SNP solves/sec at n=10k-30k, p=4: plain FP64 vs mixed precision (<=1e-6 rel)"
+UNIT = "SNP/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--m-blk", type=int, default=16384)
+    ap.add_argument("--t", type=int, default=1)
+    ap.add_argument("--limbs", type=int, default=3)
+    ap.add_argument("--pool", type=int, default=4, help="distinct dosage blocks cycled")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flops_per_snp(n: int, q: int, t: int) -> float:
+    """Algorithmic FP64 flops per SNP: the lower-triangular product L^{-1} x_i
+    (n(n+1)/2 multiply-adds) plus the fused reductions (2n(q+1+t))."""
+    return n * (n + 1) + 2.0 * n * (q + 1 + t)
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp64_peak_tflops(sm_mhz: float | None) -> tuple[float, str]:
+    """FP64 FMA peak from the unit count and the clock: 152 SMs x 2 FP64 FMA/clk/SM
+    (1.25 TFLOP/s nominal at 2070 MHz) x 2 flops, at the median SM clock of the run."""
+    mhz = sm_mhz if sm_mhz else 2070.0
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12, f"152 SM x 2 DFMA/clk x 2 flop x {mhz:.0f} MHz"
+
+
+def cpu_baseline(cohort, X_host, seconds: float) -> dict:
+    """The oracle as it stands (Algorithm 1 route), timed on the host cores."""
+    import numpy as np
+    from oracle import gls as G
+    t0 = time.perf_counter()
+    L = G.factor(cohort.phi, cohort.h, cohort.sigma2)
+    setup = G.setup_hoisted(L, cohort.XL, cohort.Y)
+    t_factor = time.perf_counter() - t0
+    m = 64
+    done = 0
+    elapsed = 0.0
+    while True:
+        Xs = np.asfortranarray(X_host[:, done:done + m])
+        t1 = time.perf_counter()
+        G.gls_hoisted(L, cohort.XL, cohort.Y, Xs, setup=setup)
+        elapsed += time.perf_counter() - t1
+        done += Xs.shape[1]
+        if elapsed >= seconds or done >= X_host.shape[1]:
+            break
+        m = min(2 * m, X_host.shape[1] - done)
+    return {"value": done / elapsed, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{done} SNPs at n={cohort.n} after a one-off factor of {t_factor:.1f} s "
+                      f"(numpy/scipy BLAS threads: library default)",
+            "factor_s": round(t_factor, 2)}
+
+
+def run_reference(args, rank, world):
+    """CPU oracle arm: rank 0 only; each step solves a bounded sample of SNPs."""
+    if rank != 0:
+        return
+    import numpy as np
+    import synth
+    from oracle import gls as G
+    dev = None
+    try:
+        import torch
+        if torch.cuda.is_available():
+            dev = "cuda:0"
+    except Exception:
+        pass
+    cohort = synth.make_cohort(0, args.n, t=args.t, device=dev)
+    L = G.factor(cohort.phi, cohort.h, cohort.sigma2)
+    setup = G.setup_hoisted(L, cohort.XL, cohort.Y)
+    per_step = max(8, int(2e10 / (args.n * args.n)))  # ~1-2 s of BLAS work per step
+    blocks = [cohort.snps(per_step, stream=s) for s in range(args.warmup + args.steps)]
+    for s in range(args.warmup):
+        G.gls_hoisted(L, cohort.XL, cohort.Y, blocks[s], setup=setup)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        G.gls_hoisted(L, cohort.XL, cohort.Y, blocks[args.warmup + s], setup=setup)
+    el = time.perf_counter() - t0
+    v = per_step * args.steps / el
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{per_step} SNPs per step at n={args.n}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args) -> dict:
+    prec = "FP64" if args.precision == "fp64" else f"mixed BF16x{args.limbs}"
+    return {"workload": f"{prec} GLS, n={args.n}, p=4, t={args.t}, blocks of {args.m_blk} SNPs "
+                        f"(block stream of a 1e6-SNP job)",
+            "n": args.n, "p": 4, "t": args.t, "m_blk": args.m_blk, "precision": args.precision,
+            "parallelism": f"replicas x{args.gpus}",
+            "l2": "inputs larger than L2: L^-1 is 800 MB at n=10k and each dosage block "
+                  f"{args.n * args.m_blk / 1e6:.0f} MB, {args.pool} distinct blocks cycled"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import synth
+    from paper_1304_2272_gb300 import gwas
+
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(dev))
+    n, mb, t, p = args.n, args.m_blk, args.t, 4
+    prec = gwas.GWAS_PREC_FP64 if args.precision == "fp64" else gwas.GWAS_PREC_MIXED
+
+    cohort = synth.make_cohort(0, n, t=t, device=dev)
+    ctx = gwas.gwas_init(n, p, t, m_blk=mb, device=local, timing=1, precision=prec,
+                         n_limbs=args.limbs)
+    gwas.gwas_factor(ctx, np.asfortranarray(cohort.phi), True, cohort.h, cohort.sigma2,
+                     cohort.XL, cohort.Y)
+    setup_stats = gwas.gwas_get_stats(ctx)
+    pool = [synth.genotypes_torch(1000 * rank + s, n, mb, dev) for s in range(args.pool)]
+    b = torch.empty((mb, t, p), dtype=torch.float64, device=dev)
+    w = torch.empty((mb, t), dtype=torch.float64, device=dev)
+    st = torch.empty(mb, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.ExternalStream(gwas.gwas_stream(ctx), device=dev)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing (value) --------------------------------------
+    for s in range(args.warmup):
+        gwas.gwas_solve_block_device(ctx, pool[s % args.pool], mb, b, w, st)
+    gwas.gwas_sync(ctx)
+    gwas.gwas_reset_stats(ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0.record(stream)
+    for s in range(args.steps):
+        gwas.gwas_solve_block_device(ctx, pool[s % args.pool], mb, b, w, st)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    el_ms = ev0.elapsed_time(ev1)
+    stats = gwas.gwas_get_stats(ctx)
+    status_ok = int((st == 0).sum().item())
+    if world > 1:
+        tt = torch.tensor([el_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        el_ms = float(tt.item())
+    value = world * args.steps * mb / (el_ms / 1e3)
+
+    # ---- end to end from pinned host memory (e2e) ------------------------------
+    hpool = [x.cpu().pin_memory() for x in pool[:2]]
+    hb = torch.empty((mb, t, p), dtype=torch.float64).pin_memory()
+    hw = torch.empty((mb, t), dtype=torch.float64).pin_memory()
+    hs = torch.empty(mb, dtype=torch.uint8).pin_memory()
+    for s in range(args.warmup):
+        gwas.gwas_solve_block(ctx, hpool[s % 2], mb, hb, hw, hs)
+    gwas.gwas_sync(ctx)
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        gwas.gwas_solve_block(ctx, hpool[s % 2], mb, hb, hw, hs)
+    gwas.gwas_sync(ctx)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": world * args.steps * mb / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": n * mb, "d2h_bytes_per_step": mb * (t * p * 8 + t * 8 + 1)}
+
+    if rank == 0:
+        q = p - 1
+        launch_ms = stats["trsm_ms"] / max(1, stats["trsm_launches"])
+        if args.precision == "fp64":
+            peak, how = fp64_peak_tflops(clk.get("sm_mhz"))
+            achieved = flops_per_snp(n, q, t) * mb / (launch_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k_block_fp64",
+                    "launch_ms": launch_ms, "peak_source": how + " (derived, of nominal)"}
+        else:
+            pk = measured_peaks().get("bf16_tflops_sustained") or 1700.0
+            roof = {"bound": "tensor", "achieved": None, "peak": pk, "unit": "TFLOP/s",
+                    "frac": None, "traffic": None}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": workload_config(args),
+                "setup_ms": setup_stats["factor_ms"], "roofline": roof, "e2e": e2e,
+                "gpu_launches": int(stats["kernel_launches"]), "clocks": clk,
+                "status_ok_last_block": status_ok}
+        if not args.no_cpu_baseline:
+            Xh = np.asfortranarray(pool[0][:4096].cpu().numpy().T)
+            line["cpu_baseline"] = cpu_baseline(cohort, Xh, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    gwas.gwas_finalize(ctx)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

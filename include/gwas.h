@@ -1,0 +1,170 @@
+/*
+ * gwas.h -- C ABI of the GB300 mixed-model GWAS GLS engine.
+ *
+ * The engine solves, for every SNP i of a cohort of n individuals, the
+ * generalized least-squares problem of Eq. (1) (Section 1):
+ *
+ *     b_i = (X_i^T M^{-1} X_i)^{-1} X_i^T M^{-1} y,   X_i = [X_L | x_i],
+ *
+ * with X_L the n x (p-1) fixed covariates shared by all SNPs, x_i the SNP's
+ * n dosages, and M the n x n SPD covariance matrix. It follows the reduction of
+ * Section 2 (Cholesky L L^T := M, Xbar := L^{-1} X, then a p x p Cholesky solve
+ * of S_i b_i = bbar_i), with the i-independent work hoisted out of the SNP loop
+ * as in Algorithm 1 (Section 2.1) and the SNPs streamed in blocks as in
+ * Algorithm 2 (Section 3).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are column-major with leading dimension = number of rows.
+ *   - Genotypes are int8 dosages in {0, 1, 2}, one SNP per column, so each SNP's
+ *     n dosages are contiguous (the paper's blocks of contiguous vectors X_blk).
+ *   - Outputs per block of mb SNPs and t phenotypes:
+ *       b      double[mb * t * p], SNP-major: b[(i*t + j)*p + c] is coefficient c
+ *              (c = p-1 is the SNP effect) of SNP i for phenotype j;
+ *       wald   double[mb * t] or NULL: wald[i*t + j] = b_{i,p}^2 / (S_i^{-1})_{pp};
+ *       status uint8_t[mb]: 0 ok, 1 singular S_i (b and wald set to NaN),
+ *              2 a dosage outside {0,1,2} (b and wald set to NaN).
+ *   - The caller owns every buffer it passes; the library owns all device memory
+ *     it allocates (L, L^{-1}, Xbar_L, Ybar, device slots, scratch).
+ *   - Every call returns a gwas_status; nothing aborts or throws across the ABI.
+ *     gwas_last_error() describes the most recent failure of a context.
+ *   - A context is bound to one CUDA device and is not thread-safe.
+ */
+#ifndef GWAS_GB300_H
+#define GWAS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gwas_ctx gwas_ctx; /* opaque */
+
+typedef enum {
+    GWAS_OK = 0,
+    GWAS_ERR_ARG = 1,         /* invalid argument (size, NULL pointer, option)      */
+    GWAS_ERR_NOT_SPD = 2,     /* M is not SPD; gwas_error_index() = failing pivot   */
+    GWAS_ERR_CUDA = 3,        /* a CUDA runtime call failed                          */
+    GWAS_ERR_OOM = 4,         /* device or pinned-host allocation failed             */
+    GWAS_ERR_TIMEOUT = 5,     /* gwas_sync gave up waiting; work is still in flight  */
+    GWAS_ERR_STATE = 6,       /* call out of order (e.g. solve before factor)        */
+    GWAS_ERR_UNSUPPORTED = 7  /* option combination not built                        */
+} gwas_status;
+
+typedef enum {
+    GWAS_PREC_FP64 = 0,  /* every step in FP64                                        */
+    GWAS_PREC_MIXED = 1  /* L^{-1} x_i on BF16 tensor cores as exact limb products,
+                            everything else FP64                                      */
+} gwas_precision;
+
+typedef struct {
+    int precision; /* gwas_precision                                                  */
+    int m_blk;     /* largest block of SNPs one solve call may pass (device slot size) */
+    int n_limbs;   /* GWAS_PREC_MIXED: BF16 limbs L^{-1} is split into (2..7)          */
+    int tile_cfg;  /* kernel tile configuration id; -1 = library default             */
+    int device;    /* CUDA device ordinal                                             */
+    int timing;    /* 1 = record CUDA events around each dominant-kernel launch       */
+} gwas_opts;
+
+/* Per-context counters (gwas_get_stats). Times are CUDA-event milliseconds. */
+typedef struct {
+    int64_t blocks;            /* solve calls completed                               */
+    int64_t snps;              /* SNPs solved                                         */
+    int64_t kernel_launches;   /* kernels this library launched for solve calls      */
+    int64_t trsm_launches;     /* launches of the dominant (L^{-1} X_blk) kernel      */
+    double trsm_ms;            /* summed event time of those launches (timing = 1)    */
+    int64_t h2d_bytes;         /* host->device bytes copied by solve calls            */
+    int64_t d2h_bytes;         /* device->host bytes copied by solve calls            */
+    double factor_ms;          /* event time of the last gwas_factor                  */
+    int64_t factor_launches;   /* kernels launched by the last gwas_factor            */
+} gwas_stats;
+
+/* Fill *opts with defaults: FP64, m_blk 16384, 3 limbs, default tiles, device 0. */
+void gwas_default_opts(gwas_opts* opts);
+
+/*
+ * Create a context for n individuals, p columns per design matrix (p-1 fixed
+ * covariates + 1 SNP; 2 <= p <= 20, Section 1) and t phenotype columns sharing
+ * one M (1 <= t <= 64). Allocates every device buffer up front; sizes:
+ * about 2 n^2 doubles (L and L^{-1}) plus the SNP slots (2 * n * m_blk bytes)
+ * plus O(n (p + t)) and O(m_blk (p + t) n / 64) scratch doubles.
+ * Errors: GWAS_ERR_ARG, GWAS_ERR_CUDA, GWAS_ERR_OOM. *out is NULL on failure.
+ */
+gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx** out);
+
+/*
+ * Per-cohort setup, Algorithm 1 before its loop (Section 2.1):
+ *   M := sigma2 * (h * Phi + (1 - h) * I)   if is_phi != 0 (M_or_Phi holds Phi),
+ *   M := M_or_Phi                           otherwise;
+ *   L L^T := M (FP64 Cholesky), L^{-1} formed explicitly in FP64,
+ *   Xbar_L := L^{-1} X_L, Ybar := L^{-1} Y,
+ *   S_TL := Xbar_L^T Xbar_L, bbar_T := Xbar_L^T Ybar.
+ * M_or_Phi: n x n column-major (only the lower triangle is read); XL: n x (p-1);
+ * Y: n x t. Each pointer may be host or device memory (any address the CUDA
+ * runtime can copy from). Blocks until the setup is complete.
+ * Errors: GWAS_ERR_NOT_SPD (gwas_error_index() = first non-positive pivot),
+ * GWAS_ERR_ARG (NULL pointer, 0 <= h <= 1 and sigma2 > 0 violated with is_phi),
+ * GWAS_ERR_CUDA.
+ */
+gwas_status gwas_factor(gwas_ctx* ctx, const double* M_or_Phi, int is_phi, double h,
+                        double sigma2, const double* XL, const double* Y);
+
+/*
+ * One block of Algorithm 2's loop (Section 3): copy X (n x mb int8, HOST memory,
+ * pinned for full overlap) into a device slot, compute Xbar_blk := L^{-1} X_blk
+ * fused with the per-SNP reductions S_BLi, S_BRi, bbar_Bi and the p x p solve,
+ * and copy b, wald (may be NULL) and status back into the caller's HOST buffers.
+ * Asynchronous: returns once the work is queued. Two slots alternate, so the
+ * copy of one block overlaps the compute of the previous one. The caller must not
+ * modify X nor read b/wald/status before gwas_sync() returns GWAS_OK.
+ * 1 <= mb <= m_blk. Errors: GWAS_ERR_ARG, GWAS_ERR_STATE (no factor), GWAS_ERR_CUDA.
+ */
+gwas_status gwas_solve_block(gwas_ctx* ctx, const int8_t* X, int64_t mb, double* b,
+                             double* wald, uint8_t* status);
+
+/*
+ * As gwas_solve_block with every pointer in DEVICE memory of the context's device
+ * (no copies). X must stay valid and unmodified, and the outputs unread, until the
+ * work completes (gwas_sync, or stream order on gwas_stream()).
+ */
+gwas_status gwas_solve_block_device(gwas_ctx* ctx, const int8_t* X, int64_t mb, double* b,
+                                    double* wald, uint8_t* status);
+
+/*
+ * Algorithm 2 end to end on host memory: m SNPs (n x m int8, column-major) in
+ * blocks of m_blk, double-buffered, then gwas_sync(-1). Outputs as above with m
+ * in place of mb. Errors as gwas_solve_block.
+ */
+gwas_status gwas_solve_all(gwas_ctx* ctx, const int8_t* X, int64_t m, double* b,
+                           double* wald, uint8_t* status);
+
+/*
+ * Wait for all queued work of the context. timeout_ms < 0 waits without limit;
+ * otherwise polls and returns GWAS_ERR_TIMEOUT after about timeout_ms (the work
+ * stays queued and a later gwas_sync may still succeed). Never hangs the host
+ * when a limit is given.
+ */
+gwas_status gwas_sync(gwas_ctx* ctx, int timeout_ms);
+
+/* Free every resource of the context; ctx is invalid afterwards. NULL is allowed. */
+gwas_status gwas_finalize(gwas_ctx* ctx);
+
+/* Text of the last error of ctx ("" if none); owned by ctx. */
+const char* gwas_last_error(const gwas_ctx* ctx);
+
+/* Failing pivot index after GWAS_ERR_NOT_SPD, else -1. */
+int64_t gwas_error_index(const gwas_ctx* ctx);
+
+/* Counters since gwas_init or the last gwas_reset_stats (waits for queued work). */
+gwas_status gwas_get_stats(gwas_ctx* ctx, gwas_stats* out);
+gwas_status gwas_reset_stats(gwas_ctx* ctx);
+
+/* The context's compute stream, as a cudaStream_t cast to void*. */
+void* gwas_stream(const gwas_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GWAS_GB300_H */

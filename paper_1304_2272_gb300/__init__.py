@@ -1,0 +1,27 @@
+"""GB300 (sm_103a) engine for the mixed-model GWAS GLS hot path.
+
+The compute path lives in the CUDA library ``libgwas_gb300.so`` (sources in
+``csrc/``, C ABI in ``include/gwas.h``); ``gwas`` is its ctypes binding. Importing
+this package loads nothing; the library is loaded on first use and fails loudly
+when it cannot be built or loaded. There is no CPU fallback.
+"""
+from .gwas import (  # noqa: F401
+    GLS,
+    GWAS_PREC_FP64,
+    GWAS_PREC_MIXED,
+    GwasError,
+    gwas_default_opts,
+    gwas_error_index,
+    gwas_factor,
+    gwas_finalize,
+    gwas_get_stats,
+    gwas_init,
+    gwas_last_error,
+    gwas_reset_stats,
+    gwas_solve_all,
+    gwas_solve_block,
+    gwas_solve_block_device,
+    gwas_stream,
+    gwas_sync,
+    load,
+)

@@ -1,0 +1,274 @@
+// Per-cohort setup in FP64: M, its Cholesky factor L, the explicit inverse L^{-1}
+// and a generic FP64 GEMM used for the blocked steps (Algorithm 1 before its loop).
+//
+// FP64 arithmetic stays on the CUDA cores (DFMA): the setup is O(n^3) once per
+// cohort, and its stability needs FP64 (Section 2: L L^T := M, triangular solves).
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gwas {
+
+// ----------------------------------------------------------------------------
+// a1: M := sigma2 (h Phi + (1-h) I), lower triangle; strict upper triangle := 0.
+// ----------------------------------------------------------------------------
+__global__ void k_build_M(const double* __restrict__ src, int64_t lds, double* __restrict__ M,
+                          int64_t ldm, int64_t n, int is_phi, double h, double sigma2) {
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            double v = 0.0;
+            if (i >= j) {
+                const double a = src[i + j * lds];
+                v = is_phi ? sigma2 * (h * a + (i == j ? 1.0 - h : 0.0)) : a;
+            }
+            M[i + j * ldm] = v;
+        }
+    }
+}
+
+cudaError_t launch_build_M(const double* src, int64_t lds, double* M, int64_t ldm, int64_t n,
+                           int is_phi, double h, double sigma2, cudaStream_t s) {
+    dim3 grid((unsigned)std::min<int64_t>(ceil_div(n, 256), 64),
+              (unsigned)std::min<int64_t>(n, 65535));
+    k_build_M<<<grid, 256, 0, s>>>(src, lds, M, ldm, n, is_phi, h, sigma2);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Generic FP64 GEMM, 64 x 64 output tile per CTA, 256 threads, 4 x 4 per thread.
+// Thread (tx, ty) owns rows tx + 16 a and columns ty + 16 b of the tile, so a warp
+// stores 16 consecutive rows of a column-major C.
+// ----------------------------------------------------------------------------
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
+    __shared__ double As[KC64][T64 + 1];  // As[k][i] = op(A)(i0 + i, k0 + k)
+    __shared__ double Bs[KC64][T64 + 1];  // Bs[k][j] = op(B)(k0 + k, j0 + j)
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t i0 = (int64_t)blockIdx.x * T64, j0 = (int64_t)blockIdx.y * T64;
+    if (g.c_lower && j0 > i0) return;
+    int64_t kbeg = 0, kend = g.K;
+    if (g.a_lower) kend = min64(kend, i0 + T64);
+    if (g.b_lower) kbeg = j0;
+
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+    for (int64_t k0 = kbeg; k0 < kend; k0 += KC64) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = tid + 256 * r;
+            int ii, kk;
+            if (!TA) { ii = e % T64; kk = e / T64; } else { kk = e % KC64; ii = e / KC64; }
+            const int64_t gi = i0 + ii, gk = k0 + kk;
+            double v = 0.0;
+            if (gi < g.M && gk < kend) v = TA ? g.A[gk + gi * g.lda] : g.A[gi + gk * g.lda];
+            As[kk][ii] = v;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = tid + 256 * r;
+            int jj, kk;
+            if (!TB) { kk = e % KC64; jj = e / KC64; } else { jj = e % T64; kk = e / T64; }
+            const int64_t gj = j0 + jj, gk = k0 + kk;
+            double v = 0.0;
+            if (gj < g.N && gk < kend) v = TB ? g.B[gj + gk * g.ldb] : g.B[gk + gj * g.ldb];
+            Bs[kk][jj] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KC64; ++kk) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t gi = i0 + tx + 16 * a;
+        if (gi >= g.M) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int64_t gj = j0 + ty + 16 * b;
+            if (gj >= g.N) continue;
+            double* c = g.C + gi + gj * g.ldc;
+            const double v = g.alpha * acc[a][b];
+            *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
+        }
+    }
+}
+
+cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    dim3 grid((unsigned)ceil_div(g.M, T64), (unsigned)ceil_div(g.N, T64));
+    if (!g.transA && !g.transB) k_gemm_f64<false, false><<<grid, 256, 0, s>>>(g);
+    else if (!g.transA && g.transB) k_gemm_f64<false, true><<<grid, 256, 0, s>>>(g);
+    else if (g.transA && !g.transB) k_gemm_f64<true, false><<<grid, 256, 0, s>>>(g);
+    else k_gemm_f64<true, true><<<grid, 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// a2 diagonal block: unblocked Cholesky of one kb x kb block (kb <= 64) in shared
+// memory, then D = L_kk^{-1} by column-wise forward substitution.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int64_t lda, int kb,
+                                                    int64_t base, double* __restrict__ D,
+                                                    int* __restrict__ info) {
+    // 2 x 64 x 65 doubles (66,560 bytes): dynamic shared memory, opted in at launch.
+    extern __shared__ double smem_potrf[];
+    double (*S)[T64 + 1] = reinterpret_cast<double (*)[T64 + 1]>(smem_potrf);
+    double (*Dn)[T64 + 1] = reinterpret_cast<double (*)[T64 + 1]>(smem_potrf + T64 * (T64 + 1));
+    __shared__ int fail;
+    const int tid = threadIdx.x;
+    if (tid == 0) fail = -1;
+    for (int e = tid; e < T64 * T64; e += blockDim.x) {
+        const int i = e % T64, j = e / T64;
+        S[i][j] = (i < kb && j < kb && i >= j) ? A[i + j * lda] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        if (tid == 0) {
+            const double d = S[j][j];
+            if (!(d > 0.0)) {
+                if (fail < 0) fail = j;
+                S[j][j] = nan("");
+            } else {
+                S[j][j] = sqrt(d);
+            }
+        }
+        __syncthreads();
+        const double piv = S[j][j];
+        for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[i][j] /= piv;
+        __syncthreads();
+        const int w = kb - j - 1;  // trailing (w x w) lower update
+        for (int e = tid; e < w * w; e += blockDim.x) {
+            const int i = j + 1 + e % w, k = j + 1 + e / w;
+            if (i >= k) S[i][k] -= S[i][j] * S[k][j];
+        }
+        __syncthreads();
+    }
+    // D = L_kk^{-1}: thread c solves L d_c = e_c for column c (rows c..kb-1).
+    if (tid < T64) {
+        const int c = tid;
+        for (int i = 0; i < T64; ++i) Dn[i][c] = 0.0;
+        if (c < kb) {
+            Dn[c][c] = 1.0 / S[c][c];
+            for (int i = c + 1; i < kb; ++i) {
+                double acc = 0.0;
+                for (int k = c; k < i; ++k) acc = fma(S[i][k], Dn[k][c], acc);
+                Dn[i][c] = -acc / S[i][i];
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < T64 * T64; e += blockDim.x) {
+        const int i = e % T64, j = e / T64;
+        if (i < kb && j < kb) A[i + j * lda] = (i >= j) ? S[i][j] : 0.0;
+        D[i + j * T64] = Dn[i][j];
+    }
+    if (tid == 0 && fail >= 0) atomicMin(info, (int)(base + fail));
+}
+
+cudaError_t cholesky_blocked(double* A, int64_t lda, int64_t n, double* Dinv, int* d_info,
+                             cudaStream_t s, int64_t* launches) {
+    const int64_t nt = ceil_div(n, T64);
+    int64_t nl = 0;
+    const int smem = 2 * T64 * (T64 + 1) * (int)sizeof(double);
+    cudaError_t ea = cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (ea != cudaSuccess) return ea;
+    for (int64_t k = 0; k < nt; ++k) {
+        const int64_t k0 = k * T64;
+        const int kb = (int)std::min<int64_t>(T64, n - k0);
+        double* Akk = A + k0 + k0 * lda;
+        double* Dk = Dinv + k * T64 * T64;
+        k_potrf_diag<<<1, 256, smem, s>>>(Akk, lda, kb, k0, Dk, d_info);
+        ++nl;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int64_t below = n - k0 - kb;
+        if (below <= 0) break;
+        double* P = A + (k0 + kb) + k0 * lda;  // panel rows below the block
+        // L_ik := A_ik L_kk^{-T} = A_ik D_k^T (one column tile: in place is safe)
+        GemmF64 g;
+        g.M = below; g.N = kb; g.K = kb;
+        g.A = P; g.lda = lda; g.B = Dk; g.ldb = T64; g.transB = true;
+        g.C = P; g.ldc = lda;
+        if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+        // A22 -= L_panel L_panel^T (lower tiles only)
+        GemmF64 u;
+        u.M = below; u.N = below; u.K = kb;
+        u.A = P; u.lda = lda; u.B = P; u.ldb = lda; u.transB = true;
+        u.C = A + (k0 + kb) + (k0 + kb) * lda; u.ldc = lda;
+        u.alpha = -1.0; u.beta = 1.0; u.c_lower = true;
+        if ((e = gemm_f64(u, s)) != cudaSuccess) return e;
+        nl += 2;
+    }
+    if (launches) *launches += nl;
+    return cudaSuccess;
+}
+
+// ----------------------------------------------------------------------------
+// a3: W := L^{-1} by recursive halving on 64-aligned splits.
+// ----------------------------------------------------------------------------
+__global__ void k_copy_diag_inv(const double* __restrict__ D, int kb, double* __restrict__ W,
+                                int64_t ldw) {
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+        const int i = e % kb, j = e / kb;
+        W[i + j * ldw] = D[i + j * T64];
+    }
+}
+
+static cudaError_t trtri_rec(const double* L, int64_t ldl, int64_t r0, int64_t size,
+                             const double* Dinv, double* W, int64_t ldw, double* tmp,
+                             cudaStream_t s, int64_t* nl) {
+    if (size <= T64) {
+        k_copy_diag_inv<<<1, 256, 0, s>>>(Dinv + (r0 / T64) * T64 * T64, (int)size,
+                                          W + r0 + r0 * ldw, ldw);
+        ++*nl;
+        return cudaGetLastError();
+    }
+    const int64_t s1 = round_up(ceil_div(size, 2), T64);
+    const int64_t s2 = size - s1;
+    cudaError_t e = trtri_rec(L, ldl, r0, s1, Dinv, W, ldw, tmp, s, nl);
+    if (e != cudaSuccess) return e;
+    if ((e = trtri_rec(L, ldl, r0 + s1, s2, Dinv, W, ldw, tmp, s, nl)) != cudaSuccess) return e;
+    // T := L21 W11   (s2 x s1; W11 lower triangular)
+    GemmF64 g;
+    g.M = s2; g.N = s1; g.K = s1;
+    g.A = L + (r0 + s1) + r0 * ldl; g.lda = ldl;
+    g.B = W + r0 + r0 * ldw; g.ldb = ldw; g.b_lower = true;
+    g.C = tmp; g.ldc = s2;
+    if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+    // W21 := -W22 T   (W22 lower triangular)
+    GemmF64 h;
+    h.M = s2; h.N = s1; h.K = s2;
+    h.A = W + (r0 + s1) + (r0 + s1) * ldw; h.lda = ldw; h.a_lower = true;
+    h.B = tmp; h.ldb = s2;
+    h.C = W + (r0 + s1) + r0 * ldw; h.ldc = ldw; h.alpha = -1.0;
+    if ((e = gemm_f64(h, s)) != cudaSuccess) return e;
+    *nl += 2;
+    return cudaSuccess;
+}
+
+cudaError_t trtri_lower(const double* L, int64_t ldl, int64_t n, const double* Dinv, double* W,
+                        int64_t ldw, double* tmp, cudaStream_t s, int64_t* launches) {
+    int64_t nl = 0;
+    cudaError_t e = trtri_rec(L, ldl, 0, n, Dinv, W, ldw, tmp, s, &nl);
+    if (launches) *launches += nl;
+    return e;
+}
+
+}  // namespace gwas

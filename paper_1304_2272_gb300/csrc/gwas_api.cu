@@ -1,0 +1,441 @@
+// C ABI of the engine (include/gwas.h): context, device memory, streams and the
+// double-buffered block pipeline of Algorithm 2 (Section 3).
+//
+// Streams: one H2D copy stream, one compute stream, one D2H copy stream. Two device
+// slots alternate between blocks; CUDA events order "copy block k+1 in" against
+// "compute block k" and "copy b of block k-1 out", which is the paper's
+// load_start/load_wait/store_start/store_wait pattern with the disk replaced by
+// pinned host memory and the second memory region by the second device slot.
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/gwas.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace gwas;
+
+struct gwas_ctx {
+    gwas_opts opts{};
+    int device = 0;
+    int64_t n = 0;
+    int p = 0, q = 0, t = 0;
+    int64_t ld = 0;               // leading dimension of L and W
+    double* L = nullptr;          // n x n: M, then its Cholesky factor
+    double* W = nullptr;          // n x n: L^{-1}
+    double* Dinv = nullptr;       // diagonal 64 x 64 inverses
+    double* XLbar = nullptr;      // n x q
+    double* Ybar = nullptr;       // n x t
+    double* S_TL = nullptr;       // q x q
+    double* bbar_T = nullptr;     // q x t
+    int* d_info = nullptr;
+    // block pipeline
+    int8_t* Xslot[2] = {nullptr, nullptr};
+    double* bslot[2] = {nullptr, nullptr};
+    double* wslot[2] = {nullptr, nullptr};
+    uint8_t* sslot[2] = {nullptr, nullptr};
+    double* part = nullptr;       // row-tile partial sums
+    int64_t ldp = 0;
+    uint8_t* bad = nullptr;
+    cudaStream_t s_comp = nullptr, s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
+    int slot = 0;
+    bool factored = false;
+    std::string err;
+    int64_t err_index = -1;
+    gwas_stats stats{};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed;  // pending trsm timings
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+gwas_status fail(gwas_ctx* c, gwas_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+gwas_status cuda_fail(gwas_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    cudaGetLastError();  // clear a sticky launch error where possible
+    return fail(c, e == cudaErrorMemoryAllocation ? GWAS_ERR_OOM : GWAS_ERR_CUDA, m);
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+template <typename T>
+cudaError_t dmalloc(T** p, size_t count) {
+    return cudaMalloc((void**)p, count * sizeof(T) + 256);
+}
+
+CohortDev cohort_view(const gwas_ctx* c) {
+    CohortDev v;
+    v.n = c->n; v.q = c->q; v.t = c->t;
+    v.W = c->W; v.ldw = c->ld;
+    v.XLbar = c->XLbar; v.Ybar = c->Ybar; v.S_TL = c->S_TL; v.bbar_T = c->bbar_T;
+    return v;
+}
+
+// Owns a temporary device allocation for the duration of one call.
+struct TmpDev {
+    void* p = nullptr;
+    ~TmpDev() {
+        if (p) cudaFree(p);
+    }
+};
+
+cudaEvent_t pooled_event(gwas_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// The block compute on the compute stream: trsm + fused reductions, then the
+// per-SNP solve. X, b, wald, status are device pointers.
+gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, double* wald,
+                      uint8_t* status) {
+    CohortDev cv = cohort_view(c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->opts.timing) {
+        e0 = pooled_event(c);
+        e1 = pooled_event(c);
+        CK(cudaEventRecord(e0, c->s_comp));
+    }
+    CK(launch_block_fp64(cv, X, c->n, mb, c->part, c->ldp, c->bad, c->s_comp));
+    if (c->opts.timing) {
+        CK(cudaEventRecord(e1, c->s_comp));
+        c->timed.emplace_back(e0, e1);
+    }
+    CK(launch_snp_solve(cv, c->part, c->ldp, (int)ceil_div(c->n, T64), c->bad, mb, b, wald,
+                        status, c->s_comp));
+    c->stats.kernel_launches += 2;
+    c->stats.trsm_launches += 1;
+    c->stats.blocks += 1;
+    c->stats.snps += mb;
+    return GWAS_OK;
+}
+
+void free_all(gwas_ctx* c) {
+    cudaFree(c->L); cudaFree(c->W); cudaFree(c->Dinv); cudaFree(c->XLbar); cudaFree(c->Ybar);
+    cudaFree(c->S_TL); cudaFree(c->bbar_T); cudaFree(c->d_info); cudaFree(c->part);
+    cudaFree(c->bad);
+    for (int s = 0; s < 2; ++s) {
+        cudaFree(c->Xslot[s]); cudaFree(c->bslot[s]); cudaFree(c->wslot[s]); cudaFree(c->sslot[s]);
+        if (c->ev_h2d[s]) cudaEventDestroy(c->ev_h2d[s]);
+        if (c->ev_comp[s]) cudaEventDestroy(c->ev_comp[s]);
+        if (c->ev_d2h[s]) cudaEventDestroy(c->ev_d2h[s]);
+    }
+    for (auto& pr : c->timed) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->s_comp) cudaStreamDestroy(c->s_comp);
+    if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
+    if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
+}
+
+}  // namespace
+
+extern "C" {
+
+void gwas_default_opts(gwas_opts* o) {
+    if (!o) return;
+    o->precision = GWAS_PREC_FP64;
+    o->m_blk = 16384;
+    o->n_limbs = 3;
+    o->tile_cfg = -1;
+    o->device = 0;
+    o->timing = 0;
+}
+
+gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx** out) {
+    if (!out) return GWAS_ERR_ARG;
+    *out = nullptr;
+    gwas_opts o;
+    gwas_default_opts(&o);
+    if (opts) o = *opts;
+    if (n < 1 || p < 2 || p > MAX_P || t < 1 || t > MAX_T || o.m_blk < 1) return GWAS_ERR_ARG;
+    if (o.precision != GWAS_PREC_FP64) return GWAS_ERR_UNSUPPORTED;
+    if (n > (int64_t)1 << 31) return GWAS_ERR_ARG;
+    gwas_ctx* c = new gwas_ctx();
+    c->opts = o;
+    c->device = o.device;
+    c->n = n; c->p = p; c->q = p - 1; c->t = t;
+    c->ld = round_up(n, T64);
+    DeviceGuard g(c->device);
+    auto bail = [&](cudaError_t e, const char* w) {
+        cuda_fail(c, e, w);
+        gwas_status st = e == cudaErrorMemoryAllocation ? GWAS_ERR_OOM : GWAS_ERR_CUDA;
+        free_all(c);
+        delete c;
+        return st;
+    };
+#define CKI(call)                                  \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return bail(e_, #call); \
+    } while (0)
+    const int64_t nt = ceil_div(n, T64);
+    const size_t nn = (size_t)c->ld * (size_t)c->ld;
+    CKI(cudaSetDevice(c->device));
+    CKI(dmalloc(&c->L, nn));
+    CKI(dmalloc(&c->W, nn));
+    CKI(dmalloc(&c->Dinv, (size_t)nt * T64 * T64));
+    CKI(dmalloc(&c->XLbar, (size_t)n * c->q));
+    CKI(dmalloc(&c->Ybar, (size_t)n * t));
+    CKI(dmalloc(&c->S_TL, (size_t)c->q * c->q));
+    CKI(dmalloc(&c->bbar_T, (size_t)c->q * t));
+    CKI(dmalloc(&c->d_info, 1));
+    c->ldp = round_up(o.m_blk, 32);
+    const int nred = c->q + 1 + t;
+    CKI(dmalloc(&c->part, (size_t)nt * nred * c->ldp));
+    CKI(dmalloc(&c->bad, (size_t)o.m_blk));
+    for (int s = 0; s < 2; ++s) {
+        CKI(dmalloc(&c->Xslot[s], (size_t)n * o.m_blk));
+        CKI(dmalloc(&c->bslot[s], (size_t)o.m_blk * t * p));
+        CKI(dmalloc(&c->wslot[s], (size_t)o.m_blk * t));
+        CKI(dmalloc(&c->sslot[s], (size_t)o.m_blk));
+        CKI(cudaEventCreateWithFlags(&c->ev_h2d[s], cudaEventDisableTiming));
+        CKI(cudaEventCreateWithFlags(&c->ev_comp[s], cudaEventDisableTiming));
+        CKI(cudaEventCreateWithFlags(&c->ev_d2h[s], cudaEventDisableTiming));
+    }
+    CKI(cudaStreamCreateWithFlags(&c->s_comp, cudaStreamNonBlocking));
+    CKI(cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking));
+    CKI(cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking));
+#undef CKI
+    *out = c;
+    return GWAS_OK;
+}
+
+gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double h,
+                        double sigma2, const double* XL, const double* Y) {
+    if (!c) return GWAS_ERR_ARG;
+    if (!M_or_Phi || !XL || !Y) return fail(c, GWAS_ERR_ARG, "gwas_factor: NULL input");
+    if (is_phi && !(h >= 0.0 && h <= 1.0 && sigma2 > 0.0))
+        return fail(c, GWAS_ERR_ARG, "gwas_factor: need 0 <= h <= 1 and sigma2 > 0");
+    DeviceGuard g(c->device);
+    c->factored = false;
+    c->err_index = -1;
+    const int64_t n = c->n, ld = c->ld;
+    cudaStream_t s = c->s_comp;
+    CK(cudaStreamSynchronize(c->s_h2d));
+    CK(cudaStreamSynchronize(c->s_d2h));
+    cudaEvent_t f0 = pooled_event(c), f1 = pooled_event(c);
+    CK(cudaEventRecord(f0, s));
+    int64_t nl = 0;
+    // Phi (or M) is staged in the W buffer, then M is built into L's buffer.
+    CK(cudaMemcpy2DAsync(c->W, ld * sizeof(double), M_or_Phi, n * sizeof(double),
+                         n * sizeof(double), n, cudaMemcpyDefault, s));
+    CK(launch_build_M(c->W, ld, c->L, ld, n, is_phi, h, sigma2, s));
+    ++nl;
+    const int init = 0x7fffffff;
+    CK(cudaMemcpyAsync(c->d_info, &init, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cholesky_blocked(c->L, ld, n, c->Dinv, c->d_info, s, &nl));
+    // W := L^{-1}
+    CK(cudaMemsetAsync(c->W, 0, (size_t)ld * ld * sizeof(double), s));
+    const int64_t half = round_up(ceil_div(n, 2), T64);
+    TmpDev tmp_buf, in_buf;
+    CK(cudaMalloc(&tmp_buf.p, (size_t)half * half * sizeof(double)));
+    double* tmp = (double*)tmp_buf.p;
+    CK(trtri_lower(c->L, ld, n, c->Dinv, c->W, ld, tmp, s, &nl));
+    // Xbar_L := W X_L, Ybar := W Y
+    CK(cudaMalloc(&in_buf.p, (size_t)n * (c->q + c->t) * sizeof(double)));
+    double* XLin = (double*)in_buf.p;
+    double* Yin = XLin + (size_t)n * c->q;
+    CK(cudaMemcpyAsync(XLin, XL, (size_t)n * c->q * sizeof(double), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(Yin, Y, (size_t)n * c->t * sizeof(double), cudaMemcpyDefault, s));
+    {
+        GemmF64 a;
+        a.M = n; a.N = c->q; a.K = n; a.A = c->W; a.lda = ld; a.a_lower = true;
+        a.B = XLin; a.ldb = n; a.C = c->XLbar; a.ldc = n;
+        CK(gemm_f64(a, s));
+        GemmF64 b = a;
+        b.N = c->t; b.B = Yin; b.C = c->Ybar;
+        CK(gemm_f64(b, s));
+        // S_TL := Xbar_L^T Xbar_L, bbar_T := Xbar_L^T Ybar
+        GemmF64 st;
+        st.M = c->q; st.N = c->q; st.K = n; st.A = c->XLbar; st.lda = n; st.transA = true;
+        st.B = c->XLbar; st.ldb = n; st.C = c->S_TL; st.ldc = c->q;
+        CK(gemm_f64(st, s));
+        GemmF64 bt = st;
+        bt.N = c->t; bt.B = c->Ybar; bt.C = c->bbar_T;
+        CK(gemm_f64(bt, s));
+        nl += 4;
+    }
+    CK(cudaEventRecord(f1, s));
+    int info = 0;
+    CK(cudaMemcpyAsync(&info, c->d_info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, f0, f1);
+    c->ev_pool.push_back(f0);
+    c->ev_pool.push_back(f1);
+    c->stats.factor_ms = ms;
+    c->stats.factor_launches = nl;
+    if (info != init) {
+        c->err_index = info;
+        char buf[128];
+        snprintf(buf, sizeof buf, "gwas_factor: M is not SPD (pivot %d)", info);
+        return fail(c, GWAS_ERR_NOT_SPD, buf);
+    }
+    c->factored = true;
+    return GWAS_OK;
+}
+
+static gwas_status check_block_args(gwas_ctx* c, const int8_t* X, int64_t mb, double* b,
+                                    uint8_t* status) {
+    if (!c) return GWAS_ERR_ARG;
+    if (!c->factored) return fail(c, GWAS_ERR_STATE, "solve before a successful gwas_factor");
+    if (!X || !b || !status) return fail(c, GWAS_ERR_ARG, "solve: NULL pointer");
+    if (mb < 1 || mb > c->opts.m_blk) return fail(c, GWAS_ERR_ARG, "solve: need 1 <= mb <= m_blk");
+    return GWAS_OK;
+}
+
+gwas_status gwas_solve_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, double* wald,
+                             uint8_t* status) {
+    gwas_status st = check_block_args(c, X, mb, b, status);
+    if (st != GWAS_OK) return st;
+    DeviceGuard g(c->device);
+    const int s = c->slot;
+    c->slot ^= 1;
+    const int64_t t = c->t, p = c->p;
+    // load_start: the slot's previous block must be consumed by the compute stream
+    CK(cudaStreamWaitEvent(c->s_h2d, c->ev_comp[s], 0));
+    CK(cudaMemcpyAsync(c->Xslot[s], X, (size_t)c->n * mb, cudaMemcpyHostToDevice, c->s_h2d));
+    CK(cudaEventRecord(c->ev_h2d[s], c->s_h2d));
+    // load_wait, and the slot's previous outputs must have left for the host
+    CK(cudaStreamWaitEvent(c->s_comp, c->ev_h2d[s], 0));
+    CK(cudaStreamWaitEvent(c->s_comp, c->ev_d2h[s], 0));
+    st = run_block(c, c->Xslot[s], mb, c->bslot[s], wald ? c->wslot[s] : nullptr, c->sslot[s]);
+    if (st != GWAS_OK) return st;
+    CK(cudaEventRecord(c->ev_comp[s], c->s_comp));
+    // store_start
+    CK(cudaStreamWaitEvent(c->s_d2h, c->ev_comp[s], 0));
+    CK(cudaMemcpyAsync(b, c->bslot[s], (size_t)mb * t * p * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->s_d2h));
+    if (wald)
+        CK(cudaMemcpyAsync(wald, c->wslot[s], (size_t)mb * t * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->s_d2h));
+    CK(cudaMemcpyAsync(status, c->sslot[s], (size_t)mb, cudaMemcpyDeviceToHost, c->s_d2h));
+    CK(cudaEventRecord(c->ev_d2h[s], c->s_d2h));
+    c->stats.h2d_bytes += c->n * mb;
+    c->stats.d2h_bytes += mb * t * p * 8 + (wald ? mb * t * 8 : 0) + mb;
+    return GWAS_OK;
+}
+
+gwas_status gwas_solve_block_device(gwas_ctx* c, const int8_t* X, int64_t mb, double* b,
+                                    double* wald, uint8_t* status) {
+    gwas_status st = check_block_args(c, X, mb, b, status);
+    if (st != GWAS_OK) return st;
+    DeviceGuard g(c->device);
+    return run_block(c, X, mb, b, wald, status);
+}
+
+gwas_status gwas_solve_all(gwas_ctx* c, const int8_t* X, int64_t m, double* b, double* wald,
+                           uint8_t* status) {
+    if (!c) return GWAS_ERR_ARG;
+    if (m < 0) return fail(c, GWAS_ERR_ARG, "solve_all: m < 0");
+    const int64_t mblk = c->opts.m_blk, t = c->t, p = c->p;
+    for (int64_t i0 = 0; i0 < m; i0 += mblk) {
+        const int64_t mb = std::min<int64_t>(mblk, m - i0);
+        gwas_status st = gwas_solve_block(c, X + i0 * c->n, mb, b + i0 * t * p,
+                                          wald ? wald + i0 * t : nullptr, status + i0);
+        if (st != GWAS_OK) return st;
+    }
+    return gwas_sync(c, -1);
+}
+
+gwas_status gwas_sync(gwas_ctx* c, int timeout_ms) {
+    if (!c) return GWAS_ERR_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t ss[3] = {c->s_h2d, c->s_comp, c->s_d2h};
+    if (timeout_ms < 0) {
+        for (auto s : ss) CK(cudaStreamSynchronize(s));
+        return GWAS_OK;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        bool done = true;
+        for (auto s : ss) {
+            cudaError_t e = cudaStreamQuery(s);
+            if (e == cudaErrorNotReady) { done = false; continue; }
+            if (e != cudaSuccess) return cuda_fail(c, e, "gwas_sync");
+        }
+        if (done) return GWAS_OK;
+        const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(
+                            std::chrono::steady_clock::now() - t0).count();
+        if (el >= timeout_ms) return fail(c, GWAS_ERR_TIMEOUT, "gwas_sync: timed out");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+gwas_status gwas_finalize(gwas_ctx* c) {
+    if (!c) return GWAS_OK;
+    {
+        DeviceGuard g(c->device);
+        cudaStreamSynchronize(c->s_h2d);
+        cudaStreamSynchronize(c->s_comp);
+        cudaStreamSynchronize(c->s_d2h);
+        free_all(c);
+    }
+    delete c;
+    return GWAS_OK;
+}
+
+const char* gwas_last_error(const gwas_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t gwas_error_index(const gwas_ctx* c) { return c ? c->err_index : -1; }
+
+gwas_status gwas_get_stats(gwas_ctx* c, gwas_stats* out) {
+    if (!c || !out) return GWAS_ERR_ARG;
+    DeviceGuard g(c->device);
+    gwas_status st = gwas_sync(c, -1);
+    if (st != GWAS_OK) return st;
+    for (auto& pr : c->timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) c->stats.trsm_ms += ms;
+        c->ev_pool.push_back(pr.first);
+        c->ev_pool.push_back(pr.second);
+    }
+    c->timed.clear();
+    *out = c->stats;
+    return GWAS_OK;
+}
+
+gwas_status gwas_reset_stats(gwas_ctx* c) {
+    if (!c) return GWAS_ERR_ARG;
+    gwas_stats tmp;
+    gwas_status st = gwas_get_stats(c, &tmp);
+    const double fms = c->stats.factor_ms;
+    const int64_t fl = c->stats.factor_launches;
+    c->stats = gwas_stats{};
+    c->stats.factor_ms = fms;
+    c->stats.factor_launches = fl;
+    return st;
+}
+
+void* gwas_stream(const gwas_ctx* c) { return c ? (void*)c->s_comp : nullptr; }
+
+}  // extern "C"

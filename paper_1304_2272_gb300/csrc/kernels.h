@@ -1,0 +1,73 @@
+// Host-side launchers of the engine's CUDA kernels (internal; not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gwas {
+
+// ---- factor path (factor.cu) ------------------------------------------------
+
+// M := sigma2 (h Phi + (1-h) I) from the lower triangle of Phi (is_phi), or a copy
+// of the lower triangle of M; the strict upper triangle of the output is zeroed.
+cudaError_t launch_build_M(const double* src, int64_t lds, double* M, int64_t ldm, int64_t n,
+                           int is_phi, double h, double sigma2, cudaStream_t s);
+
+// Blocked right-looking Cholesky of the lower triangle of A (n x n, col-major) in
+// place, 64-wide blocks. Writes D_k = L_kk^{-1} of every diagonal block into Dinv
+// (nt blocks of 64 x 64, col-major, zero padded) and the first non-positive pivot
+// (global index) into *d_info (left untouched when the factorisation succeeds).
+// Returns the number of kernels launched through *launches.
+cudaError_t cholesky_blocked(double* A, int64_t lda, int64_t n, double* Dinv, int* d_info,
+                             cudaStream_t s, int64_t* launches);
+
+// W := L^{-1} (lower triangular, zeros above the diagonal) by the recursive block
+// formula [[L11,0],[L21,L22]]^{-1} = [[W11,0],[-W22 L21 W11, W22]], with the
+// diagonal 64 x 64 inverses taken from Dinv. tmp needs ceil(n/2/64)*64 squared doubles.
+cudaError_t trtri_lower(const double* L, int64_t ldl, int64_t n, const double* Dinv, double* W,
+                        int64_t ldw, double* tmp, cudaStream_t s, int64_t* launches);
+
+// Generic FP64 GEMM: C := alpha op(A) op(B) + beta C, op(A) M x K, op(B) K x N.
+struct GemmF64 {
+    int64_t M = 0, N = 0, K = 0;
+    const double* A = nullptr; int64_t lda = 0; bool transA = false;
+    const double* B = nullptr; int64_t ldb = 0; bool transB = false;
+    double* C = nullptr; int64_t ldc = 0;
+    double alpha = 1.0, beta = 0.0;
+    bool a_lower = false;  // op(A) square lower triangular: k runs to the row tile's end
+    bool b_lower = false;  // op(B) square lower triangular: k starts at the column tile
+    bool c_lower = false;  // compute only output tiles on or below the diagonal
+};
+cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s);
+
+// ---- per-block hot path (block_fp64.cu, snp_solve.cu) -------------------------
+
+// Everything a block kernel needs about the cohort (device pointers).
+struct CohortDev {
+    int64_t n = 0;
+    int q = 0;            // p - 1 fixed covariates
+    int t = 0;            // phenotypes
+    const double* W = nullptr;     // L^{-1}, n x n col-major, ld = ldw
+    int64_t ldw = 0;
+    const double* XLbar = nullptr; // n x q, ld = n
+    const double* Ybar = nullptr;  // n x t, ld = n
+    const double* S_TL = nullptr;  // q x q, ld = q
+    const double* bbar_T = nullptr;// q x t, ld = q
+};
+
+// Number of per-SNP reduction values: q (S_BL) + 1 (S_BR) + t (bbar_B).
+inline int n_red(const CohortDev& c) { return c.q + 1 + c.t; }
+
+// FP64 path: for each (64-row tile r, 64-SNP tile) computes Xbar = W[r-tile, :] X
+// and its row-tile partial sums of Xbar^T [Xbar_L | Xbar | Ybar] into
+// part[(rt * nred + v) * ldp + snp]. Also writes bad[snp] (1 = dosage outside {0,1,2}).
+cudaError_t launch_block_fp64(const CohortDev& c, const int8_t* X, int64_t ldx, int64_t mb,
+                              double* part, int64_t ldp, uint8_t* bad, cudaStream_t s);
+
+// Sums the row-tile partials of each SNP in a fixed order, assembles S_i and bbar_i
+// (Algorithm 1), solves by p x p Cholesky, writes b, wald (may be null), status.
+cudaError_t launch_snp_solve(const CohortDev& c, const double* part, int64_t ldp, int n_tiles,
+                             const uint8_t* bad, int64_t mb, double* b, double* wald,
+                             uint8_t* status, cudaStream_t s);
+
+}  // namespace gwas

@@ -1,0 +1,254 @@
+"""Thin ctypes binding of the C ABI in ``include/gwas.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own: all steps of the GLS path run in the CUDA library
+``libgwas_gb300.so``. Array arguments may be numpy arrays (host memory), torch
+tensors (host or device; their ``data_ptr()`` is passed) or raw integer addresses.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libgwas_gb300.so"
+
+GWAS_OK = 0
+GWAS_ERR_ARG = 1
+GWAS_ERR_NOT_SPD = 2
+GWAS_ERR_CUDA = 3
+GWAS_ERR_OOM = 4
+GWAS_ERR_TIMEOUT = 5
+GWAS_ERR_STATE = 6
+GWAS_ERR_UNSUPPORTED = 7
+STATUS_NAMES = {0: "GWAS_OK", 1: "GWAS_ERR_ARG", 2: "GWAS_ERR_NOT_SPD", 3: "GWAS_ERR_CUDA",
+                4: "GWAS_ERR_OOM", 5: "GWAS_ERR_TIMEOUT", 6: "GWAS_ERR_STATE",
+                7: "GWAS_ERR_UNSUPPORTED"}
+
+GWAS_PREC_FP64 = 0
+GWAS_PREC_MIXED = 1
+
+
+class gwas_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("m_blk", ctypes.c_int), ("n_limbs", ctypes.c_int),
+                ("tile_cfg", ctypes.c_int), ("device", ctypes.c_int), ("timing", ctypes.c_int)]
+
+
+class gwas_stats(ctypes.Structure):
+    _fields_ = [("blocks", ctypes.c_int64), ("snps", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("trsm_launches", ctypes.c_int64),
+                ("trsm_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_int64),
+                ("d2h_bytes", ctypes.c_int64), ("factor_ms", ctypes.c_double),
+                ("factor_launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GwasError(RuntimeError):
+    def __init__(self, status: int, message: str, index: int = -1):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.index = index
+
+
+_ctx_p = ctypes.c_void_p
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+
+# name -> (restype, argtypes): one line per declaration of include/gwas.h
+SIGNATURES = {
+    "gwas_default_opts": (None, [ctypes.POINTER(gwas_opts)]),
+    "gwas_init": (_int, [_i64, _int, _int, ctypes.POINTER(gwas_opts), ctypes.POINTER(_ctx_p)]),
+    "gwas_factor": (_int, [_ctx_p, _vp, _int, _dbl, _dbl, _vp, _vp]),
+    "gwas_solve_block": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp]),
+    "gwas_solve_block_device": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp]),
+    "gwas_solve_all": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp]),
+    "gwas_sync": (_int, [_ctx_p, _int]),
+    "gwas_finalize": (_int, [_ctx_p]),
+    "gwas_last_error": (ctypes.c_char_p, [_ctx_p]),
+    "gwas_error_index": (_i64, [_ctx_p]),
+    "gwas_get_stats": (_int, [_ctx_p, ctypes.POINTER(gwas_stats)]),
+    "gwas_reset_stats": (_int, [_ctx_p]),
+    "gwas_stream": (_vp, [_ctx_p]),
+}
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it in-tree first when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists() or os.environ.get("GWAS_FORCE_BUILD"):
+        if not build_if_missing:
+            raise OSError(f"{LIB_PATH} is missing: run paper_1304_2272_gb300.build.build()")
+        from .build import build
+        build()
+    lib = ctypes.CDLL(str(LIB_PATH))
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _addr(x) -> int | None:
+    """Raw address of a numpy array, torch tensor, ctypes buffer or int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot pass {type(x).__name__} as a pointer")
+
+
+def _check(ctx, st: int):
+    if st != GWAS_OK:
+        lib = load()
+        msg = lib.gwas_last_error(ctx).decode() if ctx else ""
+        idx = lib.gwas_error_index(ctx) if ctx else -1
+        raise GwasError(st, msg, idx)
+
+
+def _require(x, dtype, name: str, order: str = "F"):
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype:
+            raise TypeError(f"{name} must be {np.dtype(dtype).name}, got {x.dtype}")
+        ok = x.flags.f_contiguous if order == "F" else x.flags.c_contiguous
+        if not ok and x.ndim > 1:
+            raise ValueError(f"{name} must be contiguous in {order}-order")
+    return x
+
+
+# ---- entry points (same names as the C ABI) -----------------------------------
+def gwas_default_opts() -> gwas_opts:
+    o = gwas_opts()
+    load().gwas_default_opts(ctypes.byref(o))
+    return o
+
+
+def gwas_init(n: int, p: int, t: int = 1, opts: gwas_opts | None = None, **kw):
+    """Create a context; keyword arguments override fields of the default options."""
+    lib = load()
+    o = opts if opts is not None else gwas_default_opts()
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    ctx = _ctx_p()
+    st = lib.gwas_init(int(n), int(p), int(t), ctypes.byref(o), ctypes.byref(ctx))
+    if st != GWAS_OK:
+        raise GwasError(st, "gwas_init failed")
+    return ctx
+
+
+def gwas_factor(ctx, M_or_Phi, is_phi: bool, h: float, sigma2: float, XL, Y) -> None:
+    for a, nm in ((M_or_Phi, "M_or_Phi"), (XL, "XL"), (Y, "Y")):
+        _require(a, np.float64, nm)
+    _check(ctx, load().gwas_factor(ctx, _addr(M_or_Phi), int(bool(is_phi)), float(h),
+                                   float(sigma2), _addr(XL), _addr(Y)))
+
+
+def gwas_solve_block(ctx, X, mb: int, b, wald, status) -> None:
+    _require(X, np.int8, "X")
+    _check(ctx, load().gwas_solve_block(ctx, _addr(X), int(mb), _addr(b), _addr(wald),
+                                        _addr(status)))
+
+
+def gwas_solve_block_device(ctx, X, mb: int, b, wald, status) -> None:
+    _check(ctx, load().gwas_solve_block_device(ctx, _addr(X), int(mb), _addr(b), _addr(wald),
+                                               _addr(status)))
+
+
+def gwas_solve_all(ctx, X, m: int, b, wald, status) -> None:
+    _require(X, np.int8, "X")
+    _check(ctx, load().gwas_solve_all(ctx, _addr(X), int(m), _addr(b), _addr(wald),
+                                      _addr(status)))
+
+
+def gwas_sync(ctx, timeout_ms: int = -1) -> None:
+    _check(ctx, load().gwas_sync(ctx, int(timeout_ms)))
+
+
+def gwas_finalize(ctx) -> None:
+    if ctx:
+        load().gwas_finalize(ctx)
+
+
+def gwas_last_error(ctx) -> str:
+    return load().gwas_last_error(ctx).decode()
+
+
+def gwas_error_index(ctx) -> int:
+    return int(load().gwas_error_index(ctx))
+
+
+def gwas_get_stats(ctx) -> dict:
+    s = gwas_stats()
+    _check(ctx, load().gwas_get_stats(ctx, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def gwas_reset_stats(ctx) -> None:
+    _check(ctx, load().gwas_reset_stats(ctx))
+
+
+def gwas_stream(ctx) -> int:
+    return int(load().gwas_stream(ctx) or 0)
+
+
+# ---- convenience wrapper (still marshalling only) --------------------------------
+class GLS:
+    """One cohort: ``GLS(n, p, t).factor(phi, h, sigma2, XL, Y).solve(X)``."""
+
+    def __init__(self, n: int, p: int = 4, t: int = 1, **opts):
+        self.n, self.p, self.t = int(n), int(p), int(t)
+        self.ctx = gwas_init(n, p, t, **opts)
+
+    def factor(self, M_or_Phi, h=None, sigma2=None, XL=None, Y=None, is_phi=True):
+        Y = np.asfortranarray(np.asarray(Y, dtype=np.float64).reshape(self.n, -1))
+        XL = np.asfortranarray(np.asarray(XL, dtype=np.float64).reshape(self.n, -1))
+        A = np.asfortranarray(np.asarray(M_or_Phi, dtype=np.float64))
+        gwas_factor(self.ctx, A, is_phi, 0.0 if h is None else h,
+                    1.0 if sigma2 is None else sigma2, XL, Y)
+        return self
+
+    def solve(self, X):
+        """b (m x t x p), wald (m x t), status (m) for host dosages X (n x m int8)."""
+        X = np.asfortranarray(np.asarray(X, dtype=np.int8))
+        m = X.shape[1]
+        b = np.empty((m, self.t, self.p), dtype=np.float64)
+        wald = np.empty((m, self.t), dtype=np.float64)
+        status = np.empty(m, dtype=np.uint8)
+        if m:
+            gwas_solve_all(self.ctx, X, m, b, wald, status)
+        return b, wald, status
+
+    def stats(self) -> dict:
+        return gwas_get_stats(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            gwas_finalize(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
