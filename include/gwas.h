@@ -49,7 +49,8 @@ typedef enum {
     GWAS_ERR_OOM = 4,         /* device or pinned-host allocation failed             */
     GWAS_ERR_TIMEOUT = 5,     /* gwas_sync gave up waiting; work is still in flight  */
     GWAS_ERR_STATE = 6,       /* call out of order (e.g. solve before factor)        */
-    GWAS_ERR_UNSUPPORTED = 7  /* option combination not built                        */
+    GWAS_ERR_UNSUPPORTED = 7, /* option combination not built                        */
+    GWAS_ERR_TOO_LARGE = 8    /* gwas_solve_block_noalloc: sizes exceed its scratch   */
 } gwas_status;
 
 typedef enum {
@@ -162,6 +163,40 @@ gwas_status gwas_reset_stats(gwas_ctx* ctx);
 
 /* The context's compute stream, as a cudaStream_t cast to void*. */
 void* gwas_stream(const gwas_ctx* ctx);
+
+/*
+ * Allocation-free FP64 block solve. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they call in -- their
+ * GPU memory is already fully reserved by another allocator (a framework's caching
+ * allocator, or a fixed per-process budget), or they run a latency-sensitive serving
+ * loop in which cudaMalloc/cudaFree, which may synchronise the device, are not
+ * acceptable. It allocates nothing and needs no context: it runs the FP64 block
+ * kernels of gwas_solve_block_device on the caller's buffers, and their scratch lives
+ * in one fixed 16 MiB array in device global memory that belongs to the library image
+ * (every GPU that loads the library holds it until the process exits).
+ *
+ * Everything is DEVICE memory of the CURRENT device, column-major:
+ *   Linv    n x n lower-triangular L^{-1} with zeros above the diagonal, ld = ld_linv >= n;
+ *   XLbar   n x (p-1) = L^{-1} X_L;  Ybar n x t = L^{-1} Y  (ld = n);
+ *   S_TL    (p-1) x (p-1) = XLbar^T XLbar;  bbar_T (p-1) x t = XLbar^T Ybar;
+ *   X       n x mb int8 dosages;  b, wald (may be NULL), status as in gwas_solve_block.
+ * Runs on `stream` (a cudaStream_t; NULL = the default stream) and returns once the
+ * work is queued; the caller synchronises.
+ * Scratch limit: ceil(n/64) * (p+t) * round_up(mb,32) * 8 bytes, rounded up to 256,
+ * plus round_up(mb,256) must not exceed 16 MiB (16,777,216 bytes); otherwise the call
+ * returns GWAS_ERR_TOO_LARGE before launching anything (at n = 10,000, p = 4, t = 1 that
+ * is about 2,600 SNPs per call). The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture. All calls share the one array and it keeps the last call's contents
+ * (nothing in it needs to start at zero): calls that overlap on the GPU -- on
+ * different streams, or from different threads -- race on it and must be serialised
+ * by the caller. Errors: GWAS_ERR_ARG, GWAS_ERR_TOO_LARGE, GWAS_ERR_CUDA.
+ */
+gwas_status gwas_solve_block_noalloc(int64_t n, int p, int t, const double* Linv,
+                                     int64_t ld_linv, const double* XLbar, const double* Ybar,
+                                     const double* S_TL, const double* bbar_T, const int8_t* X,
+                                     int64_t mb, double* b, double* wald, uint8_t* status,
+                                     void* stream);
 
 #ifdef __cplusplus
 }

@@ -24,9 +24,10 @@ GWAS_ERR_OOM = 4
 GWAS_ERR_TIMEOUT = 5
 GWAS_ERR_STATE = 6
 GWAS_ERR_UNSUPPORTED = 7
+GWAS_ERR_TOO_LARGE = 8
 STATUS_NAMES = {0: "GWAS_OK", 1: "GWAS_ERR_ARG", 2: "GWAS_ERR_NOT_SPD", 3: "GWAS_ERR_CUDA",
                 4: "GWAS_ERR_OOM", 5: "GWAS_ERR_TIMEOUT", 6: "GWAS_ERR_STATE",
-                7: "GWAS_ERR_UNSUPPORTED"}
+                7: "GWAS_ERR_UNSUPPORTED", 8: "GWAS_ERR_TOO_LARGE"}
 
 GWAS_PREC_FP64 = 0
 GWAS_PREC_MIXED = 1
@@ -76,6 +77,8 @@ SIGNATURES = {
     "gwas_get_stats": (_int, [_ctx_p, ctypes.POINTER(gwas_stats)]),
     "gwas_reset_stats": (_int, [_ctx_p]),
     "gwas_stream": (_vp, [_ctx_p]),
+    "gwas_solve_block_noalloc": (_int, [_i64, _int, _int, _vp, _i64, _vp, _vp, _vp, _vp, _vp,
+                                        _i64, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -204,6 +207,24 @@ def gwas_reset_stats(ctx) -> None:
 
 def gwas_stream(ctx) -> int:
     return int(load().gwas_stream(ctx) or 0)
+
+
+def gwas_solve_block_noalloc(n: int, p: int, t: int, Linv, ld_linv: int, XLbar, Ybar, S_TL,
+                             bbar_T, X, mb: int, b, wald, status, stream=None) -> None:
+    """Allocation-free FP64 block solve on caller-provided device buffers.
+
+    For callers that must not allocate GPU memory at call time (memory already held by
+    another allocator, or a serving loop that cannot afford cudaMalloc). All arrays are
+    device memory on the current device; see include/gwas.h for layouts and the 16 MiB
+    scratch limit (GWAS_ERR_TOO_LARGE beyond it). ``stream`` is a cudaStream_t address
+    (None = the default stream). Returns once the work is queued.
+    """
+    st = load().gwas_solve_block_noalloc(
+        int(n), int(p), int(t), _addr(Linv), int(ld_linv), _addr(XLbar), _addr(Ybar),
+        _addr(S_TL), _addr(bbar_T), _addr(X), int(mb), _addr(b), _addr(wald), _addr(status),
+        stream)
+    if st != GWAS_OK:
+        raise GwasError(st, "gwas_solve_block_noalloc failed")
 
 
 # ---- convenience wrapper (still marshalling only) --------------------------------
