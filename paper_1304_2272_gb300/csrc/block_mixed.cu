@@ -1,0 +1,583 @@
+// Mixed-precision hot path of one SNP block on the BF16 tensor cores (tcgen05).
+//
+// Xbar_blk := L^{-1} X_blk (Algorithm 2, Section 3) is the dominant dense contraction.
+// Dosages {0,1,2} are exact in BF16, so only W = L^{-1} needs splitting: per 64-row
+// tile with exponent E (max |W| <= 2^E),
+//     W = 2^(E-8) * sum_{l<S} A_l * 2^(-9 l) + O(2^(E-9S)),   A_l integers in [-256, 256],
+// and every A_l is exact in BF16. A_l x_i then has integer products <= 512 whose sums
+// stay below 2^24 for n < 32768, so the FP32 tensor-core accumulation of each limb is
+// exact. The epilogue recombines the limbs in 64-bit integers,
+//     T = sum_l C_l * 2^(9 (S-1-l)),   xbar = 2^(E-8-9(S-1)) * T,
+// and accumulates T^2 exactly in 128-bit integers for S_BRi = Xbar_Ri^T Xbar_Ri. The
+// only rounding left is the limb truncation of W (relative 2^(-9S) of the tile maximum)
+// and one conversion to FP64 per (row tile, SNP).
+//
+// The linear reductions of Algorithm 1, S_BLi = Xbar_Ri^T Xbar_L and bbar_Bi =
+// Xbar_Ri^T ybar, are the same numbers as Z^T x_i with Z = L^{-T} [Xbar_L | Ybar]
+// (= M^{-1} [X_L | Y]); Z is split into limbs the same way and appended as extra UMMA
+// rows, so the tensor cores produce them too.
+//
+// Kernel structure (one persistent CTA per SM, 8 warps):
+//   warp 0 lane 0: TMA producer (dosage tile 128 SNPs x 64 k, limb tile N x 64 k),
+//   warp 1 lane 0: tcgen05.mma issuer, FP32 accumulators in TMEM (2 x 256 columns),
+//   warps 4-7   : epilogue, one SNP per thread (TMEM lane), no cross-thread reduction.
+// Every wait is bounded (2 s); on expiry the CTA records an error and winds down.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc.cuh"
+
+namespace gwas {
+namespace mx {
+constexpr int BM = 128;          // SNPs per tile: UMMA M, TMEM lanes
+constexpr int R = 64;            // rows of L^{-1} per tile
+constexpr int BK = 64;           // k per pipeline stage: one 128-byte swizzle row of BF16
+constexpr int BUF = 256;         // TMEM columns per accumulator buffer
+constexpr uint32_t EXTRA = 0xFFFFu;
+constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr int SMEM_BUDGET = 200 * 1024;
+}  // namespace mx
+
+struct MixedArgs {
+    int n_rt;        // row tiles of L^{-1}
+    int n_ct;        // SNP tiles of 128
+    int n_kc_full;   // k chunks covering n
+    int R_e;         // linear rows (q + t)
+    int N_e;         // UMMA N of the linear tile
+    int stages;
+    int group;       // SNP tiles per L2 group
+    int n_units;
+    int64_t mb;
+    int64_t ldp;
+    const int* E_w;
+    const int* E_e;
+    double* sq_part;  // [n_rt][ldp]
+    double* lin;      // [R_e][ldp]
+    int* err;
+};
+
+// Unit u -> (rt, ct). Groups of `group` SNP tiles; inside a group the linear tile of
+// every SNP tile comes first, then row tiles from the heaviest (rt = n_rt-1) down.
+__device__ __forceinline__ void decode_unit(const MixedArgs& a, int u, int& rt, int& ct) {
+    const int levels = a.n_rt + 1;
+    const int per_group = a.group * levels;
+    const int g = u / per_group;
+    const int w = u - g * per_group;
+    const int ngroups = (a.n_ct + a.group - 1) / a.group;
+    const int gsize = (g == ngroups - 1) ? a.n_ct - g * a.group : a.group;
+    const int level = w / gsize;
+    ct = g * a.group + (w - level * gsize);
+    rt = (level == 0) ? (int)mx::EXTRA : a.n_rt - level;
+}
+
+__device__ __forceinline__ void record_error(const MixedArgs& a, volatile int* abort_flag,
+                                             int code) {
+    *abort_flag = 1;
+    atomicCAS(a.err, 0, code);
+}
+
+template <int S>
+__global__ void __launch_bounds__(256, 1)
+k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
+              const __grid_constant__ CUtensorMap tmE, const MixedArgs a) {
+    using namespace tc;
+    constexpr int N = mx::R * S;
+    constexpr uint32_t A_BYTES = mx::BM * mx::BK * 2;
+    const int NB = N > a.N_e ? N : a.N_e;
+    const uint32_t B_BYTES = (uint32_t)NB * mx::BK * 2;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + a.stages * A_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + a.stages * B_BYTES);
+    uint64_t* empty = full + a.stages;
+    uint64_t* tfull = empty + a.stages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* done = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&tfull[s], 1);
+            mbar_init(&tempty[s], 4);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, 2 * mx::BUF);
+        tmem_relinquish();
+    }
+    if (warp == 1 && lane == 0) {
+        prefetch_tmap(&tmX);
+        prefetch_tmap(&tmW);
+        prefetch_tmap(&tmE);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const int P = gridDim.x, me = blockIdx.x;
+    const int rounds = (a.n_units + P - 1) / P;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t issued_parity[16];
+        bool issued[16];
+        for (int s = 0; s < 16; ++s) issued[s] = false;
+        for (int r = 0; r < rounds && !*abort_flag; ++r) {
+            const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
+            if (u >= a.n_units) continue;
+            int rt, ct;
+            decode_unit(a, u, rt, ct);
+            const bool ex = (rt == (int)mx::EXTRA);
+            const int nk = ex ? a.n_kc_full : min(rt + 1, a.n_kc_full);
+            const int ybase = ex ? a.n_rt * N : rt * N;
+            const uint32_t bytes = A_BYTES + (uint32_t)(ex ? a.N_e : N) * mx::BK * 2;
+            for (int kc = 0; kc < nk; ++kc) {
+                if (!mbar_wait(&empty[stage], phase ^ 1, mx::WAIT_NS)) {
+                    record_error(a, abort_flag, 1);
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[stage], bytes);
+                tma_load_2d(sA + stage * A_BYTES, &tmX, kc * mx::BK, ct * mx::BM, &full[stage]);
+                tma_load_2d(sB + stage * B_BYTES, ex ? &tmE : &tmW, kc * mx::BK, ybase,
+                            &full[stage]);
+                issued[stage] = true;
+                issued_parity[stage] = phase;
+                if (++stage == a.stages) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+            }
+        }
+        if (*abort_flag) {
+            // let copies already in flight land before the CTA's shared memory goes away
+            for (int s = 0; s < a.stages && s < 16; ++s)
+                if (issued[s]) mbar_wait(&full[s], issued_parity[s], 10000000ull);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        int stage = 0;
+        uint32_t phase = 0;
+        int abuf = 0;
+        uint32_t aphase = 0;
+        for (int r = 0; r < rounds && !*abort_flag; ++r) {
+            const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
+            if (u >= a.n_units) continue;
+            int rt, ct;
+            decode_unit(a, u, rt, ct);
+            const bool ex = (rt == (int)mx::EXTRA);
+            const int nk = ex ? a.n_kc_full : min(rt + 1, a.n_kc_full);
+            if (!mbar_wait(&tempty[abuf], aphase ^ 1, mx::WAIT_NS)) {
+                record_error(a, abort_flag, 2);
+                break;
+            }
+            fence_after_sync();
+            const uint32_t d = tmem_base + (uint32_t)(abuf * mx::BUF);
+            const uint32_t idesc = idesc_bf16_f32(mx::BM, ex ? a.N_e : N);
+            bool ok = true;
+            for (int kc = 0; kc < nk; ++kc) {
+                if (!mbar_wait(&full[stage], phase, mx::WAIT_NS)) {
+                    record_error(a, abort_flag, 3);
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint64_t ad = smem_desc_sw128(smem_u32(sA + stage * A_BYTES));
+                const uint64_t bd = smem_desc_sw128(smem_u32(sB + stage * B_BYTES));
+#pragma unroll
+                for (int kk = 0; kk < mx::BK / 16; ++kk)
+                    umma_bf16(d, ad + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0);
+                umma_commit(&empty[stage]);
+                if (++stage == a.stages) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+            }
+            if (!ok) break;
+            umma_commit(&tfull[abuf]);
+            abuf ^= 1;
+            if (abuf == 0) aphase ^= 1;
+        }
+        // every MMA issued by this thread has completed once `done` flips
+        umma_commit(done);
+        mbar_wait(done, 0, mx::WAIT_NS);
+    } else if (warp >= 4) {
+        // ---------------- epilogue: one SNP per thread ----------------
+        const int qd = warp & 3;
+        int abuf = 0;
+        uint32_t aphase = 0;
+        const int shift0 = 8 + 9 * (S - 1);
+        for (int r = 0; r < rounds && !*abort_flag; ++r) {
+            const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
+            if (u >= a.n_units) continue;
+            int rt, ct;
+            decode_unit(a, u, rt, ct);
+            const bool ex = (rt == (int)mx::EXTRA);
+            if (!mbar_wait(&tfull[abuf], aphase, mx::WAIT_NS)) {
+                record_error(a, abort_flag, 4);
+                break;
+            }
+            fence_after_sync();
+            const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
+            const int64_t snp = (int64_t)ct * mx::BM + qd * 32 + lane;
+            if (!ex) {
+                unsigned __int128 acc = 0;
+#pragma unroll 1
+                for (int i0 = 0; i0 < mx::R; i0 += 16) {
+                    uint32_t v[S][16];
+#pragma unroll
+                    for (int l = 0; l < S; ++l) tmem_ld16(tb + (uint32_t)(l * mx::R + i0), v[l]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        long long T = 0;
+#pragma unroll
+                        for (int l = 0; l < S; ++l)
+                            T = T * 512 + (long long)__float2int_rn(__uint_as_float(v[l][i]));
+                        const unsigned long long uT = (unsigned long long)(T < 0 ? -T : T);
+                        acc += (unsigned __int128)uT * uT;
+                    }
+                }
+                const double hi = (double)(unsigned long long)(acc >> 64);
+                const double lo = (double)(unsigned long long)acc;
+                const double val = ldexp(fma(hi, 18446744073709551616.0, lo),
+                                         2 * (a.E_w[rt] - shift0));
+                if (snp < a.mb) a.sq_part[(int64_t)rt * a.ldp + snp] = val;
+            } else {
+#pragma unroll 1
+                for (int j = 0; j < a.R_e; ++j) {
+                    long long T = 0;
+#pragma unroll
+                    for (int l = 0; l < S; ++l) {
+                        uint32_t x;
+                        tmem_ld1(tb + (uint32_t)(l * a.R_e + j), x);
+                        tmem_wait_ld();
+                        T = T * 512 + (long long)__float2int_rn(__uint_as_float(x));
+                    }
+                    if (snp < a.mb)
+                        a.lin[(int64_t)j * a.ldp + snp] = ldexp((double)T, a.E_e[j] - shift0);
+                }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[abuf]);
+            abuf ^= 1;
+            if (abuf == 0) aphase ^= 1;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        fence_after_sync();
+        tmem_dealloc(tmem_base, 2 * mx::BUF);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Dosages -> BF16 rows (one SNP per row, k contiguous), flags for bad dosages.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_geno_bf16(const int8_t* __restrict__ X, int64_t ldx, int64_t n, int64_t mb,
+            uint16_t* __restrict__ Xb, int64_t n_pad, uint8_t* __restrict__ bad) {
+    for (int64_t j = blockIdx.x; j < mb; j += gridDim.x) {
+        const int8_t* src = X + j * ldx;
+        uint16_t* dst = Xb + j * n_pad;
+        int flag = 0;
+        for (int64_t k = 4 * (int64_t)threadIdx.x; k < n; k += 4 * (int64_t)blockDim.x) {
+            uint16_t o[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int v = (k + e < n) ? (int)src[k + e] : 0;
+                flag |= (unsigned)v > 2u;
+                o[e] = v == 1 ? 0x3F80u : (v == 2 ? 0x4000u : 0u);
+            }
+            if (k + 3 < n) {
+                *reinterpret_cast<uint2*>(dst + k) =
+                    make_uint2((uint32_t)o[0] | ((uint32_t)o[1] << 16),
+                               (uint32_t)o[2] | ((uint32_t)o[3] << 16));
+            } else {
+                for (int e = 0; k + e < n; ++e) dst[k + e] = o[e];
+            }
+        }
+        flag = __syncthreads_or(flag);
+        if (threadIdx.x == 0) bad[j] = (uint8_t)(flag != 0);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Exponents and limb split of L^{-1} (row tiles) and of Z (linear rows).
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_absmax_w(const double* __restrict__ W, int64_t ldw, int64_t n, unsigned long long* bits) {
+    // grid: x = k chunks of 256, y = row tile
+    const int rt = blockIdx.y;
+    const int64_t r = (int64_t)rt * 64 + (threadIdx.x % 64);
+    double m = 0.0;
+    if (r < n) {
+        const int64_t k_end = min64(r + 1, n);
+        for (int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x / 64; k < k_end &&
+                                                                      k < (int64_t)(blockIdx.x + 1) * 256;
+             k += 4)
+            m = fmax(m, fabs(W[r + k * ldw]));
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && red[0] > 0.0)
+        atomicMax(&bits[rt], (unsigned long long)__double_as_longlong(red[0]));
+}
+
+__global__ void __launch_bounds__(256)
+k_absmax_z(const double* __restrict__ Z, int64_t n, unsigned long long* bits) {
+    const int j = blockIdx.y;
+    double m = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(Z[k + (int64_t)j * n]));
+    __shared__ double red[256];
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && red[0] > 0.0)
+        atomicMax(&bits[j], (unsigned long long)__double_as_longlong(red[0]));
+}
+
+// E with max|.| <= 2^E (frexp exponent); 0 for an all-zero tile.
+__global__ void k_exponents(const unsigned long long* bits, int count, int* E) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    int e = 0;
+    const double m = __longlong_as_double((long long)bits[i]);
+    if (m > 0.0) frexp(m, &e);
+    E[i] = e;
+}
+
+template <int S>
+__device__ __forceinline__ void split_limbs(double w, int E, uint16_t (&out)[S]) {
+    double r = ldexp(w, 8 - E);  // |r| <= 256
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+        const double a = rint(r);
+        r = (r - a) * 512.0;  // exact: |r - a| <= 1/2
+        // |a| <= 256 has at most 9 significant bits: the top half of its FP32 pattern
+        // is its exact BF16 pattern
+        out[l] = (uint16_t)(__float_as_uint((float)a) >> 16);
+    }
+}
+
+// Lower triangle of W (column-major) -> limb rows rt*N + l*64 + i of WL (k contiguous).
+template <int S>
+__global__ void __launch_bounds__(256)
+k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, const int* __restrict__ E_w,
+          uint16_t* __restrict__ WL, int64_t n_pad) {
+    __shared__ double tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+    if (k0 > r0 + 31) return;  // strictly upper tile: stays zero
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+    for (int j = ty; j < 32; j += 8) {
+        const int64_t r = r0 + tx, k = k0 + j;
+        tile[j][tx] = (r < n && k < n && k <= r) ? W[r + k * ldw] : 0.0;
+    }
+    __syncthreads();
+    constexpr int N = 64 * S;
+    for (int j = ty; j < 32; j += 8) {
+        const int64_t r = r0 + j, k = k0 + tx;
+        if (r >= n || k >= n || k > r) continue;
+        const int rt = (int)(r / 64), i = (int)(r % 64);
+        uint16_t limbs[S];
+        split_limbs<S>(tile[tx][j], E_w[rt], limbs);
+#pragma unroll
+        for (int l = 0; l < S; ++l) WL[((int64_t)rt * N + l * 64 + i) * n_pad + k] = limbs[l];
+    }
+}
+
+// Z (n x R_e, column-major) -> limb rows base + l*R_e + j of WL.
+template <int S>
+__global__ void __launch_bounds__(256)
+k_split_z(const double* __restrict__ Z, int64_t n, int R_e, const int* __restrict__ E_e,
+          uint16_t* __restrict__ WL, int64_t n_pad, int64_t base_row) {
+    const int j = blockIdx.y;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        uint16_t limbs[S];
+        split_limbs<S>(Z[k + (int64_t)j * n], E_e[j], limbs);
+#pragma unroll
+        for (int l = 0; l < S; ++l) WL[(base_row + (int64_t)l * R_e + j) * n_pad + k] = limbs[l];
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Host side.
+// ----------------------------------------------------------------------------
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+bool tmap_bf16_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
+                  uint32_t box_inner, uint32_t box_outer) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+              es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int S>
+int stage_count(int N_e) {
+    const int N = 64 * S;
+    const int NB = std::max(N, N_e);
+    const int per = mx::BM * mx::BK * 2 + NB * mx::BK * 2;
+    return std::min(8, mx::SMEM_BUDGET / per);
+}
+
+template <int S>
+size_t smem_bytes(int N_e, int stages) {
+    const int NB = std::max(64 * S, N_e);
+    return (size_t)stages * (mx::BM * mx::BK * 2 + NB * mx::BK * 2) + 1024 + 256;
+}
+
+}  // namespace
+
+int mixed_linear_n(int S, int R_e) { return (int)round_up((int64_t)S * R_e, 16); }
+
+cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk) {
+    m.S = S;
+    m.n = n;
+    m.n_rt = (int)ceil_div(n, 64);
+    m.n_pad = round_up(n, 64);
+    m.R_e = R_e;
+    m.N_e = mixed_linear_n(S, R_e);
+    m.rows_total = (int64_t)m.n_rt * 64 * S + m.N_e;
+    m.mb_pad_max = round_up(m_blk, mx::BM);
+    m.ldp = round_up(m_blk, 32);
+    return cudaSuccess;
+}
+
+cudaError_t mixed_prepare(MixedDev& m, const double* W, int64_t ldw, const double* Z,
+                          cudaStream_t s, int64_t* launches) {
+    cudaError_t e;
+    const int64_t n = m.n;
+    if ((e = cudaMemsetAsync(m.WL, 0, (size_t)m.rows_total * m.n_pad * 2, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.bits, 0, (size_t)(m.n_rt + m.R_e) * 8, s)) != cudaSuccess) return e;
+    k_absmax_w<<<dim3((unsigned)ceil_div(n, 256), (unsigned)m.n_rt), 256, 0, s>>>(W, ldw, n, m.bits);
+    k_absmax_z<<<dim3(64, (unsigned)m.R_e), 256, 0, s>>>(Z, n, m.bits + m.n_rt);
+    k_exponents<<<(unsigned)ceil_div(m.n_rt + m.R_e, 128), 128, 0, s>>>(m.bits, m.n_rt + m.R_e, m.E);
+    const dim3 gw((unsigned)ceil_div(n, 32), (unsigned)ceil_div((int64_t)m.n_rt * 64, 32));
+    const dim3 gz(64, (unsigned)m.R_e);
+    const int64_t zbase = (int64_t)m.n_rt * 64 * m.S;
+    switch (m.S) {
+        case 2:
+            k_split_w<2><<<gw, 256, 0, s>>>(W, ldw, n, m.E, m.WL, m.n_pad);
+            k_split_z<2><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
+            break;
+        case 3:
+            k_split_w<3><<<gw, 256, 0, s>>>(W, ldw, n, m.E, m.WL, m.n_pad);
+            k_split_z<3><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
+            break;
+        case 4:
+            k_split_w<4><<<gw, 256, 0, s>>>(W, ldw, n, m.E, m.WL, m.n_pad);
+            k_split_z<4><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    if (launches) *launches += 6;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // tensor maps over the fixed buffers
+    const int N = 64 * m.S;
+    if (!tmap_bf16_2d(&m.tmX, m.Xb, (uint64_t)m.n_pad, (uint64_t)m.mb_pad_max, mx::BK, mx::BM) ||
+        !tmap_bf16_2d(&m.tmW, m.WL, (uint64_t)m.n_pad, (uint64_t)m.rows_total, mx::BK, (uint32_t)N) ||
+        !tmap_bf16_2d(&m.tmE, m.WL, (uint64_t)m.n_pad, (uint64_t)m.rows_total, mx::BK,
+                      (uint32_t)m.N_e))
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+template <int S>
+static cudaError_t launch_mixed_t(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
+    MixedArgs a;
+    a.n_rt = m.n_rt;
+    a.n_ct = (int)ceil_div(mb, mx::BM);
+    a.n_kc_full = (int)(m.n_pad / mx::BK);
+    a.R_e = m.R_e;
+    a.N_e = m.N_e;
+    a.stages = stage_count<S>(m.N_e);
+    const int64_t per_tile = (int64_t)mx::BM * m.n_pad * 2;  // BF16 dosages of one SNP tile
+    a.group = (int)std::max<int64_t>(1, std::min<int64_t>(a.n_ct, (40ll << 20) / per_tile));
+    a.n_units = a.n_ct * (a.n_rt + 1);
+    a.mb = mb;
+    a.ldp = m.ldp;
+    a.E_w = m.E;
+    a.E_e = m.E + m.n_rt;
+    a.sq_part = m.sq_part;
+    a.lin = m.lin;
+    a.err = m.err;
+    const size_t smem = smem_bytes<S>(m.N_e, a.stages);
+    cudaError_t e = cudaFuncSetAttribute(k_block_mixed<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(num_sms, a.n_units));
+    k_block_mixed<S><<<grid, 256, smem, s>>>(m.tmX, m.tmW, m.tmE, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geno_bf16(const MixedDev& m, const int8_t* X, int64_t ldx, int64_t mb,
+                             uint8_t* bad, cudaStream_t s) {
+    const unsigned grid = (unsigned)std::min<int64_t>(mb, 65535);
+    k_geno_bf16<<<grid, 256, 0, s>>>(X, ldx, m.n, mb, m.Xb, m.n_pad, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
+    if (mb < 1 || mb > m.mb_pad_max) return cudaErrorInvalidValue;
+    switch (m.S) {
+        case 2: return launch_mixed_t<2>(m, mb, num_sms, s);
+        case 3: return launch_mixed_t<3>(m, mb, num_sms, s);
+        case 4: return launch_mixed_t<4>(m, mb, num_sms, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gwas

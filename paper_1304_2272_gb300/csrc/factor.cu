@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
     if (g.c_lower && j0 > i0) return;
     int64_t kbeg = 0, kend = g.K;
     if (g.a_lower) kend = min64(kend, i0 + T64);
-    if (g.b_lower) kbeg = j0;
+    if (g.a_upper) kbeg = i0;
+    if (g.b_lower && j0 > kbeg) kbeg = j0;
 
     double acc[4][4];
 #pragma unroll

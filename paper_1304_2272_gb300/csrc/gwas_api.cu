@@ -41,6 +41,11 @@ struct gwas_ctx {
     double* part = nullptr;       // row-tile partial sums
     int64_t ldp = 0;
     uint8_t* bad = nullptr;
+    // mixed-precision path
+    bool mixed = false;
+    MixedDev mx;
+    double* Z = nullptr;          // n x (q + t): L^{-T} [Xbar_L | Ybar]
+    int num_sms = 0;
     cudaStream_t s_comp = nullptr, s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
     int slot = 0;
@@ -125,13 +130,30 @@ gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, doubl
         e1 = pooled_event(c);
         CK(cudaEventRecord(e0, c->s_comp));
     }
-    CK(launch_block_fp64(cv, X, c->n, mb, c->part, c->ldp, c->bad, c->s_comp));
+    if (c->mixed) {
+        // the dosage conversion runs before the timed region of the dominant kernel
+        if (c->opts.timing) {
+            CK(cudaEventRecord(e1, c->s_comp));
+            CK(launch_geno_bf16(c->mx, X, c->n, mb, c->bad, c->s_comp));
+            CK(cudaEventRecord(e0, c->s_comp));
+        } else {
+            CK(launch_geno_bf16(c->mx, X, c->n, mb, c->bad, c->s_comp));
+        }
+        CK(launch_block_mixed(c->mx, mb, c->num_sms, c->s_comp));
+    } else {
+        CK(launch_block_fp64(cv, X, c->n, mb, c->part, c->ldp, c->bad, c->s_comp));
+    }
     if (c->opts.timing) {
         CK(cudaEventRecord(e1, c->s_comp));
         c->timed.emplace_back(e0, e1);
     }
-    CK(launch_snp_solve(cv, c->part, c->ldp, (int)ceil_div(c->n, T64), c->bad, mb, b, wald,
-                        status, c->s_comp));
+    if (c->mixed) {
+        CK(launch_snp_solve_mixed(cv, c->mx, c->bad, mb, b, wald, status, c->s_comp));
+        c->stats.kernel_launches += 1;
+    } else {
+        CK(launch_snp_solve(cv, c->part, c->ldp, (int)ceil_div(c->n, T64), c->bad, mb, b, wald,
+                            status, c->s_comp));
+    }
     c->stats.kernel_launches += 2;
     c->stats.trsm_launches += 1;
     c->stats.blocks += 1;
@@ -143,6 +165,8 @@ void free_all(gwas_ctx* c) {
     cudaFree(c->L); cudaFree(c->W); cudaFree(c->Dinv); cudaFree(c->XLbar); cudaFree(c->Ybar);
     cudaFree(c->S_TL); cudaFree(c->bbar_T); cudaFree(c->d_info); cudaFree(c->part);
     cudaFree(c->bad);
+    cudaFree(c->Z); cudaFree(c->mx.WL); cudaFree(c->mx.bits); cudaFree(c->mx.E);
+    cudaFree(c->mx.Xb); cudaFree(c->mx.sq_part); cudaFree(c->mx.lin); cudaFree(c->mx.err);
     for (int s = 0; s < 2; ++s) {
         cudaFree(c->Xslot[s]); cudaFree(c->bslot[s]); cudaFree(c->wslot[s]); cudaFree(c->sslot[s]);
         if (c->ev_h2d[s]) cudaEventDestroy(c->ev_h2d[s]);
@@ -177,8 +201,15 @@ gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx**
     gwas_default_opts(&o);
     if (opts) o = *opts;
     if (n < 1 || p < 2 || p > MAX_P || t < 1 || t > MAX_T || o.m_blk < 1) return GWAS_ERR_ARG;
-    if (o.precision != GWAS_PREC_FP64) return GWAS_ERR_UNSUPPORTED;
+    if (o.precision != GWAS_PREC_FP64 && o.precision != GWAS_PREC_MIXED) return GWAS_ERR_ARG;
     if (n > (int64_t)1 << 31) return GWAS_ERR_ARG;
+    if (o.precision == GWAS_PREC_MIXED) {
+        // exact FP32 accumulation of integer limb products needs 512 n < 2^24; the
+        // linear tile must fit one UMMA (N <= 256)
+        if (o.n_limbs < 2 || o.n_limbs > 4 || n >= 32768 ||
+            o.n_limbs * ((p - 1) + t) > 256)
+            return GWAS_ERR_UNSUPPORTED;
+    }
     gwas_ctx* c = new gwas_ctx();
     c->opts = o;
     c->device = o.device;
@@ -210,7 +241,24 @@ gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx**
     CKI(dmalloc(&c->d_info, 1));
     c->ldp = round_up(o.m_blk, 32);
     const int nred = c->q + 1 + t;
-    CKI(dmalloc(&c->part, (size_t)nt * nred * c->ldp));
+    c->mixed = (o.precision == GWAS_PREC_MIXED);
+    CKI(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (!c->mixed) {
+        CKI(dmalloc(&c->part, (size_t)nt * nred * c->ldp));
+    } else {
+        MixedDev& m = c->mx;
+        mixed_layout(m, n, o.n_limbs, c->q + t, o.m_blk);
+        CKI(dmalloc(&c->Z, (size_t)n * (c->q + t)));
+        CKI(dmalloc(&m.WL, (size_t)m.rows_total * m.n_pad));
+        CKI(dmalloc(&m.bits, (size_t)(m.n_rt + m.R_e)));
+        CKI(dmalloc(&m.E, (size_t)(m.n_rt + m.R_e)));
+        CKI(dmalloc(&m.Xb, (size_t)m.mb_pad_max * m.n_pad));
+        CKI(cudaMemset(m.Xb, 0, (size_t)m.mb_pad_max * m.n_pad * sizeof(uint16_t)));
+        CKI(dmalloc(&m.sq_part, (size_t)m.n_rt * m.ldp));
+        CKI(dmalloc(&m.lin, (size_t)m.R_e * m.ldp));
+        CKI(dmalloc(&m.err, 1));
+        CKI(cudaMemset(m.err, 0, sizeof(int)));
+    }
     CKI(dmalloc(&c->bad, (size_t)o.m_blk));
     for (int s = 0; s < 2; ++s) {
         CKI(dmalloc(&c->Xslot[s], (size_t)n * o.m_blk));
@@ -283,6 +331,18 @@ gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double 
         bt.N = c->t; bt.B = c->Ybar; bt.C = c->bbar_T;
         CK(gemm_f64(bt, s));
         nl += 4;
+        if (c->mixed) {
+            // Z := W^T [Xbar_L | Ybar] (so S_BLi = Z_L^T x_i and bbar_Bi = Z_y^T x_i)
+            GemmF64 z;
+            z.M = n; z.N = c->q; z.K = n; z.A = c->W; z.lda = ld; z.transA = true;
+            z.a_upper = true; z.B = c->XLbar; z.ldb = n; z.C = c->Z; z.ldc = n;
+            CK(gemm_f64(z, s));
+            GemmF64 zy = z;
+            zy.N = c->t; zy.B = c->Ybar; zy.C = c->Z + (size_t)n * c->q;
+            CK(gemm_f64(zy, s));
+            nl += 2;
+            CK(mixed_prepare(c->mx, c->W, ld, c->Z, s, &nl));
+        }
     }
     CK(cudaEventRecord(f1, s));
     int info = 0;
@@ -371,9 +431,19 @@ gwas_status gwas_sync(gwas_ctx* c, int timeout_ms) {
     if (!c) return GWAS_ERR_ARG;
     DeviceGuard g(c->device);
     cudaStream_t ss[3] = {c->s_h2d, c->s_comp, c->s_d2h};
+    auto check_kernel_flag = [&]() -> gwas_status {
+        if (!c->mixed || !c->mx.err) return GWAS_OK;
+        int code = 0;
+        CK(cudaMemcpy(&code, c->mx.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (code == 0) return GWAS_OK;
+        CK(cudaMemset(c->mx.err, 0, sizeof(int)));
+        char buf[128];
+        snprintf(buf, sizeof buf, "mixed block kernel: a pipeline wait timed out (site %d)", code);
+        return fail(c, GWAS_ERR_CUDA, buf);
+    };
     if (timeout_ms < 0) {
         for (auto s : ss) CK(cudaStreamSynchronize(s));
-        return GWAS_OK;
+        return check_kernel_flag();
     }
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
@@ -383,7 +453,7 @@ gwas_status gwas_sync(gwas_ctx* c, int timeout_ms) {
             if (e == cudaErrorNotReady) { done = false; continue; }
             if (e != cudaSuccess) return cuda_fail(c, e, "gwas_sync");
         }
-        if (done) return GWAS_OK;
+        if (done) return check_kernel_flag();
         const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(
                             std::chrono::steady_clock::now() - t0).count();
         if (el >= timeout_ms) return fail(c, GWAS_ERR_TIMEOUT, "gwas_sync: timed out");

@@ -1,6 +1,7 @@
 // Host-side launchers of the engine's CUDA kernels (internal; not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -35,6 +36,7 @@ struct GemmF64 {
     double* C = nullptr; int64_t ldc = 0;
     double alpha = 1.0, beta = 0.0;
     bool a_lower = false;  // op(A) square lower triangular: k runs to the row tile's end
+    bool a_upper = false;  // op(A) square upper triangular: k starts at the row tile
     bool b_lower = false;  // op(B) square lower triangular: k starts at the column tile
     bool c_lower = false;  // compute only output tiles on or below the diagonal
 };
@@ -69,5 +71,43 @@ cudaError_t launch_block_fp64(const CohortDev& c, const int8_t* X, int64_t ldx, 
 cudaError_t launch_snp_solve(const CohortDev& c, const double* part, int64_t ldp, int n_tiles,
                              const uint8_t* bad, int64_t mb, double* b, double* wald,
                              uint8_t* status, cudaStream_t s);
+
+// ---- mixed-precision hot path (block_mixed.cu) ----------------------------------
+
+// Device buffers and tensor maps of the BF16-limb path for one cohort.
+struct MixedDev {
+    int S = 3;                  // BF16 limbs per element of L^{-1} and Z
+    int64_t n = 0;
+    int n_rt = 0;               // 64-row tiles of L^{-1}
+    int64_t n_pad = 0;          // n rounded up to 64 (k extent of every BF16 row)
+    int R_e = 0;                // linear rows q + t (Z = L^{-T} [Xbar_L | Ybar])
+    int N_e = 0;                // UMMA N of the linear tile (S * R_e rounded up to 16)
+    int64_t rows_total = 0;     // rows of WL: n_rt * 64 * S + N_e
+    int64_t mb_pad_max = 0;     // rows of Xb
+    int64_t ldp = 0;            // leading dimension of sq_part / lin
+    uint16_t* WL = nullptr;     // BF16 limbs, [rows_total][n_pad], k contiguous
+    unsigned long long* bits = nullptr;  // max |.| per row tile / linear row (FP64 bits)
+    int* E = nullptr;           // exponents: n_rt row tiles, then R_e linear rows
+    uint16_t* Xb = nullptr;     // BF16 dosages, [mb_pad_max][n_pad]
+    double* sq_part = nullptr;  // [n_rt][ldp] row-tile partials of S_BRi
+    double* lin = nullptr;      // [R_e][ldp] S_BLi (q rows) then bbar_Bi (t rows)
+    int* err = nullptr;         // kernel wait-timeout code (0 = none)
+    CUtensorMap tmX, tmW, tmE;  // TMA maps of Xb, WL (row tiles), WL (linear tile)
+};
+
+int mixed_linear_n(int S, int R_e);
+cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk);
+// Exponents and BF16 limbs of W = L^{-1} (lower triangle) and Z (n x R_e), tensor maps.
+cudaError_t mixed_prepare(MixedDev& m, const double* W, int64_t ldw, const double* Z,
+                          cudaStream_t s, int64_t* launches);
+// Dosages (n x mb int8, column-major) -> BF16 rows of m.Xb and bad-dosage flags.
+cudaError_t launch_geno_bf16(const MixedDev& m, const int8_t* X, int64_t ldx, int64_t mb,
+                             uint8_t* bad, cudaStream_t s);
+// The tcgen05 kernel: row-tile partials of S_BRi into m.sq_part, S_BLi / bbar_Bi into m.lin.
+cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s);
+// p x p solves from the mixed partial layout.
+cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const uint8_t* bad,
+                                   int64_t mb, double* b, double* wald, uint8_t* status,
+                                   cudaStream_t s);
 
 }  // namespace gwas

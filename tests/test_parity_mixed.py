@@ -1,0 +1,137 @@
+"""Mixed-precision CUDA path (BF16 limbs of L^{-1} on tcgen05) vs the FP64 oracle.
+
+Tolerance: every coefficient of b_i within 1e-6 of the FP64 oracle, relative to
+max_c |b_ic| of the same SNP, for 3 and 4 limbs (the contract of the mixed path).
+With 2 limbs the limb truncation alone is ~2^-18 of the row maximum per element of
+L^{-1}; the tests hold that option to 1e-4. The Wald statistic's error is reported,
+not bounded, except that it must stay below 1e-3 max(W, 1) for 3+ limbs.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gls as G
+
+pytestmark = pytest.mark.gpu
+
+TOL = {2: 1e-4, 3: 1e-6, 4: 1e-6}
+
+
+def rel_b(b, ref):
+    scale = np.maximum(np.nanmax(np.abs(ref), axis=-1, keepdims=True), 1e-300)
+    return float(np.nanmax(np.abs(b - ref) / scale))
+
+
+def wald_err(w, rw):
+    return float(np.max(np.abs(w - rw) / np.maximum(rw, 1.0)))
+
+
+@pytest.fixture(scope="module")
+def gwas(gpu):
+    from paper_1304_2272_gb300 import gwas as g
+    g.load()
+    return g
+
+
+def run(gwas, c, X, limbs=3, **opts):
+    with gwas.GLS(c.n, c.q + 1, c.t, precision=gwas.GWAS_PREC_MIXED, n_limbs=limbs,
+                  **opts) as e:
+        e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
+        return e.solve(X)
+
+
+def check(out, ref, limbs):
+    b, w, s = out
+    rb, rw, rs = ref
+    np.testing.assert_array_equal(s, rs)
+    ok = rs == 0
+    assert np.all(np.isnan(b[~ok])) and np.all(np.isnan(w[~ok]))
+    eb = rel_b(b[ok], rb[ok]) if ok.any() else 0.0
+    ew = wald_err(w[ok], rw[ok]) if ok.any() else 0.0
+    assert eb <= TOL[limbs], f"b error {eb:.3e}"
+    if limbs >= 3:
+        assert ew <= 1e-3, f"Wald error {ew:.3e}"
+    return eb, ew
+
+
+def oracle(c, X):
+    return G.gls(c.phi, c.h, c.sigma2, c.XL, c.Y, X)
+
+
+def test_mixed_small_first(gwas):
+    c = synth.make_cohort(3, 128, n_markers=200)
+    X = c.snps(130)
+    check(run(gwas, c, X, m_blk=256), oracle(c, X), 3)
+
+
+def test_mixed_small_workload_full(gwas):
+    # n = 1000, p = 4, m = 10,000 (the oracle-sized workload), 3 limbs
+    c = synth.make_cohort(0, 1000)
+    X = c.snps(10000)
+    eb, ew = check(run(gwas, c, X, m_blk=4096), oracle(c, X), 3)
+    print(f"n=1000 mixed x3: max rel b err {eb:.2e}, Wald err {ew:.2e}")
+
+
+@pytest.mark.parametrize("limbs", [2, 3, 4])
+@pytest.mark.parametrize("n,m,p,t,mblk", [
+    (64, 1, 4, 1, 64), (65, 127, 4, 1, 128), (130, 129, 3, 2, 128), (1003, 300, 4, 3, 512),
+    (200, 257, 6, 1, 256),
+])
+def test_mixed_ragged(gwas, limbs, n, m, p, t, mblk):
+    c = synth.make_cohort(200 + n + limbs, n, q=p - 1, t=t, n_markers=300)
+    X = c.snps(m)
+    check(run(gwas, c, X, limbs=limbs, m_blk=mblk), oracle(c, X), limbs)
+
+
+def test_mixed_degenerate_and_bad(gwas):
+    c = synth.make_cohort(12, 300, n_markers=400)
+    X = c.snps(70).copy(order="F")
+    X[:, 1] = 1
+    X[:, 2] = 0
+    X[5, 3] = 3
+    X[0, 4] = -1
+    out = run(gwas, c, X, m_blk=128)
+    assert list(out[2][:6]) == [0, 1, 1, 2, 2, 0]
+    check(out, oracle(c, X), 3)
+
+
+def test_mixed_multi_phenotype(gwas):
+    c = synth.make_cohort(52, 900, t=16, n_markers=900)
+    X = c.snps(400)
+    check(run(gwas, c, X, m_blk=512), oracle(c, X), 3)
+
+
+def test_mixed_block_size_and_order_bitwise(gwas):
+    c = synth.make_cohort(22, 600, n_markers=700)
+    X = c.snps(500)
+    b1, _, _ = run(gwas, c, X, m_blk=128)
+    b2, _, _ = run(gwas, c, X, m_blk=4096)
+    np.testing.assert_array_equal(b1, b2)
+    perm = np.random.default_rng(4).permutation(500)
+    b3, _, _ = run(gwas, c, np.asfortranarray(X[:, perm]), m_blk=256)
+    np.testing.assert_array_equal(b3, b1[perm])
+
+
+def test_mixed_full_size_sampled(gwas):
+    """n = 10,000, one block of 16,384 SNPs in the benchmark's launch shape."""
+    import torch
+    n, mb = 10000, 16384
+    c = synth.make_cohort(0, n, device="cuda")
+    Xd = synth.genotypes_torch(5, n, mb, "cuda")
+    e = gwas.GLS(n, 4, 1, m_blk=mb, precision=gwas.GWAS_PREC_MIXED, n_limbs=3)
+    e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
+    bd = torch.empty((mb, 1, 4), dtype=torch.float64, device="cuda")
+    wd = torch.empty((mb, 1), dtype=torch.float64, device="cuda")
+    sd = torch.empty(mb, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    gwas.gwas_solve_block_device(e.ctx, Xd, mb, bd, wd, sd)
+    gwas.gwas_sync(e.ctx)
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([[0, 127, 128, mb - 1], rng.choice(mb, 252, replace=False)]))
+    Xs = np.asfortranarray(Xd[idx].cpu().numpy().T)
+    L = G.factor(c.phi, c.h, c.sigma2)
+    ref = G.gls_hoisted(L, c.XL, c.Y, Xs)
+    out = (bd.cpu().numpy()[idx], wd.cpu().numpy()[idx], sd.cpu().numpy()[idx])
+    eb, ew = check(out, ref, 3)
+    print(f"n=10000 mixed x3: max rel b err {eb:.2e}, Wald err {ew:.2e}")
+    e.close()
