@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--limbs", type=int, default=3)
     ap.add_argument("--pool", type=int, default=4, help="distinct dosage blocks cycled")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision legs (n and n=30000) of an FP64 run")
+    ap.add_argument("--mixed-steps", type=int, default=240)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -116,6 +119,12 @@ def flops_per_snp(n: int, q: int, t: int) -> float:
     """Algorithmic FP64 flops per SNP: the lower-triangular product L^{-1} x_i
     (n(n+1)/2 multiply-adds) plus the fused reductions (2n(q+1+t))."""
     return n * (n + 1) + 2.0 * n * (q + 1 + t)
+
+
+def bf16_flops_per_snp(n: int, q: int, t: int, limbs: int) -> float:
+    """Algorithmic BF16 tensor flops per SNP of the limb path: `limbs` lower-triangular
+    products (n(n+1) flop each) plus the `limbs` x (q+t) linear rows (2n flop each)."""
+    return limbs * (n * (n + 1) + 2.0 * n * (q + t))
 
 
 def measured_peaks() -> dict:
@@ -202,35 +211,28 @@ def workload_config(args) -> dict:
                         f"(block stream of a 1e6-SNP job)",
             "n": args.n, "p": 4, "t": args.t, "m_blk": args.m_blk, "precision": args.precision,
             "parallelism": f"replicas x{args.gpus}",
-            "l2": "inputs larger than L2: L^-1 is 800 MB at n=10k and each dosage block "
-                  f"{args.n * args.m_blk / 1e6:.0f} MB, {args.pool} distinct blocks cycled"}
+            "l2": f"inputs larger than L2: L^-1 is {8 * args.n * args.n / 1e6:.0f} MB and each "
+                  f"dosage block {args.n * args.m_blk / 1e6:.0f} MB, {args.pool} distinct "
+                  "blocks cycled"}
 
 
-def main():
-    args = parse()
-    rank, world, local = dist_env()
-    if args.impl == "reference":
-        return run_reference(args, rank, world)
-
+def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
+    """Factor one cohort, then time `steps` blocks (device-resident) and, if asked,
+    the same blocks end to end from pinned host memory. Returns (result, cohort, pool)."""
     import numpy as np
     import torch
     import synth
     from paper_1304_2272_gb300 import gwas
 
-    torch.cuda.set_device(local)
-    dev = f"cuda:{local}"
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device(dev))
-    n, mb, t, p = args.n, args.m_blk, args.t, 4
-    prec = gwas.GWAS_PREC_FP64 if args.precision == "fp64" else gwas.GWAS_PREC_MIXED
-
+    rank, world, local, dev = env
+    mb, t, p = args.m_blk, args.t, 4
+    prec = gwas.GWAS_PREC_FP64 if precision == "fp64" else gwas.GWAS_PREC_MIXED
     cohort = synth.make_cohort(0, n, t=t, device=dev)
     ctx = gwas.gwas_init(n, p, t, m_blk=mb, device=local, timing=1, precision=prec,
-                         n_limbs=args.limbs)
+                         n_limbs=limbs)
     gwas.gwas_factor(ctx, np.asfortranarray(cohort.phi), True, cohort.h, cohort.sigma2,
                      cohort.XL, cohort.Y)
-    setup_stats = gwas.gwas_get_stats(ctx)
+    setup_ms = gwas.gwas_get_stats(ctx)["factor_ms"]
     pool = [synth.genotypes_torch(1000 * rank + s, n, mb, dev) for s in range(args.pool)]
     b = torch.empty((mb, t, p), dtype=torch.float64, device=dev)
     w = torch.empty((mb, t), dtype=torch.float64, device=dev)
@@ -243,8 +245,15 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(x):
+        if world > 1:
+            tt = torch.tensor([x], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            x = float(tt.item())
+        return x
+
     # ---- device-resident timing (value) --------------------------------------
-    for s in range(args.warmup):
+    for s in range(warmup):
         gwas.gwas_solve_block_device(ctx, pool[s % args.pool], mb, b, w, st)
     gwas.gwas_sync(ctx)
     gwas.gwas_reset_stats(ctx)
@@ -254,67 +263,106 @@ def main():
     barrier()
     clocks.start()
     ev0.record(stream)
-    for s in range(args.steps):
+    for s in range(steps):
         gwas.gwas_solve_block_device(ctx, pool[s % args.pool], mb, b, w, st)
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    el_ms = ev0.elapsed_time(ev1)
+    el_ms = max_over_ranks(ev0.elapsed_time(ev1))
     stats = gwas.gwas_get_stats(ctx)
     status_ok = int((st == 0).sum().item())
-    if world > 1:
-        tt = torch.tensor([el_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        el_ms = float(tt.item())
-    value = world * args.steps * mb / (el_ms / 1e3)
+    value = world * steps * mb / (el_ms / 1e3)
 
     # ---- end to end from pinned host memory (e2e) ------------------------------
-    hpool = [x.cpu().pin_memory() for x in pool[:2]]
-    hb = torch.empty((mb, t, p), dtype=torch.float64).pin_memory()
-    hw = torch.empty((mb, t), dtype=torch.float64).pin_memory()
-    hs = torch.empty(mb, dtype=torch.uint8).pin_memory()
-    for s in range(args.warmup):
-        gwas.gwas_solve_block(ctx, hpool[s % 2], mb, hb, hw, hs)
-    gwas.gwas_sync(ctx)
-    barrier()
-    t0 = time.perf_counter()
-    for s in range(args.steps):
-        gwas.gwas_solve_block(ctx, hpool[s % 2], mb, hb, hw, hs)
-    gwas.gwas_sync(ctx)
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": world * args.steps * mb / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": n * mb, "d2h_bytes_per_step": mb * (t * p * 8 + t * 8 + 1)}
+    e2e = None
+    if want_e2e:
+        hpool = [x.cpu().pin_memory() for x in pool[:2]]
+        hb = torch.empty((mb, t, p), dtype=torch.float64).pin_memory()
+        hw = torch.empty((mb, t), dtype=torch.float64).pin_memory()
+        hs = torch.empty(mb, dtype=torch.uint8).pin_memory()
+        for s in range(warmup):
+            gwas.gwas_solve_block(ctx, hpool[s % 2], mb, hb, hw, hs)
+        gwas.gwas_sync(ctx)
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(steps):
+            gwas.gwas_solve_block(ctx, hpool[s % 2], mb, hb, hw, hs)
+        gwas.gwas_sync(ctx)
+        barrier()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * steps * mb / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": n * mb, "d2h_bytes_per_step": mb * (t * p * 8 + t * 8 + 1)}
 
+    q = p - 1
+    launch_ms = stats["trsm_ms"] / max(1, stats["trsm_launches"])
+    if precision == "fp64":
+        peak, how = fp64_peak_tflops(clk.get("sm_mhz"))
+        achieved = flops_per_snp(n, q, t) * mb / (launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_block_fp64",
+                "launch_ms": launch_ms, "peak_source": how + " (derived, of nominal)"}
+    else:
+        pk = measured_peaks()
+        long_run = el_ms >= 1000.0
+        peak = pk.get("bf16_tflops_sustained" if long_run else "bf16_tflops")
+        src = ("MEASURED_PEAKS.json " + ("bf16_tflops_sustained" if long_run else "bf16_tflops")
+               + " (of measured)") if peak else "fallback 1700 TFLOP/s sustained (of fallback)"
+        peak = peak or 1700.0
+        achieved = bf16_flops_per_snp(n, q, t, limbs) * mb / (launch_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": f"k_block_mixed<{limbs}>",
+                "launch_ms": launch_ms, "peak_source": src,
+                "fp64_equivalent_tflops": flops_per_snp(n, q, t) * value / world / 1e12}
+    res = {"value": value, "ms_per_step": el_ms / steps, "steps": steps, "warmup": warmup,
+           "setup_ms": setup_ms, "roofline": roof, "e2e": e2e,
+           "gpu_launches": int(stats["kernel_launches"]), "clocks": clk,
+           "status_ok_last_block": status_ok}
+    gwas.gwas_finalize(ctx)
+    return res, cohort, pool
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(dev))
+    env = (rank, world, local, dev)
+    res, cohort, pool = measure(args, env, n=args.n, precision=args.precision,
+                                limbs=args.limbs, steps=args.steps, warmup=args.warmup)
+    mixed = []
+    if args.precision == "fp64" and not args.no_mixed:
+        for n_mx, steps_mx in ((args.n, args.mixed_steps), (30000, max(1, args.mixed_steps // 8))):
+            r, _, _ = measure(args, env, n=n_mx, precision="mixed", limbs=args.limbs,
+                              steps=steps_mx, warmup=args.warmup)
+            mixed.append({"n": n_mx, "limbs": args.limbs, "value": r["value"], "unit": UNIT,
+                          "ms_per_step": r["ms_per_step"], "steps": steps_mx,
+                          "setup_ms": r["setup_ms"], "roofline": r["roofline"],
+                          "e2e": r["e2e"], "clocks": r["clocks"],
+                          "gpu_launches": r["gpu_launches"]})
     if rank == 0:
-        q = p - 1
-        launch_ms = stats["trsm_ms"] / max(1, stats["trsm_launches"])
-        if args.precision == "fp64":
-            peak, how = fp64_peak_tflops(clk.get("sm_mhz"))
-            achieved = flops_per_snp(n, q, t) * mb / (launch_ms / 1e3) / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "k_block_fp64",
-                    "launch_ms": launch_ms, "peak_source": how + " (derived, of nominal)"}
-        else:
-            pk = measured_peaks().get("bf16_tflops_sustained") or 1700.0
-            roof = {"bound": "tensor", "achieved": None, "peak": pk, "unit": "TFLOP/s",
-                    "frac": None, "traffic": None}
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
+        line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+                "steps": res["steps"], "warmup": res["warmup"], "ms_per_step": res["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64", "data": "synthetic", "config": workload_config(args),
-                "setup_ms": setup_stats["factor_ms"], "roofline": roof, "e2e": e2e,
-                "gpu_launches": int(stats["kernel_launches"]), "clocks": clk,
-                "status_ok_last_block": status_ok}
+                "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.limbs}+f64",
+                "data": "synthetic", "config": workload_config(args),
+                "setup_ms": res["setup_ms"], "roofline": res["roofline"], "e2e": res["e2e"],
+                "gpu_launches": res["gpu_launches"], "clocks": res["clocks"],
+                "status_ok_last_block": res["status_ok_last_block"]}
+        if mixed:
+            line["mixed"] = mixed
         if not args.no_cpu_baseline:
             Xh = np.asfortranarray(pool[0][:4096].cpu().numpy().T)
             line["cpu_baseline"] = cpu_baseline(cohort, Xh, args.cpu_seconds)
         print(json.dumps(line), flush=True)
-    gwas.gwas_finalize(ctx)
     if world > 1:
         torch.distributed.destroy_process_group()
 
