@@ -63,7 +63,11 @@ typedef struct {
     int precision; /* gwas_precision                                                  */
     int m_blk;     /* largest block of SNPs one solve call may pass (device slot size) */
     int n_limbs;   /* GWAS_PREC_MIXED: BF16 limbs L^{-1} is split into (2..7)          */
-    int tile_cfg;  /* kernel tile configuration id; -1 = library default             */
+    int tile_cfg;  /* -1 = library default; for GWAS_PREC_MIXED, bits 0-3 = pipeline
+                      stages (2..8, 0 = as many as fit), bits 4-11 = MB of BF16 dosages
+                      per L2 group of SNP tiles (0 = 40), bit 12 = force one CTA per
+                      128-SNP tile, bit 13 = force CTA pairs (cta_group::2); by default
+                      the variant with the taller limb tile is used                     */
     int device;    /* CUDA device ordinal                                             */
     int timing;    /* 1 = record CUDA events around each dominant-kernel launch       */
 } gwas_opts;

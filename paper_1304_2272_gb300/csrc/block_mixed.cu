@@ -35,12 +35,19 @@
 namespace gwas {
 namespace mx {
 constexpr int BM = 128;          // SNPs per tile: UMMA M, TMEM lanes
-constexpr int R = 64;            // rows of L^{-1} per tile
 constexpr int BK = 64;           // k per pipeline stage: one 128-byte swizzle row of BF16
 constexpr int BUF = 256;         // TMEM columns per accumulator buffer
 constexpr uint32_t EXTRA = 0xFFFFu;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int SMEM_BUDGET = 200 * 1024;
+
+// Rows of L^{-1} per tile. One UMMA with M = 128 (or 256 across a CTA pair) takes about
+// the same time for any N <= 256, so the tile is made as tall as S limbs allow:
+// N = R * S close to 256 (one CTA: N a multiple of 16; CTA pair: a multiple of 32).
+__host__ __device__ constexpr int rows_single(int S) { return (256 / S) & ~15; }
+__host__ __device__ constexpr int rows_pair(int S) {
+    return ((256 / S) & ~15) * S % 32 == 0 ? ((256 / S) & ~15) : ((256 / S) & ~31);
+}
 }  // namespace mx
 
 struct MixedArgs {
@@ -81,12 +88,58 @@ __device__ __forceinline__ void record_error(const MixedArgs& a, volatile int* a
     atomicCAS(a.err, 0, code);
 }
 
-template <int S>
+// Epilogue of one unit for the SNP held in TMEM lane `tb` (one thread = one SNP):
+// row tiles -> sum over the tile's R rows of xbar^2, exact in 128-bit integers;
+// the linear tile -> the q + t linear reductions.
+template <int S, int R>
+__device__ __forceinline__ void epilogue_unit(const MixedArgs& a, uint32_t tb, int rt,
+                                              int64_t snp) {
+    using namespace tc;
+    const int shift0 = 8 + 9 * (S - 1);
+    if (rt != (int)mx::EXTRA) {
+        unsigned __int128 acc = 0;
+#pragma unroll 1
+        for (int i0 = 0; i0 < R; i0 += 16) {
+            uint32_t v[S][16];
+#pragma unroll
+            for (int l = 0; l < S; ++l) tmem_ld16(tb + (uint32_t)(l * R + i0), v[l]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                long long T = 0;
+#pragma unroll
+                for (int l = 0; l < S; ++l)
+                    T = T * 512 + (long long)__float2int_rn(__uint_as_float(v[l][i]));
+                const unsigned long long uT = (unsigned long long)(T < 0 ? -T : T);
+                acc += (unsigned __int128)uT * uT;
+            }
+        }
+        const double hi = (double)(unsigned long long)(acc >> 64);
+        const double lo = (double)(unsigned long long)acc;
+        const double val = ldexp(fma(hi, 18446744073709551616.0, lo), 2 * (a.E_w[rt] - shift0));
+        if (snp < a.mb) a.sq_part[(int64_t)rt * a.ldp + snp] = val;
+    } else {
+#pragma unroll 1
+        for (int j = 0; j < a.R_e; ++j) {
+            long long T = 0;
+#pragma unroll
+            for (int l = 0; l < S; ++l) {
+                uint32_t x;
+                tmem_ld1(tb + (uint32_t)(l * a.R_e + j), x);
+                tmem_wait_ld();
+                T = T * 512 + (long long)__float2int_rn(__uint_as_float(x));
+            }
+            if (snp < a.mb) a.lin[(int64_t)j * a.ldp + snp] = ldexp((double)T, a.E_e[j] - shift0);
+        }
+    }
+}
+
+template <int S, int R>
 __global__ void __launch_bounds__(256, 1)
 k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
               const __grid_constant__ CUtensorMap tmE, const MixedArgs a) {
     using namespace tc;
-    constexpr int N = mx::R * S;
+    constexpr int N = R * S;
     constexpr uint32_t A_BYTES = mx::BM * mx::BK * 2;
     const int NB = N > a.N_e ? N : a.N_e;
     const uint32_t B_BYTES = (uint32_t)NB * mx::BK * 2;
@@ -148,7 +201,7 @@ k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
             int rt, ct;
             decode_unit(a, u, rt, ct);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? a.n_kc_full : min(rt + 1, a.n_kc_full);
+            const int nk = ex ? a.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.n_kc_full);
             const int ybase = ex ? a.n_rt * N : rt * N;
             const uint32_t bytes = A_BYTES + (uint32_t)(ex ? a.N_e : N) * mx::BK * 2;
             for (int kc = 0; kc < nk; ++kc) {
@@ -185,7 +238,7 @@ k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
             int rt, ct;
             decode_unit(a, u, rt, ct);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? a.n_kc_full : min(rt + 1, a.n_kc_full);
+            const int nk = ex ? a.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.n_kc_full);
             if (!mbar_wait(&tempty[abuf], aphase ^ 1, mx::WAIT_NS)) {
                 record_error(a, abort_flag, 2);
                 break;
@@ -225,58 +278,18 @@ k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         const int qd = warp & 3;
         int abuf = 0;
         uint32_t aphase = 0;
-        const int shift0 = 8 + 9 * (S - 1);
         for (int r = 0; r < rounds && !*abort_flag; ++r) {
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
             int rt, ct;
             decode_unit(a, u, rt, ct);
-            const bool ex = (rt == (int)mx::EXTRA);
             if (!mbar_wait(&tfull[abuf], aphase, mx::WAIT_NS)) {
                 record_error(a, abort_flag, 4);
                 break;
             }
             fence_after_sync();
             const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
-            const int64_t snp = (int64_t)ct * mx::BM + qd * 32 + lane;
-            if (!ex) {
-                unsigned __int128 acc = 0;
-#pragma unroll 1
-                for (int i0 = 0; i0 < mx::R; i0 += 16) {
-                    uint32_t v[S][16];
-#pragma unroll
-                    for (int l = 0; l < S; ++l) tmem_ld16(tb + (uint32_t)(l * mx::R + i0), v[l]);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        long long T = 0;
-#pragma unroll
-                        for (int l = 0; l < S; ++l)
-                            T = T * 512 + (long long)__float2int_rn(__uint_as_float(v[l][i]));
-                        const unsigned long long uT = (unsigned long long)(T < 0 ? -T : T);
-                        acc += (unsigned __int128)uT * uT;
-                    }
-                }
-                const double hi = (double)(unsigned long long)(acc >> 64);
-                const double lo = (double)(unsigned long long)acc;
-                const double val = ldexp(fma(hi, 18446744073709551616.0, lo),
-                                         2 * (a.E_w[rt] - shift0));
-                if (snp < a.mb) a.sq_part[(int64_t)rt * a.ldp + snp] = val;
-            } else {
-#pragma unroll 1
-                for (int j = 0; j < a.R_e; ++j) {
-                    long long T = 0;
-#pragma unroll
-                    for (int l = 0; l < S; ++l) {
-                        uint32_t x;
-                        tmem_ld1(tb + (uint32_t)(l * a.R_e + j), x);
-                        tmem_wait_ld();
-                        T = T * 512 + (long long)__float2int_rn(__uint_as_float(x));
-                    }
-                    if (snp < a.mb)
-                        a.lin[(int64_t)j * a.ldp + snp] = ldexp((double)T, a.E_e[j] - shift0);
-                }
-            }
+            epilogue_unit<S, R>(a, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[abuf]);
@@ -289,6 +302,195 @@ k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         __syncwarp();
         fence_after_sync();
         tmem_dealloc(tmem_base, 2 * mx::BUF);
+    }
+}
+
+
+// ----------------------------------------------------------------------------
+// CTA-pair variant (cta_group::2): a cluster of 2 CTAs on one TPC computes a
+// 256-SNP x N tile with M = 256 UMMAs. Each CTA loads its own 128 SNPs (A) and half of
+// the limb tile (N/2 rows of B); the UMMA issued by the even CTA reads both halves, so
+// every SM moves 28 KB instead of 40 KB per 64-k stage (3 limbs) and fits 7 stages.
+// The even CTA's full barriers collect both CTAs' TMA bytes; its MMA commits arrive
+// on the empty / accumulator barriers of both CTAs; both CTAs' epilogues release an
+// accumulator buffer on the even CTA's barrier (8 warp arrivals).
+// In this kernel a.n_ct counts pairs of 128-SNP tiles.
+// ----------------------------------------------------------------------------
+template <int S, int R>
+__global__ void __launch_bounds__(256, 1)
+k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
+               const __grid_constant__ CUtensorMap tmE, const MixedArgs a) {
+    using namespace tc;
+    constexpr int N = R * S;
+    constexpr int NH = N / 2;
+    constexpr uint32_t A_BYTES = mx::BM * mx::BK * 2;
+    const int NeH = a.N_e / 2;
+    const int NBH = NH > NeH ? NH : NeH;
+    const uint32_t B_BYTES = (uint32_t)NBH * mx::BK * 2;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + a.stages * A_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + a.stages * B_BYTES);
+    uint64_t* empty = full + a.stages;
+    uint64_t* tfull = empty + a.stages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* done = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = (rank == 0);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&tfull[s], 1);
+            mbar_init(&tempty[s], 8);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc2(tmem_slot, 2 * mx::BUF);
+        tmem_relinquish2();
+    }
+    if (warp == 1 && lane == 0) {
+        prefetch_tmap(&tmX);
+        prefetch_tmap(&tmW);
+        prefetch_tmap(&tmE);
+    }
+    fence_before_sync();
+    __syncthreads();
+    cluster_sync();  // both CTAs' barriers initialised before any cross-CTA signal
+    fence_after_sync();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const int P = gridDim.x / 2, me = blockIdx.x / 2;
+    const int rounds = (a.n_units + P - 1) / P;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer (both CTAs) ----------------
+        int stage = 0;
+        uint32_t phase = 0;
+        uint32_t issued_parity[16];
+        bool issued[16];
+        for (int s = 0; s < 16; ++s) issued[s] = false;
+        for (int r = 0; r < rounds && !*abort_flag; ++r) {
+            const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
+            if (u >= a.n_units) continue;
+            int rt, ctp;
+            decode_unit(a, u, rt, ctp);
+            const bool ex = (rt == (int)mx::EXTRA);
+            const int nk = ex ? a.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.n_kc_full);
+            const int half = ex ? NeH : NH;
+            const int ybase = (ex ? a.n_rt * N : rt * N) + (int)rank * half;
+            const int ct = 2 * ctp + (int)rank;
+            const uint32_t pair_bytes = 2u * (A_BYTES + (uint32_t)half * mx::BK * 2);
+            for (int kc = 0; kc < nk; ++kc) {
+                if (!mbar_wait(&empty[stage], phase ^ 1, mx::WAIT_NS)) {
+                    record_error(a, abort_flag, 11);
+                    break;
+                }
+                if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
+                const uint32_t fbar = mapa_shared(smem_u32(&full[stage]), 0);
+                tma_load_2d_pair(sA + stage * A_BYTES, &tmX, kc * mx::BK, ct * mx::BM, fbar);
+                tma_load_2d_pair(sB + stage * B_BYTES, ex ? &tmE : &tmW, kc * mx::BK, ybase, fbar);
+                issued[stage] = true;
+                issued_parity[stage] = phase;
+                if (++stage == a.stages) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+            }
+        }
+        if (*abort_flag && leader) {
+            for (int s = 0; s < a.stages && s < 16; ++s)
+                if (issued[s]) mbar_wait(&full[s], issued_parity[s], 10000000ull);
+        }
+    } else if (warp == 1 && lane == 0 && leader) {
+        // ---------------- MMA issuer (even CTA) ----------------
+        int stage = 0;
+        uint32_t phase = 0;
+        int abuf = 0;
+        uint32_t aphase = 0;
+        for (int r = 0; r < rounds && !*abort_flag; ++r) {
+            const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
+            if (u >= a.n_units) continue;
+            int rt, ctp;
+            decode_unit(a, u, rt, ctp);
+            const bool ex = (rt == (int)mx::EXTRA);
+            const int nk = ex ? a.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.n_kc_full);
+            if (!mbar_wait(&tempty[abuf], aphase ^ 1, mx::WAIT_NS)) {
+                record_error(a, abort_flag, 12);
+                break;
+            }
+            fence_after_sync();
+            const uint32_t d = tmem_base + (uint32_t)(abuf * mx::BUF);
+            const uint32_t idesc = idesc_bf16_f32(2 * mx::BM, ex ? a.N_e : N);
+            bool ok = true;
+            for (int kc = 0; kc < nk; ++kc) {
+                if (!mbar_wait(&full[stage], phase, mx::WAIT_NS)) {
+                    record_error(a, abort_flag, 13);
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
+                const uint64_t ad = smem_desc_sw128(smem_u32(sA + stage * A_BYTES));
+                const uint64_t bd = smem_desc_sw128(smem_u32(sB + stage * B_BYTES));
+#pragma unroll
+                for (int kk = 0; kk < mx::BK / 16; ++kk)
+                    umma_bf16_pair(d, ad + 2 * kk, bd + 2 * kk, idesc, (kc | kk) != 0);
+                umma_commit_pair(&empty[stage]);
+                if (++stage == a.stages) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+            }
+            if (!ok) break;
+            umma_commit_pair(&tfull[abuf]);
+            abuf ^= 1;
+            if (abuf == 0) aphase ^= 1;
+        }
+        umma_commit_pair(done);
+        mbar_wait(done, 0, mx::WAIT_NS);
+    } else if (warp >= 4) {
+        // ---------------- epilogue (both CTAs): one SNP per thread ----------------
+        const int qd = warp & 3;
+        int abuf = 0;
+        uint32_t aphase = 0;
+        for (int r = 0; r < rounds && !*abort_flag; ++r) {
+            const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
+            if (u >= a.n_units) continue;
+            int rt, ctp;
+            decode_unit(a, u, rt, ctp);
+            if (!mbar_wait(&tfull[abuf], aphase, mx::WAIT_NS)) {
+                record_error(a, abort_flag, 14);
+                break;
+            }
+            fence_after_sync();
+            const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
+            const int ct = 2 * ctp + (int)rank;
+            epilogue_unit<S, R>(a, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[abuf]), 0));
+            abuf ^= 1;
+            if (abuf == 0) aphase ^= 1;
+        }
+    }
+    __syncthreads();
+    cluster_sync();  // no CTA leaves while its peer may still signal it or use its TMEM
+    if (warp == 0) {
+        __syncwarp();
+        fence_after_sync();
+        tmem_dealloc2(tmem_base, 2 * mx::BUF);
     }
 }
 
@@ -327,17 +529,15 @@ k_geno_bf16(const int8_t* __restrict__ X, int64_t ldx, int64_t n, int64_t mb,
 // Exponents and limb split of L^{-1} (row tiles) and of Z (linear rows).
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-k_absmax_w(const double* __restrict__ W, int64_t ldw, int64_t n, unsigned long long* bits) {
-    // grid: x = k chunks of 256, y = row tile
+k_absmax_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, unsigned long long* bits) {
+    // grid: x = k chunks of 256, y = row tile of R rows; elements (i, k) of the tile's
+    // lower part, i fastest (coalesced along the column-major rows)
     const int rt = blockIdx.y;
-    const int64_t r = (int64_t)rt * 64 + (threadIdx.x % 64);
+    const int64_t r0 = (int64_t)rt * R, k0 = (int64_t)blockIdx.x * 256;
     double m = 0.0;
-    if (r < n) {
-        const int64_t k_end = min64(r + 1, n);
-        for (int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x / 64; k < k_end &&
-                                                                      k < (int64_t)(blockIdx.x + 1) * 256;
-             k += 4)
-            m = fmax(m, fabs(W[r + k * ldw]));
+    for (int e = threadIdx.x; e < R * 256; e += blockDim.x) {
+        const int64_t r = r0 + e % R, k = k0 + e / R;
+        if (r < n && k <= r) m = fmax(m, fabs(W[r + k * ldw]));
     }
     __shared__ double red[256];
     red[threadIdx.x] = m;
@@ -391,10 +591,11 @@ __device__ __forceinline__ void split_limbs(double w, int E, uint16_t (&out)[S])
     }
 }
 
-// Lower triangle of W (column-major) -> limb rows rt*N + l*64 + i of WL (k contiguous).
+// Lower triangle of W (column-major) -> limb rows rt*R*S + l*R + i of WL (k contiguous),
+// R rows of L^{-1} per tile.
 template <int S>
 __global__ void __launch_bounds__(256)
-k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, const int* __restrict__ E_w,
+k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, const int* __restrict__ E_w,
           uint16_t* __restrict__ WL, int64_t n_pad) {
     __shared__ double tile[32][33];
     const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
@@ -405,15 +606,15 @@ k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, const int* __res
         tile[j][tx] = (r < n && k < n && k <= r) ? W[r + k * ldw] : 0.0;
     }
     __syncthreads();
-    constexpr int N = 64 * S;
+    const int64_t N = (int64_t)R * S;
     for (int j = ty; j < 32; j += 8) {
         const int64_t r = r0 + j, k = k0 + tx;
         if (r >= n || k >= n || k > r) continue;
-        const int rt = (int)(r / 64), i = (int)(r % 64);
+        const int64_t rt = r / R, i = r % R;
         uint16_t limbs[S];
         split_limbs<S>(tile[tx][j], E_w[rt], limbs);
 #pragma unroll
-        for (int l = 0; l < S; ++l) WL[((int64_t)rt * N + l * 64 + i) * n_pad + k] = limbs[l];
+        for (int l = 0; l < S; ++l) WL[(rt * N + (int64_t)l * R + i) * n_pad + k] = limbs[l];
     }
 }
 
@@ -464,33 +665,40 @@ bool tmap_bf16_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t out
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int S>
-int stage_count(int N_e) {
-    const int N = 64 * S;
-    const int NB = std::max(N, N_e);
+// Pipeline stages that fit the shared-memory budget for a tile of N = R*S limb rows
+// (a CTA pair holds half of the limb tile per CTA).
+int stage_count(int N, int N_e, bool pair) {
+    const int NB = pair ? std::max(N, N_e) / 2 : std::max(N, N_e);
     const int per = mx::BM * mx::BK * 2 + NB * mx::BK * 2;
     return std::min(8, mx::SMEM_BUDGET / per);
 }
 
-template <int S>
-size_t smem_bytes(int N_e, int stages) {
-    const int NB = std::max(64 * S, N_e);
+size_t smem_bytes(int N, int N_e, bool pair, int stages) {
+    const int NB = pair ? std::max(N, N_e) / 2 : std::max(N, N_e);
     return (size_t)stages * (mx::BM * mx::BK * 2 + NB * mx::BK * 2) + 1024 + 256;
 }
 
 }  // namespace
 
-int mixed_linear_n(int S, int R_e) { return (int)round_up((int64_t)S * R_e, 16); }
+// UMMA N of the linear tile: a multiple of 32 (so each CTA of a pair holds whole
+// 8-row swizzle groups of it) and at least 32.
+int mixed_linear_n(int S, int R_e) { return (int)std::max<int64_t>(32, round_up((int64_t)S * R_e, 32)); }
 
 cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk) {
     m.S = S;
     m.n = n;
-    m.n_rt = (int)ceil_div(n, 64);
+    // kernel variant and tile height: the taller UMMA N wins; CTA pairs on a tie
+    const int rs = mx::rows_single(S), rp = mx::rows_pair(S);
+    if (m.cfg_single_cta) m.pair = false;
+    else if (m.cfg_pair) m.pair = true;
+    else m.pair = (rp >= rs);
+    m.R = m.pair ? rp : rs;
+    m.n_rt = (int)ceil_div(n, m.R);
     m.n_pad = round_up(n, 64);
     m.R_e = R_e;
     m.N_e = mixed_linear_n(S, R_e);
-    m.rows_total = (int64_t)m.n_rt * 64 * S + m.N_e;
-    m.mb_pad_max = round_up(m_blk, mx::BM);
+    m.rows_total = (int64_t)m.n_rt * m.R * S + m.N_e;
+    m.mb_pad_max = round_up(m_blk, 2 * mx::BM);
     m.ldp = round_up(m_blk, 32);
     return cudaSuccess;
 }
@@ -501,23 +709,24 @@ cudaError_t mixed_prepare(MixedDev& m, const double* W, int64_t ldw, const doubl
     const int64_t n = m.n;
     if ((e = cudaMemsetAsync(m.WL, 0, (size_t)m.rows_total * m.n_pad * 2, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(m.bits, 0, (size_t)(m.n_rt + m.R_e) * 8, s)) != cudaSuccess) return e;
-    k_absmax_w<<<dim3((unsigned)ceil_div(n, 256), (unsigned)m.n_rt), 256, 0, s>>>(W, ldw, n, m.bits);
+    k_absmax_w<<<dim3((unsigned)ceil_div(n, 256), (unsigned)m.n_rt), 256, 0, s>>>(W, ldw, n, m.R,
+                                                                                 m.bits);
     k_absmax_z<<<dim3(64, (unsigned)m.R_e), 256, 0, s>>>(Z, n, m.bits + m.n_rt);
     k_exponents<<<(unsigned)ceil_div(m.n_rt + m.R_e, 128), 128, 0, s>>>(m.bits, m.n_rt + m.R_e, m.E);
-    const dim3 gw((unsigned)ceil_div(n, 32), (unsigned)ceil_div((int64_t)m.n_rt * 64, 32));
+    const dim3 gw((unsigned)ceil_div(n, 32), (unsigned)ceil_div((int64_t)m.n_rt * m.R, 32));
     const dim3 gz(64, (unsigned)m.R_e);
-    const int64_t zbase = (int64_t)m.n_rt * 64 * m.S;
+    const int64_t zbase = (int64_t)m.n_rt * m.R * m.S;
     switch (m.S) {
         case 2:
-            k_split_w<2><<<gw, 256, 0, s>>>(W, ldw, n, m.E, m.WL, m.n_pad);
+            k_split_w<2><<<gw, 256, 0, s>>>(W, ldw, n, m.R, m.E, m.WL, m.n_pad);
             k_split_z<2><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
             break;
         case 3:
-            k_split_w<3><<<gw, 256, 0, s>>>(W, ldw, n, m.E, m.WL, m.n_pad);
+            k_split_w<3><<<gw, 256, 0, s>>>(W, ldw, n, m.R, m.E, m.WL, m.n_pad);
             k_split_z<3><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
             break;
         case 4:
-            k_split_w<4><<<gw, 256, 0, s>>>(W, ldw, n, m.E, m.WL, m.n_pad);
+            k_split_w<4><<<gw, 256, 0, s>>>(W, ldw, n, m.R, m.E, m.WL, m.n_pad);
             k_split_z<4><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
             break;
         default:
@@ -526,26 +735,31 @@ cudaError_t mixed_prepare(MixedDev& m, const double* W, int64_t ldw, const doubl
     if (launches) *launches += 6;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // tensor maps over the fixed buffers
-    const int N = 64 * m.S;
+    const int N = m.R * m.S;
     if (!tmap_bf16_2d(&m.tmX, m.Xb, (uint64_t)m.n_pad, (uint64_t)m.mb_pad_max, mx::BK, mx::BM) ||
         !tmap_bf16_2d(&m.tmW, m.WL, (uint64_t)m.n_pad, (uint64_t)m.rows_total, mx::BK, (uint32_t)N) ||
         !tmap_bf16_2d(&m.tmE, m.WL, (uint64_t)m.n_pad, (uint64_t)m.rows_total, mx::BK,
-                      (uint32_t)m.N_e))
+                      (uint32_t)m.N_e) ||
+        !tmap_bf16_2d(&m.tmWh, m.WL, (uint64_t)m.n_pad, (uint64_t)m.rows_total, mx::BK,
+                      (uint32_t)(N / 2)) ||
+        !tmap_bf16_2d(&m.tmEh, m.WL, (uint64_t)m.n_pad, (uint64_t)m.rows_total, mx::BK,
+                      (uint32_t)(m.N_e / 2)))
         return cudaErrorInvalidValue;
     return cudaSuccess;
 }
 
-template <int S>
-static cudaError_t launch_mixed_t(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
+static MixedArgs make_args(const MixedDev& m, int64_t mb, bool pair) {
     MixedArgs a;
     a.n_rt = m.n_rt;
-    a.n_ct = (int)ceil_div(mb, mx::BM);
+    a.n_ct = (int)ceil_div(mb, pair ? 2 * mx::BM : mx::BM);  // SNP tiles, or pairs of them
     a.n_kc_full = (int)(m.n_pad / mx::BK);
     a.R_e = m.R_e;
     a.N_e = m.N_e;
-    a.stages = stage_count<S>(m.N_e);
-    const int64_t per_tile = (int64_t)mx::BM * m.n_pad * 2;  // BF16 dosages of one SNP tile
-    a.group = (int)std::max<int64_t>(1, std::min<int64_t>(a.n_ct, (40ll << 20) / per_tile));
+    a.stages = stage_count(m.R * m.S, m.N_e, pair);
+    if (m.cfg_stages >= 2) a.stages = std::min(a.stages, m.cfg_stages);
+    const int64_t per_tile = (pair ? 2ll : 1ll) * mx::BM * m.n_pad * 2;  // BF16 dosages
+    const int64_t budget = (int64_t)std::max(1, m.cfg_group_mb) << 20;
+    a.group = (int)std::max<int64_t>(1, std::min<int64_t>(a.n_ct, budget / per_tile));
     a.n_units = a.n_ct * (a.n_rt + 1);
     a.mb = mb;
     a.ldp = m.ldp;
@@ -554,12 +768,50 @@ static cudaError_t launch_mixed_t(const MixedDev& m, int64_t mb, int num_sms, cu
     a.sq_part = m.sq_part;
     a.lin = m.lin;
     a.err = m.err;
-    const size_t smem = smem_bytes<S>(m.N_e, a.stages);
-    cudaError_t e = cudaFuncSetAttribute(k_block_mixed<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    return a;
+}
+
+template <int S, int R>
+static cudaError_t launch_single_t(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
+    const MixedArgs a = make_args(m, mb, false);
+    const size_t smem = smem_bytes(R * S, m.N_e, false, a.stages);
+    cudaError_t e = cudaFuncSetAttribute(k_block_mixed<S, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(num_sms, a.n_units));
-    k_block_mixed<S><<<grid, 256, smem, s>>>(m.tmX, m.tmW, m.tmE, a);
+    k_block_mixed<S, R><<<grid, 256, smem, s>>>(m.tmX, m.tmW, m.tmE, a);
+    return cudaGetLastError();
+}
+
+template <int S, int R>
+static cudaError_t launch_pair_t(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
+    const MixedArgs a = make_args(m, mb, true);
+    const size_t smem = smem_bytes(R * S, m.N_e, true, a.stages);
+    cudaError_t e = cudaFuncSetAttribute(k_block_mixed2<S, R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // as many CTA pairs as can be resident at once (persistent), at most one per unit
+    cfg.gridDim = dim3((unsigned)(2 * std::max(1, num_sms / 2)), 1, 1);
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, k_block_mixed2<S, R>, &cfg);
+    if (e != cudaSuccess) return e;
+    if (clusters < 1) return cudaErrorLaunchOutOfResources;
+    clusters = std::min(clusters, std::max(1, num_sms / 2));
+    clusters = std::min(clusters, a.n_units);
+    cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+    e = cudaLaunchKernelEx(&cfg, k_block_mixed2<S, R>, m.tmX, m.tmWh, m.tmEh, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -572,12 +824,17 @@ cudaError_t launch_geno_bf16(const MixedDev& m, const int8_t* X, int64_t ldx, in
 
 cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
     if (mb < 1 || mb > m.mb_pad_max) return cudaErrorInvalidValue;
-    switch (m.S) {
-        case 2: return launch_mixed_t<2>(m, mb, num_sms, s);
-        case 3: return launch_mixed_t<3>(m, mb, num_sms, s);
-        case 4: return launch_mixed_t<4>(m, mb, num_sms, s);
-        default: return cudaErrorInvalidValue;
+    using namespace mx;
+    if (m.pair) {
+        if (m.S == 2 && m.R == rows_pair(2)) return launch_pair_t<2, rows_pair(2)>(m, mb, num_sms, s);
+        if (m.S == 3 && m.R == rows_pair(3)) return launch_pair_t<3, rows_pair(3)>(m, mb, num_sms, s);
+        if (m.S == 4 && m.R == rows_pair(4)) return launch_pair_t<4, rows_pair(4)>(m, mb, num_sms, s);
+    } else {
+        if (m.S == 2 && m.R == rows_single(2)) return launch_single_t<2, rows_single(2)>(m, mb, num_sms, s);
+        if (m.S == 3 && m.R == rows_single(3)) return launch_single_t<3, rows_single(3)>(m, mb, num_sms, s);
+        if (m.S == 4 && m.R == rows_single(4)) return launch_single_t<4, rows_single(4)>(m, mb, num_sms, s);
     }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace gwas

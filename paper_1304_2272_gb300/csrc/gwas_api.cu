@@ -247,6 +247,13 @@ gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx**
         CKI(dmalloc(&c->part, (size_t)nt * nred * c->ldp));
     } else {
         MixedDev& m = c->mx;
+        if (o.tile_cfg >= 0) {
+            m.cfg_stages = o.tile_cfg & 0xF;
+            const int g = (o.tile_cfg >> 4) & 0xFF;
+            if (g > 0) m.cfg_group_mb = g;
+            m.cfg_single_cta = ((o.tile_cfg >> 12) & 1) != 0;
+            m.cfg_pair = ((o.tile_cfg >> 13) & 1) != 0;
+        }
         mixed_layout(m, n, o.n_limbs, c->q + t, o.m_blk);
         CKI(dmalloc(&c->Z, (size_t)n * (c->q + t)));
         CKI(dmalloc(&m.WL, (size_t)m.rows_total * m.n_pad));

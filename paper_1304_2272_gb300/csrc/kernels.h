@@ -78,11 +78,13 @@ cudaError_t launch_snp_solve(const CohortDev& c, const double* part, int64_t ldp
 struct MixedDev {
     int S = 3;                  // BF16 limbs per element of L^{-1} and Z
     int64_t n = 0;
-    int n_rt = 0;               // 64-row tiles of L^{-1}
+    int R = 64;                 // rows of L^{-1} per tile (UMMA N = R * S)
+    bool pair = true;           // CTA-pair kernel (cta_group::2) instead of one CTA per tile
+    int n_rt = 0;               // R-row tiles of L^{-1}
     int64_t n_pad = 0;          // n rounded up to 64 (k extent of every BF16 row)
     int R_e = 0;                // linear rows q + t (Z = L^{-T} [Xbar_L | Ybar])
     int N_e = 0;                // UMMA N of the linear tile (S * R_e rounded up to 16)
-    int64_t rows_total = 0;     // rows of WL: n_rt * 64 * S + N_e
+    int64_t rows_total = 0;     // rows of WL: n_rt * R * S + N_e
     int64_t mb_pad_max = 0;     // rows of Xb
     int64_t ldp = 0;            // leading dimension of sq_part / lin
     uint16_t* WL = nullptr;     // BF16 limbs, [rows_total][n_pad], k contiguous
@@ -92,7 +94,12 @@ struct MixedDev {
     double* sq_part = nullptr;  // [n_rt][ldp] row-tile partials of S_BRi
     double* lin = nullptr;      // [R_e][ldp] S_BLi (q rows) then bbar_Bi (t rows)
     int* err = nullptr;         // kernel wait-timeout code (0 = none)
+    int cfg_stages = 0;         // pipeline stages (0 = as many as fit)
+    int cfg_group_mb = 40;      // MB of BF16 dosages per L2 group of SNP tiles
+    bool cfg_single_cta = false;  // force one CTA per 128-SNP tile
+    bool cfg_pair = false;        // force CTA pairs
     CUtensorMap tmX, tmW, tmE;  // TMA maps of Xb, WL (row tiles), WL (linear tile)
+    CUtensorMap tmWh, tmEh;     // the same WL maps with half-height boxes (CTA pairs)
 };
 
 int mixed_linear_n(int S, int R_e);

@@ -15,6 +15,8 @@ from oracle import gls as G
 pytestmark = pytest.mark.gpu
 
 TOL = {2: 1e-4, 3: 1e-6, 4: 1e-6}
+# tile_cfg bits: 12 forces one CTA per 128-SNP tile, 13 forces CTA pairs (cta_group::2)
+VARIANTS = {"default": -1, "single": 1 << 12, "pair": 1 << 13}
 
 
 def rel_b(b, ref):
@@ -58,29 +60,44 @@ def oracle(c, X):
     return G.gls(c.phi, c.h, c.sigma2, c.XL, c.Y, X)
 
 
-def test_mixed_small_first(gwas):
+@pytest.mark.parametrize("variant", ["single", "pair", "default"])
+def test_mixed_small_first(gwas, variant):
     c = synth.make_cohort(3, 128, n_markers=200)
     X = c.snps(130)
-    check(run(gwas, c, X, m_blk=256), oracle(c, X), 3)
+    check(run(gwas, c, X, m_blk=256, tile_cfg=VARIANTS[variant]), oracle(c, X), 3)
 
 
-def test_mixed_small_workload_full(gwas):
+@pytest.mark.parametrize("variant", ["default", "pair", "single"])
+def test_mixed_small_workload_full(gwas, variant):
     # n = 1000, p = 4, m = 10,000 (the oracle-sized workload), 3 limbs
     c = synth.make_cohort(0, 1000)
     X = c.snps(10000)
-    eb, ew = check(run(gwas, c, X, m_blk=4096), oracle(c, X), 3)
-    print(f"n=1000 mixed x3: max rel b err {eb:.2e}, Wald err {ew:.2e}")
+    eb, ew = check(run(gwas, c, X, m_blk=4096, tile_cfg=VARIANTS[variant]), oracle(c, X), 3)
+    print(f"n=1000 mixed x3 ({variant}): max rel b err {eb:.2e}, Wald err {ew:.2e}")
 
 
+@pytest.mark.parametrize("limbs", [2, 4])
+def test_pair_and_single_cta_bitwise(gwas, limbs):
+    # with 2 or 4 limbs both variants use the same tile height, hence the same limbs
+    c = synth.make_cohort(23, 700, n_markers=700)
+    X = c.snps(777)
+    b1, w1, _ = run(gwas, c, X, limbs=limbs, m_blk=1024, tile_cfg=VARIANTS["pair"])
+    b2, w2, _ = run(gwas, c, X, limbs=limbs, m_blk=1024, tile_cfg=VARIANTS["single"])
+    np.testing.assert_array_equal(b1, b2)
+    np.testing.assert_array_equal(w1, w2)
+
+
+@pytest.mark.parametrize("variant", ["pair", "single"])
 @pytest.mark.parametrize("limbs", [2, 3, 4])
 @pytest.mark.parametrize("n,m,p,t,mblk", [
     (64, 1, 4, 1, 64), (65, 127, 4, 1, 128), (130, 129, 3, 2, 128), (1003, 300, 4, 3, 512),
     (200, 257, 6, 1, 256),
 ])
-def test_mixed_ragged(gwas, limbs, n, m, p, t, mblk):
+def test_mixed_ragged(gwas, variant, limbs, n, m, p, t, mblk):
     c = synth.make_cohort(200 + n + limbs, n, q=p - 1, t=t, n_markers=300)
     X = c.snps(m)
-    check(run(gwas, c, X, limbs=limbs, m_blk=mblk), oracle(c, X), limbs)
+    check(run(gwas, c, X, limbs=limbs, m_blk=mblk, tile_cfg=VARIANTS[variant]), oracle(c, X),
+          limbs)
 
 
 def test_mixed_degenerate_and_bad(gwas):
