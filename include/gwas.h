@@ -39,7 +39,8 @@
 extern "C" {
 #endif
 
-typedef struct gwas_ctx gwas_ctx; /* opaque */
+typedef struct gwas_ctx gwas_ctx;     /* opaque: one cohort                      */
+typedef struct gwas_batch gwas_batch; /* opaque: many cohorts solved together    */
 
 typedef enum {
     GWAS_OK = 0,
@@ -70,6 +71,8 @@ typedef struct {
                       the variant with the taller limb tile is used                     */
     int device;    /* CUDA device ordinal                                             */
     int timing;    /* 1 = record CUDA events around each dominant-kernel launch       */
+    int use_graph; /* batches: 1 = capture the batched solve in a CUDA graph and
+                      replay it while its pointers and sizes stay the same            */
 } gwas_opts;
 
 /* Per-context counters (gwas_get_stats). Times are CUDA-event milliseconds. */
@@ -85,7 +88,8 @@ typedef struct {
     int64_t factor_launches;   /* kernels launched by the last gwas_factor            */
 } gwas_stats;
 
-/* Fill *opts with defaults: FP64, m_blk 16384, 3 limbs, default tiles, device 0. */
+/* Fill *opts with defaults: FP64, m_blk 16384, 3 limbs, default tiles, device 0,
+ * no timing events, CUDA graphs on. */
 void gwas_default_opts(gwas_opts* opts);
 
 /*
@@ -167,6 +171,54 @@ gwas_status gwas_reset_stats(gwas_ctx* ctx);
 
 /* The context's compute stream, as a cudaStream_t cast to void*. */
 void* gwas_stream(const gwas_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------
+ * Batches of cohorts. Many independent cohorts (each its own n, M, X_L and Y with t
+ * phenotype columns; the same p, t and options for all) are solved together: every
+ * cohort is factored once (as gwas_factor), and one batched solve runs ONE grouped
+ * launch of the block kernel over all cohorts' work units, so cohorts of uneven n
+ * share the GPU without a launch per cohort. With opts.use_graph the launches of a
+ * batched solve are captured once into a CUDA graph and replayed while the pointers
+ * and sizes passed in stay the same. This is Eq. (1) for each (cohort, SNP, phenotype);
+ * several phenotypes sharing one M are the one-M case of the multi-trait problem in
+ * the paper's outlook (Section 5).
+ * --------------------------------------------------------------------------------- */
+
+/* Create a batch of n_cohorts contexts with sizes n[c] (host array). opts->m_blk is the
+ * largest number of SNPs per cohort in one batched solve. GWAS_PREC_MIXED batches use
+ * the one-CTA-per-tile kernel variant. Errors as gwas_init. */
+gwas_status gwas_batch_init(int n_cohorts, const int64_t* n, int p, int t, const gwas_opts* opts,
+                            gwas_batch** out);
+
+/* gwas_factor for cohort `cohort` of the batch (same arguments and errors). */
+gwas_status gwas_batch_factor(gwas_batch* b, int cohort, const double* M_or_Phi, int is_phi,
+                              double h, double sigma2, const double* XL, const double* Y);
+
+/* One batched solve. X, mb, b, wald, status are HOST arrays with one entry per cohort;
+ * the entries X[c] (n[c] x mb[c] int8 dosages), b[c], wald[c] (may be NULL, or wald
+ * itself NULL), status[c] are DEVICE pointers laid out as in gwas_solve_block_device.
+ * 1 <= mb[c] <= m_blk. Asynchronous on gwas_batch_stream(); the device tables behind
+ * the launch are rebuilt (synchronously) when the pointers or sizes change.
+ * Errors: GWAS_ERR_ARG, GWAS_ERR_STATE (a cohort not factored), GWAS_ERR_CUDA. */
+gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const int64_t* mb,
+                                    double* const* bo, double* const* wald,
+                                    uint8_t* const* status);
+
+/* Wait for the batch's queued work (timeout_ms < 0: no limit; else GWAS_ERR_TIMEOUT). */
+gwas_status gwas_batch_sync(gwas_batch* b, int timeout_ms);
+
+/* Counters summed over the batch's solves (factor_* summed over cohorts). */
+gwas_status gwas_batch_get_stats(gwas_batch* b, gwas_stats* out);
+gwas_status gwas_batch_reset_stats(gwas_batch* b);
+
+/* Free the batch and every cohort context in it. NULL is allowed. */
+gwas_status gwas_batch_finalize(gwas_batch* b);
+
+/* Text of the batch's last error ("" if none). */
+const char* gwas_batch_last_error(const gwas_batch* b);
+
+/* The batch's stream, as a cudaStream_t cast to void*. */
+void* gwas_batch_stream(const gwas_batch* b);
 
 /*
  * Allocation-free FP64 block solve. The paper has no counterpart: this entry point

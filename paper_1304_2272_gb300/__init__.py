@@ -10,6 +10,15 @@ from .gwas import (  # noqa: F401
     GWAS_PREC_FP64,
     GWAS_PREC_MIXED,
     GwasError,
+    gwas_batch_factor,
+    gwas_batch_finalize,
+    gwas_batch_get_stats,
+    gwas_batch_init,
+    gwas_batch_last_error,
+    gwas_batch_reset_stats,
+    gwas_batch_solve_device,
+    gwas_batch_stream,
+    gwas_batch_sync,
     gwas_default_opts,
     gwas_error_index,
     gwas_factor,
@@ -21,6 +30,7 @@ from .gwas import (  # noqa: F401
     gwas_solve_all,
     gwas_solve_block,
     gwas_solve_block_device,
+    gwas_solve_block_noalloc,
     gwas_stream,
     gwas_sync,
     load,

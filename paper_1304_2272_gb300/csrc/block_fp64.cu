@@ -18,17 +18,15 @@ namespace gwas {
 // One CTA = one 64-row x 64-SNP unit; 256 threads, 4 rows x 4 SNPs per thread.
 // Thread (tx, ty): rows tx + 16 a, SNPs ty + 16 b. Units are ordered heaviest row
 // tile first (a row tile r needs k < (r+1)*64) so the tail of the grid is short.
-__global__ void __launch_bounds__(256)
-k_block_fp64(CohortDev c, const int8_t* __restrict__ X, int64_t ldx, int64_t mb, int n_rt,
-             int n_ct, double* __restrict__ part, int64_t ldp, uint8_t* __restrict__ bad) {
+__device__ __forceinline__ void block_fp64_unit(const CohortDev& c, const int8_t* __restrict__ X,
+                                                int64_t ldx, int64_t mb, int n_rt, int rt, int ct,
+                                                double* __restrict__ part, int64_t ldp,
+                                                uint8_t* __restrict__ bad) {
     __shared__ double As[KC64][T64 + 1];  // W(r0 + i, k0 + k)
     __shared__ double Bs[KC64][T64 + 1];  // x(k0 + k, c0 + j) as double
     __shared__ int sbad[T64];
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
-    const int unit = blockIdx.x;
-    const int rt = n_rt - 1 - unit / n_ct;
-    const int ct = unit % n_ct;
     const int64_t n = c.n;
     const int64_t r0 = (int64_t)rt * T64, c0 = (int64_t)ct * T64;
     const int64_t kend = min64(n, r0 + T64);
@@ -110,6 +108,37 @@ k_block_fp64(CohortDev c, const int8_t* __restrict__ X, int64_t ldx, int64_t mb,
         __syncthreads();
         if (tid < T64 && c0 + tid < mb) bad[c0 + tid] = (uint8_t)sbad[tid];
     }
+}
+
+__global__ void __launch_bounds__(256)
+k_block_fp64(CohortDev c, const int8_t* __restrict__ X, int64_t ldx, int64_t mb, int n_rt,
+             int n_ct, double* __restrict__ part, int64_t ldp, uint8_t* __restrict__ bad) {
+    const int unit = blockIdx.x;
+    block_fp64_unit(c, X, ldx, mb, n_rt, n_rt - 1 - unit / n_ct, unit % n_ct, part, ldp, bad);
+}
+
+// Batched cohorts: one grid over every cohort's units (cohort found by binary search).
+__global__ void __launch_bounds__(256)
+k_block_fp64_batch(const BatchJob* __restrict__ jobs, int n_jobs) {
+    const int64_t u = blockIdx.x;
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (jobs[mid].unit_base <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchJob& j = jobs[lo];
+    const int unit = (int)(u - j.unit_base);
+    block_fp64_unit(j.c, j.X, j.c.n, j.mb, j.n_rt64, j.n_rt64 - 1 - unit / j.n_ct64,
+                    unit % j.n_ct64, j.part, j.ldp, j.bad);
+}
+
+cudaError_t launch_block_fp64_batch(const BatchJob* jobs, int n_jobs, int64_t n_units,
+                                    cudaStream_t s) {
+    if (n_units <= 0) return cudaSuccess;
+    if (n_units > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_block_fp64_batch<<<(unsigned)n_units, 256, 0, s>>>(jobs, n_jobs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_block_fp64(const CohortDev& c, const int8_t* X, int64_t ldx, int64_t mb,

@@ -50,49 +50,77 @@ __host__ __device__ constexpr int rows_pair(int S) {
 }
 }  // namespace mx
 
+// Launch-wide values (shared by every cohort of a batch).
 struct MixedArgs {
-    int n_rt;        // row tiles of L^{-1}
-    int n_ct;        // SNP tiles of 128
-    int n_kc_full;   // k chunks covering n
-    int R_e;         // linear rows (q + t)
-    int N_e;         // UMMA N of the linear tile
+    CohortMx c;   // the cohort of a single-cohort launch
+    int R_e;      // linear rows (q + t)
+    int N_e;      // UMMA N of the linear tile
     int stages;
-    int group;       // SNP tiles per L2 group
     int n_units;
-    int64_t mb;
-    int64_t ldp;
-    const int* E_w;
-    const int* E_e;
-    double* sq_part;  // [n_rt][ldp]
-    double* lin;      // [R_e][ldp]
     int* err;
 };
 
-// Unit u -> (rt, ct). Groups of `group` SNP tiles; inside a group the linear tile of
-// every SNP tile comes first, then row tiles from the heaviest (rt = n_rt-1) down.
-__device__ __forceinline__ void decode_unit(const MixedArgs& a, int u, int& rt, int& ct) {
-    const int levels = a.n_rt + 1;
-    const int per_group = a.group * levels;
+// Unit u -> (rt, ct) inside one cohort. Groups of `group` SNP tiles; inside a group the
+// linear tile of every SNP tile comes first, then row tiles from the heaviest down.
+__device__ __forceinline__ void decode_unit(const CohortMx& c, int u, int& rt, int& ct) {
+    const int levels = c.n_rt + 1;
+    const int per_group = c.group * levels;
     const int g = u / per_group;
     const int w = u - g * per_group;
-    const int ngroups = (a.n_ct + a.group - 1) / a.group;
-    const int gsize = (g == ngroups - 1) ? a.n_ct - g * a.group : a.group;
+    const int ngroups = (c.n_ct + c.group - 1) / c.group;
+    const int gsize = (g == ngroups - 1) ? c.n_ct - g * c.group : c.group;
     const int level = w / gsize;
-    ct = g * a.group + (w - level * gsize);
-    rt = (level == 0) ? (int)mx::EXTRA : a.n_rt - level;
+    ct = g * c.group + (w - level * gsize);
+    rt = (level == 0) ? (int)mx::EXTRA : c.n_rt - level;
 }
 
-__device__ __forceinline__ void record_error(const MixedArgs& a, volatile int* abort_flag,
-                                             int code) {
+__device__ __forceinline__ void record_error(int* err, volatile int* abort_flag, int code) {
     *abort_flag = 1;
-    atomicCAS(a.err, 0, code);
+    atomicCAS(err, 0, code);
 }
+
+// Where a unit's cohort and tensor maps come from: one cohort (maps as kernel
+// parameters) or a table of cohorts in global memory (maps in global memory, three per
+// cohort: dosages, limb row tiles, linear tile).
+struct SrcOne {
+    CUtensorMap tmX, tmW, tmE;
+    MixedArgs a;
+    __device__ __forceinline__ const CohortMx* locate(int u, int& ci, int& local) const {
+        ci = 0;
+        local = u;
+        return &a.c;
+    }
+    __device__ __forceinline__ const CUtensorMap* mapX(int) const { return &tmX; }
+    __device__ __forceinline__ const CUtensorMap* mapB(int, bool ex) const { return ex ? &tmE : &tmW; }
+};
+
+struct SrcBatch {
+    const CohortMx* tab;
+    const CUtensorMap* maps;
+    int n_cohorts;
+    MixedArgs a;  // launch-wide fields; a.c unused
+    __device__ __forceinline__ const CohortMx* locate(int u, int& ci, int& local) const {
+        int lo = 0, hi = n_cohorts - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (tab[mid].unit_base <= (int64_t)u) lo = mid;
+            else hi = mid - 1;
+        }
+        ci = lo;
+        local = (int)(u - tab[lo].unit_base);
+        return &tab[lo];
+    }
+    __device__ __forceinline__ const CUtensorMap* mapX(int ci) const { return maps + 3 * ci; }
+    __device__ __forceinline__ const CUtensorMap* mapB(int ci, bool ex) const {
+        return maps + 3 * ci + (ex ? 2 : 1);
+    }
+};
 
 // Epilogue of one unit for the SNP held in TMEM lane `tb` (one thread = one SNP):
 // row tiles -> sum over the tile's R rows of xbar^2, exact in 128-bit integers;
 // the linear tile -> the q + t linear reductions.
 template <int S, int R>
-__device__ __forceinline__ void epilogue_unit(const MixedArgs& a, uint32_t tb, int rt,
+__device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32_t tb, int rt,
                                               int64_t snp) {
     using namespace tc;
     const int shift0 = 8 + 9 * (S - 1);
@@ -120,12 +148,12 @@ __device__ __forceinline__ void epilogue_unit(const MixedArgs& a, uint32_t tb, i
         if (snp < a.mb) a.sq_part[(int64_t)rt * a.ldp + snp] = val;
     } else {
 #pragma unroll 1
-        for (int j = 0; j < a.R_e; ++j) {
+        for (int j = 0; j < R_e; ++j) {
             long long T = 0;
 #pragma unroll
             for (int l = 0; l < S; ++l) {
                 uint32_t x;
-                tmem_ld1(tb + (uint32_t)(l * a.R_e + j), x);
+                tmem_ld1(tb + (uint32_t)(l * R_e + j), x);
                 tmem_wait_ld();
                 T = T * 512 + (long long)__float2int_rn(__uint_as_float(x));
             }
@@ -134,11 +162,10 @@ __device__ __forceinline__ void epilogue_unit(const MixedArgs& a, uint32_t tb, i
     }
 }
 
-template <int S, int R>
-__global__ void __launch_bounds__(256, 1)
-k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
-              const __grid_constant__ CUtensorMap tmE, const MixedArgs a) {
+template <int S, int R, class Src>
+__global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ Src src) {
     using namespace tc;
+    const MixedArgs& a = src.a;
     constexpr int N = R * S;
     constexpr uint32_t A_BYTES = mx::BM * mx::BK * 2;
     const int NB = N > a.N_e ? N : a.N_e;
@@ -176,9 +203,9 @@ k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         tmem_relinquish();
     }
     if (warp == 1 && lane == 0) {
-        prefetch_tmap(&tmX);
-        prefetch_tmap(&tmW);
-        prefetch_tmap(&tmE);
+        prefetch_tmap(src.mapX(0));
+        prefetch_tmap(src.mapB(0, false));
+        prefetch_tmap(src.mapB(0, true));
     }
     fence_before_sync();
     __syncthreads();
@@ -198,20 +225,22 @@ k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         for (int r = 0; r < rounds && !*abort_flag; ++r) {
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
-            int rt, ct;
-            decode_unit(a, u, rt, ct);
+            int ci, lu, rt, ct;
+            const CohortMx& cm = *src.locate(u, ci, lu);
+            decode_unit(cm, lu, rt, ct);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? a.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.n_kc_full);
-            const int ybase = ex ? a.n_rt * N : rt * N;
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, cm.n_kc_full);
+            const int ybase = ex ? cm.n_rt * N : rt * N;
             const uint32_t bytes = A_BYTES + (uint32_t)(ex ? a.N_e : N) * mx::BK * 2;
             for (int kc = 0; kc < nk; ++kc) {
                 if (!mbar_wait(&empty[stage], phase ^ 1, mx::WAIT_NS)) {
-                    record_error(a, abort_flag, 1);
+                    record_error(a.err, abort_flag, 1);
                     break;
                 }
                 mbar_arrive_expect_tx(&full[stage], bytes);
-                tma_load_2d(sA + stage * A_BYTES, &tmX, kc * mx::BK, ct * mx::BM, &full[stage]);
-                tma_load_2d(sB + stage * B_BYTES, ex ? &tmE : &tmW, kc * mx::BK, ybase,
+                tma_load_2d(sA + stage * A_BYTES, src.mapX(ci), kc * mx::BK, ct * mx::BM,
+                            &full[stage]);
+                tma_load_2d(sB + stage * B_BYTES, src.mapB(ci, ex), kc * mx::BK, ybase,
                             &full[stage]);
                 issued[stage] = true;
                 issued_parity[stage] = phase;
@@ -235,12 +264,13 @@ k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         for (int r = 0; r < rounds && !*abort_flag; ++r) {
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
-            int rt, ct;
-            decode_unit(a, u, rt, ct);
+            int ci, lu, rt, ct;
+            const CohortMx& cm = *src.locate(u, ci, lu);
+            decode_unit(cm, lu, rt, ct);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? a.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.n_kc_full);
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, cm.n_kc_full);
             if (!mbar_wait(&tempty[abuf], aphase ^ 1, mx::WAIT_NS)) {
-                record_error(a, abort_flag, 2);
+                record_error(a.err, abort_flag, 2);
                 break;
             }
             fence_after_sync();
@@ -249,7 +279,7 @@ k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
             bool ok = true;
             for (int kc = 0; kc < nk; ++kc) {
                 if (!mbar_wait(&full[stage], phase, mx::WAIT_NS)) {
-                    record_error(a, abort_flag, 3);
+                    record_error(a.err, abort_flag, 3);
                     ok = false;
                     break;
                 }
@@ -281,15 +311,16 @@ k_block_mixed(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         for (int r = 0; r < rounds && !*abort_flag; ++r) {
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
-            int rt, ct;
-            decode_unit(a, u, rt, ct);
+            int ci, lu, rt, ct;
+            const CohortMx& cm = *src.locate(u, ci, lu);
+            decode_unit(cm, lu, rt, ct);
             if (!mbar_wait(&tfull[abuf], aphase, mx::WAIT_NS)) {
-                record_error(a, abort_flag, 4);
+                record_error(a.err, abort_flag, 4);
                 break;
             }
             fence_after_sync();
             const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
-            epilogue_unit<S, R>(a, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
+            epilogue_unit<S, R>(cm, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[abuf]);
@@ -386,16 +417,16 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
             int rt, ctp;
-            decode_unit(a, u, rt, ctp);
+            decode_unit(a.c, u, rt, ctp);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? a.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.n_kc_full);
+            const int nk = ex ? a.c.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.c.n_kc_full);
             const int half = ex ? NeH : NH;
-            const int ybase = (ex ? a.n_rt * N : rt * N) + (int)rank * half;
+            const int ybase = (ex ? a.c.n_rt * N : rt * N) + (int)rank * half;
             const int ct = 2 * ctp + (int)rank;
             const uint32_t pair_bytes = 2u * (A_BYTES + (uint32_t)half * mx::BK * 2);
             for (int kc = 0; kc < nk; ++kc) {
                 if (!mbar_wait(&empty[stage], phase ^ 1, mx::WAIT_NS)) {
-                    record_error(a, abort_flag, 11);
+                    record_error(a.err, abort_flag, 11);
                     break;
                 }
                 if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
@@ -424,11 +455,11 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
             int rt, ctp;
-            decode_unit(a, u, rt, ctp);
+            decode_unit(a.c, u, rt, ctp);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? a.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.n_kc_full);
+            const int nk = ex ? a.c.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.c.n_kc_full);
             if (!mbar_wait(&tempty[abuf], aphase ^ 1, mx::WAIT_NS)) {
-                record_error(a, abort_flag, 12);
+                record_error(a.err, abort_flag, 12);
                 break;
             }
             fence_after_sync();
@@ -437,7 +468,7 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             bool ok = true;
             for (int kc = 0; kc < nk; ++kc) {
                 if (!mbar_wait(&full[stage], phase, mx::WAIT_NS)) {
-                    record_error(a, abort_flag, 13);
+                    record_error(a.err, abort_flag, 13);
                     ok = false;
                     break;
                 }
@@ -469,15 +500,15 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
             int rt, ctp;
-            decode_unit(a, u, rt, ctp);
+            decode_unit(a.c, u, rt, ctp);
             if (!mbar_wait(&tfull[abuf], aphase, mx::WAIT_NS)) {
-                record_error(a, abort_flag, 14);
+                record_error(a.err, abort_flag, 14);
                 break;
             }
             fence_after_sync();
             const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
             const int ct = 2 * ctp + (int)rank;
-            epilogue_unit<S, R>(a, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
+            epilogue_unit<S, R>(a.c, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[abuf]), 0));
@@ -497,31 +528,53 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 // ----------------------------------------------------------------------------
 // Dosages -> BF16 rows (one SNP per row, k contiguous), flags for bad dosages.
 // ----------------------------------------------------------------------------
+// One SNP row: n dosages -> BF16, returns nonzero (block-wide) if a dosage is not in {0,1,2}.
+__device__ __forceinline__ int geno_row(const int8_t* __restrict__ src, int64_t n,
+                                        uint16_t* __restrict__ dst) {
+    int flag = 0;
+    for (int64_t k = 4 * (int64_t)threadIdx.x; k < n; k += 4 * (int64_t)blockDim.x) {
+        uint16_t o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int v = (k + e < n) ? (int)src[k + e] : 0;
+            flag |= (unsigned)v > 2u;
+            o[e] = v == 1 ? 0x3F80u : (v == 2 ? 0x4000u : 0u);
+        }
+        if (k + 3 < n) {
+            *reinterpret_cast<uint2*>(dst + k) =
+                make_uint2((uint32_t)o[0] | ((uint32_t)o[1] << 16),
+                           (uint32_t)o[2] | ((uint32_t)o[3] << 16));
+        } else {
+            for (int e = 0; k + e < n; ++e) dst[k + e] = o[e];
+        }
+    }
+    return __syncthreads_or(flag);
+}
+
 __global__ void __launch_bounds__(256)
 k_geno_bf16(const int8_t* __restrict__ X, int64_t ldx, int64_t n, int64_t mb,
             uint16_t* __restrict__ Xb, int64_t n_pad, uint8_t* __restrict__ bad) {
     for (int64_t j = blockIdx.x; j < mb; j += gridDim.x) {
-        const int8_t* src = X + j * ldx;
-        uint16_t* dst = Xb + j * n_pad;
-        int flag = 0;
-        for (int64_t k = 4 * (int64_t)threadIdx.x; k < n; k += 4 * (int64_t)blockDim.x) {
-            uint16_t o[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int v = (k + e < n) ? (int)src[k + e] : 0;
-                flag |= (unsigned)v > 2u;
-                o[e] = v == 1 ? 0x3F80u : (v == 2 ? 0x4000u : 0u);
-            }
-            if (k + 3 < n) {
-                *reinterpret_cast<uint2*>(dst + k) =
-                    make_uint2((uint32_t)o[0] | ((uint32_t)o[1] << 16),
-                               (uint32_t)o[2] | ((uint32_t)o[3] << 16));
-            } else {
-                for (int e = 0; k + e < n; ++e) dst[k + e] = o[e];
-            }
-        }
-        flag = __syncthreads_or(flag);
+        const int flag = geno_row(X + j * ldx, n, Xb + j * n_pad);
         if (threadIdx.x == 0) bad[j] = (uint8_t)(flag != 0);
+    }
+}
+
+// Batched cohorts: one block per SNP of every cohort.
+__global__ void __launch_bounds__(256)
+k_geno_bf16_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps) {
+    for (int64_t g = blockIdx.x; g < n_snps; g += gridDim.x) {
+        int lo = 0, hi = n_jobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (jobs[mid].snp_base <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchJob& jb = jobs[lo];
+        const int64_t j = g - jb.snp_base;
+        if (j >= jb.mb) continue;  // uniform across the block
+        const int flag = geno_row(jb.X + j * jb.c.n, jb.c.n, jb.Xb + j * jb.n_pad);
+        if (threadIdx.x == 0) jb.bad[j] = (uint8_t)(flag != 0);
     }
 }
 
@@ -748,38 +801,49 @@ cudaError_t mixed_prepare(MixedDev& m, const double* W, int64_t ldw, const doubl
     return cudaSuccess;
 }
 
+static CohortMx make_cohort(const MixedDev& m, int64_t mb, bool pair) {
+    CohortMx c;
+    c.n_rt = m.n_rt;
+    c.n_ct = (int)ceil_div(mb, pair ? 2 * mx::BM : mx::BM);  // SNP tiles, or pairs of them
+    c.n_kc_full = (int)(m.n_pad / mx::BK);
+    const int64_t per_tile = (pair ? 2ll : 1ll) * mx::BM * m.n_pad * 2;  // BF16 dosages
+    const int64_t budget = (int64_t)std::max(1, m.cfg_group_mb) << 20;
+    c.group = (int)std::max<int64_t>(1, std::min<int64_t>(c.n_ct, budget / per_tile));
+    c.mb = mb;
+    c.ldp = m.ldp;
+    c.unit_base = 0;
+    c.E_w = m.E;
+    c.E_e = m.E + m.n_rt;
+    c.sq_part = m.sq_part;
+    c.lin = m.lin;
+    return c;
+}
+
 static MixedArgs make_args(const MixedDev& m, int64_t mb, bool pair) {
     MixedArgs a;
-    a.n_rt = m.n_rt;
-    a.n_ct = (int)ceil_div(mb, pair ? 2 * mx::BM : mx::BM);  // SNP tiles, or pairs of them
-    a.n_kc_full = (int)(m.n_pad / mx::BK);
+    a.c = make_cohort(m, mb, pair);
     a.R_e = m.R_e;
     a.N_e = m.N_e;
     a.stages = stage_count(m.R * m.S, m.N_e, pair);
     if (m.cfg_stages >= 2) a.stages = std::min(a.stages, m.cfg_stages);
-    const int64_t per_tile = (pair ? 2ll : 1ll) * mx::BM * m.n_pad * 2;  // BF16 dosages
-    const int64_t budget = (int64_t)std::max(1, m.cfg_group_mb) << 20;
-    a.group = (int)std::max<int64_t>(1, std::min<int64_t>(a.n_ct, budget / per_tile));
-    a.n_units = a.n_ct * (a.n_rt + 1);
-    a.mb = mb;
-    a.ldp = m.ldp;
-    a.E_w = m.E;
-    a.E_e = m.E + m.n_rt;
-    a.sq_part = m.sq_part;
-    a.lin = m.lin;
+    a.n_units = a.c.n_ct * (a.c.n_rt + 1);
     a.err = m.err;
     return a;
 }
 
 template <int S, int R>
 static cudaError_t launch_single_t(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
-    const MixedArgs a = make_args(m, mb, false);
-    const size_t smem = smem_bytes(R * S, m.N_e, false, a.stages);
-    cudaError_t e = cudaFuncSetAttribute(k_block_mixed<S, R>,
+    SrcOne src;
+    src.tmX = m.tmX;
+    src.tmW = m.tmW;
+    src.tmE = m.tmE;
+    src.a = make_args(m, mb, false);
+    const size_t smem = smem_bytes(R * S, m.N_e, false, src.a.stages);
+    cudaError_t e = cudaFuncSetAttribute(k_block_mixed<S, R, SrcOne>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = std::max(1, std::min(num_sms, a.n_units));
-    k_block_mixed<S, R><<<grid, 256, smem, s>>>(m.tmX, m.tmW, m.tmE, a);
+    const int grid = std::max(1, std::min(num_sms, src.a.n_units));
+    k_block_mixed<S, R, SrcOne><<<grid, 256, smem, s>>>(src);
     return cudaGetLastError();
 }
 
@@ -822,6 +886,14 @@ cudaError_t launch_geno_bf16(const MixedDev& m, const int8_t* X, int64_t ldx, in
     return cudaGetLastError();
 }
 
+cudaError_t launch_geno_bf16_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps,
+                                   cudaStream_t s) {
+    if (n_snps <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<int64_t>(n_snps, 1 << 20);
+    k_geno_bf16_batch<<<grid, 256, 0, s>>>(jobs, n_jobs, n_snps);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
     if (mb < 1 || mb > m.mb_pad_max) return cudaErrorInvalidValue;
     using namespace mx;
@@ -835,6 +907,76 @@ cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaS
         if (m.S == 4 && m.R == rows_single(4)) return launch_single_t<4, rows_single(4)>(m, mb, num_sms, s);
     }
     return cudaErrorInvalidValue;
+}
+
+// ---- batched cohorts: one persistent launch over a device table of cohorts ----------
+
+int mixed_stage_count(const MixedDev& m) {
+    int st = stage_count(m.R * m.S, m.N_e, false);
+    if (m.cfg_stages >= 2) st = std::min(st, m.cfg_stages);
+    return st;
+}
+
+CohortMx mixed_cohort_entry(const MixedDev& m, int64_t mb, int64_t unit_base) {
+    CohortMx c = make_cohort(m, mb, false);
+    c.unit_base = unit_base;
+    return c;
+}
+
+int64_t mixed_cohort_units(const MixedDev& m, int64_t mb) {
+    const CohortMx c = make_cohort(m, mb, false);
+    return (int64_t)c.n_ct * (c.n_rt + 1);
+}
+
+template <int S, int R>
+static cudaError_t batch_prepare_t(int R_e, int N_e, int stages) {
+    const size_t smem = smem_bytes(R * S, N_e, false, stages);
+    return cudaFuncSetAttribute(k_block_mixed<S, R, SrcBatch>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int S, int R>
+static cudaError_t batch_launch_t(const CohortMx* tab, const CUtensorMap* maps, int n_cohorts,
+                                  int n_units, int R_e, int N_e, int stages, int* err, int num_sms,
+                                  cudaStream_t s) {
+    SrcBatch src;
+    src.tab = tab;
+    src.maps = maps;
+    src.n_cohorts = n_cohorts;
+    src.a = MixedArgs{};
+    src.a.R_e = R_e;
+    src.a.N_e = N_e;
+    src.a.stages = stages;
+    src.a.n_units = n_units;
+    src.a.err = err;
+    const size_t smem = smem_bytes(R * S, N_e, false, stages);
+    const int grid = std::max(1, std::min(num_sms, n_units));
+    k_block_mixed<S, R, SrcBatch><<<grid, 256, smem, s>>>(src);
+    return cudaGetLastError();
+}
+
+cudaError_t mixed_batch_prepare(int S, int R_e, int N_e, int stages) {
+    using namespace mx;
+    switch (S) {
+        case 2: return batch_prepare_t<2, rows_single(2)>(R_e, N_e, stages);
+        case 3: return batch_prepare_t<3, rows_single(3)>(R_e, N_e, stages);
+        case 4: return batch_prepare_t<4, rows_single(4)>(R_e, N_e, stages);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_block_mixed_batch(const CohortMx* tab, const CUtensorMap* maps, int n_cohorts,
+                                     int64_t n_units, int S, int R_e, int N_e, int stages,
+                                     int* err, int num_sms, cudaStream_t s) {
+    using namespace mx;
+    if (n_units <= 0) return cudaSuccess;
+    if (n_units > 0x7fffffffLL) return cudaErrorInvalidValue;
+    switch (S) {
+        case 2: return batch_launch_t<2, rows_single(2)>(tab, maps, n_cohorts, (int)n_units, R_e, N_e, stages, err, num_sms, s);
+        case 3: return batch_launch_t<3, rows_single(3)>(tab, maps, n_cohorts, (int)n_units, R_e, N_e, stages, err, num_sms, s);
+        case 4: return batch_launch_t<4, rows_single(4)>(tab, maps, n_cohorts, (int)n_units, R_e, N_e, stages, err, num_sms, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace gwas

@@ -58,7 +58,7 @@ struct CohortDev {
 };
 
 // Number of per-SNP reduction values: q (S_BL) + 1 (S_BR) + t (bbar_B).
-inline int n_red(const CohortDev& c) { return c.q + 1 + c.t; }
+__host__ __device__ inline int n_red(const CohortDev& c) { return c.q + 1 + c.t; }
 
 // FP64 path: for each (64-row tile r, 64-SNP tile) computes Xbar = W[r-tile, :] X
 // and its row-tile partial sums of Xbar^T [Xbar_L | Xbar | Ybar] into
@@ -73,6 +73,21 @@ cudaError_t launch_snp_solve(const CohortDev& c, const double* part, int64_t ldp
                              uint8_t* status, cudaStream_t s);
 
 // ---- mixed-precision hot path (block_mixed.cu) ----------------------------------
+
+// Per-cohort constants of a mixed launch (one entry per cohort of a batched launch).
+struct CohortMx {
+    int n_rt;           // row tiles of L^{-1}
+    int n_ct;           // SNP tiles (of 128; of 256 in the CTA-pair kernel)
+    int n_kc_full;      // k chunks covering n
+    int group;          // SNP tiles per L2 group
+    int64_t mb;         // SNPs
+    int64_t ldp;        // leading dimension of sq_part / lin
+    int64_t unit_base;  // first unit of this cohort in a batched launch
+    const int* E_w;     // exponent per row tile
+    const int* E_e;     // exponent per linear row
+    double* sq_part;    // [n_rt][ldp]
+    double* lin;        // [R_e][ldp]
+};
 
 // Device buffers and tensor maps of the BF16-limb path for one cohort.
 struct MixedDev {
@@ -115,6 +130,45 @@ cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaS
 // p x p solves from the mixed partial layout.
 cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const uint8_t* bad,
                                    int64_t mb, double* b, double* wald, uint8_t* status,
+                                   cudaStream_t s);
+
+// Batched cohorts (one CTA per 128-SNP tile, tile height rows_single(S)).
+int mixed_stage_count(const MixedDev& m);
+CohortMx mixed_cohort_entry(const MixedDev& m, int64_t mb, int64_t unit_base);
+int64_t mixed_cohort_units(const MixedDev& m, int64_t mb);
+cudaError_t mixed_batch_prepare(int S, int R_e, int N_e, int stages);
+cudaError_t launch_block_mixed_batch(const CohortMx* tab, const CUtensorMap* maps, int n_cohorts,
+                                     int64_t n_units, int S, int R_e, int N_e, int stages,
+                                     int* err, int num_sms, cudaStream_t s);
+
+// ---- batched FP64 path, dosage conversion and p x p solves (batch.cu) ------------------
+
+// One cohort of a batched FP64 / conversion / solve launch.
+struct BatchJob {
+    CohortDev c;
+    const int8_t* X = nullptr;   // n x mb dosages (device), ld = n
+    int64_t mb = 0;
+    int64_t snp_base = 0;        // first SNP of this cohort in the batch's SNP numbering
+    int64_t unit_base = 0;       // first FP64 unit of this cohort
+    int n_rt64 = 0, n_ct64 = 0;  // FP64 tiles (64 rows, 64 SNPs)
+    double* part = nullptr;      // FP64 partials [n_rt64][p+t][ldp]
+    int64_t ldp = 0;
+    uint8_t* bad = nullptr;
+    uint16_t* Xb = nullptr;      // mixed: BF16 rows [mb_pad][n_pad]
+    int64_t n_pad = 0;
+    const double* sq_part = nullptr;  // mixed partials
+    const double* lin = nullptr;
+    int n_tiles_mx = 0;
+    double* b = nullptr;
+    double* wald = nullptr;
+    uint8_t* status = nullptr;
+};
+
+cudaError_t launch_block_fp64_batch(const BatchJob* jobs, int n_jobs, int64_t n_units,
+                                    cudaStream_t s);
+cudaError_t launch_geno_bf16_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps,
+                                   cudaStream_t s);
+cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, bool mixed,
                                    cudaStream_t s);
 
 }  // namespace gwas

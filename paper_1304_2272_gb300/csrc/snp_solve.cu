@@ -45,11 +45,10 @@ struct RedMixed {
 };
 
 template <class Red>
-__global__ void __launch_bounds__(128)
-k_snp_solve(CohortDev c, Red red, const uint8_t* __restrict__ bad, int64_t mb,
-            double* __restrict__ b, double* __restrict__ wald, uint8_t* __restrict__ status) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= mb) return;
+__device__ __forceinline__ void solve_snp(const CohortDev& c, const Red& red,
+                                          const uint8_t* __restrict__ bad, int64_t i,
+                                          double* __restrict__ b, double* __restrict__ wald,
+                                          uint8_t* __restrict__ status) {
     const int q = c.q, t = c.t, p = q + 1;
 
     double sbl[MAX_P];  // S_BLi (q values) then S_BRi
@@ -92,12 +91,54 @@ k_snp_solve(CohortDev c, Red red, const uint8_t* __restrict__ bad, int64_t mb,
     status[i] = st;
 }
 
+template <class Red>
+__global__ void __launch_bounds__(128)
+k_snp_solve(CohortDev c, Red red, const uint8_t* __restrict__ bad, int64_t mb,
+            double* __restrict__ b, double* __restrict__ wald, uint8_t* __restrict__ status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= mb) return;
+    solve_snp(c, red, bad, i, b, wald, status);
+}
+
+// Batched cohorts: one thread per SNP of every cohort.
+template <bool MIXED>
+__global__ void __launch_bounds__(128)
+k_snp_solve_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n_snps) return;
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (jobs[mid].snp_base <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchJob& j = jobs[lo];
+    const int64_t i = g - j.snp_base;
+    if (i >= j.mb) return;
+    if (MIXED) {
+        RedMixed red{j.sq_part, j.lin, j.ldp, j.n_tiles_mx, j.c.q};
+        solve_snp(j.c, red, j.bad, i, j.b, j.wald, j.status);
+    } else {
+        RedFp64 red{j.part, j.ldp, j.n_rt64, n_red(j.c)};
+        solve_snp(j.c, red, j.bad, i, j.b, j.wald, j.status);
+    }
+}
+
 cudaError_t launch_snp_solve(const CohortDev& c, const double* part, int64_t ldp, int n_tiles,
                              const uint8_t* bad, int64_t mb, double* b, double* wald,
                              uint8_t* status, cudaStream_t s) {
     if (mb <= 0) return cudaSuccess;
     RedFp64 red{part, ldp, n_tiles, n_red(c)};
     k_snp_solve<<<(unsigned)ceil_div(mb, 128), 128, 0, s>>>(c, red, bad, mb, b, wald, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, bool mixed,
+                                   cudaStream_t s) {
+    if (n_snps <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)ceil_div(n_snps, 128);
+    if (mixed) k_snp_solve_batch<true><<<grid, 128, 0, s>>>(jobs, n_jobs, n_snps);
+    else k_snp_solve_batch<false><<<grid, 128, 0, s>>>(jobs, n_jobs, n_snps);
     return cudaGetLastError();
 }
 

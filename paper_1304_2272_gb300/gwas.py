@@ -35,7 +35,8 @@ GWAS_PREC_MIXED = 1
 
 class gwas_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("m_blk", ctypes.c_int), ("n_limbs", ctypes.c_int),
-                ("tile_cfg", ctypes.c_int), ("device", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("tile_cfg", ctypes.c_int), ("device", ctypes.c_int), ("timing", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
 
 
 class gwas_stats(ctypes.Structure):
@@ -79,6 +80,18 @@ SIGNATURES = {
     "gwas_stream": (_vp, [_ctx_p]),
     "gwas_solve_block_noalloc": (_int, [_i64, _int, _int, _vp, _i64, _vp, _vp, _vp, _vp, _vp,
                                         _i64, _vp, _vp, _vp, _vp]),
+    "gwas_batch_init": (_int, [_int, ctypes.POINTER(_i64), _int, _int, ctypes.POINTER(gwas_opts),
+                               ctypes.POINTER(_ctx_p)]),
+    "gwas_batch_factor": (_int, [_ctx_p, _int, _vp, _int, _dbl, _dbl, _vp, _vp]),
+    "gwas_batch_solve_device": (_int, [_ctx_p, ctypes.POINTER(_vp), ctypes.POINTER(_i64),
+                                       ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                       ctypes.POINTER(_vp)]),
+    "gwas_batch_sync": (_int, [_ctx_p, _int]),
+    "gwas_batch_get_stats": (_int, [_ctx_p, ctypes.POINTER(gwas_stats)]),
+    "gwas_batch_reset_stats": (_int, [_ctx_p]),
+    "gwas_batch_finalize": (_int, [_ctx_p]),
+    "gwas_batch_last_error": (ctypes.c_char_p, [_ctx_p]),
+    "gwas_batch_stream": (_vp, [_ctx_p]),
 }
 
 _lib = None
@@ -225,6 +238,75 @@ def gwas_solve_block_noalloc(n: int, p: int, t: int, Linv, ld_linv: int, XLbar, 
         stream)
     if st != GWAS_OK:
         raise GwasError(st, "gwas_solve_block_noalloc failed")
+
+
+# ---- batches of cohorts -------------------------------------------------------------
+def _bcheck(batch, st: int):
+    if st != GWAS_OK:
+        msg = load().gwas_batch_last_error(batch).decode() if batch else ""
+        raise GwasError(st, msg)
+
+
+def gwas_batch_init(n, p: int, t: int = 1, opts: gwas_opts | None = None, **kw):
+    """Create a batch of len(n) cohorts; keyword arguments override default options."""
+    lib = load()
+    o = opts if opts is not None else gwas_default_opts()
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    arr = (_i64 * len(n))(*[int(v) for v in n])
+    b = _ctx_p()
+    st = lib.gwas_batch_init(len(n), arr, int(p), int(t), ctypes.byref(o), ctypes.byref(b))
+    if st != GWAS_OK:
+        raise GwasError(st, "gwas_batch_init failed")
+    return b
+
+
+def gwas_batch_factor(batch, cohort: int, M_or_Phi, is_phi: bool, h: float, sigma2: float,
+                      XL, Y) -> None:
+    for a, nm in ((M_or_Phi, "M_or_Phi"), (XL, "XL"), (Y, "Y")):
+        _require(a, np.float64, nm)
+    _bcheck(batch, load().gwas_batch_factor(batch, int(cohort), _addr(M_or_Phi), int(bool(is_phi)),
+                                            float(h), float(sigma2), _addr(XL), _addr(Y)))
+
+
+def _ptr_array(items):
+    return (_vp * len(items))(*[_addr(x) for x in items])
+
+
+def gwas_batch_solve_device(batch, X, mb, b, wald, status) -> None:
+    """X, b, wald, status: sequences of device arrays (one per cohort); mb: SNP counts."""
+    n = len(X)
+    mbs = (_i64 * n)(*[int(v) for v in mb])
+    w = _ptr_array(wald) if wald is not None else None
+    _bcheck(batch, load().gwas_batch_solve_device(batch, _ptr_array(X), mbs, _ptr_array(b), w,
+                                                  _ptr_array(status)))
+
+
+def gwas_batch_sync(batch, timeout_ms: int = -1) -> None:
+    _bcheck(batch, load().gwas_batch_sync(batch, int(timeout_ms)))
+
+
+def gwas_batch_get_stats(batch) -> dict:
+    s = gwas_stats()
+    _bcheck(batch, load().gwas_batch_get_stats(batch, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def gwas_batch_reset_stats(batch) -> None:
+    _bcheck(batch, load().gwas_batch_reset_stats(batch))
+
+
+def gwas_batch_finalize(batch) -> None:
+    if batch:
+        load().gwas_batch_finalize(batch)
+
+
+def gwas_batch_last_error(batch) -> str:
+    return load().gwas_batch_last_error(batch).decode()
+
+
+def gwas_batch_stream(batch) -> int:
+    return int(load().gwas_batch_stream(batch) or 0)
 
 
 # ---- convenience wrapper (still marshalling only) --------------------------------
