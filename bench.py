@@ -45,6 +45,14 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision legs (n and n=30000) of an FP64 run")
     ap.add_argument("--mixed-steps", type=int, default=240)
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (mixed legs)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-cohorts legs (48 cohorts, 16 phenotypes)")
+    ap.add_argument("--batch-cohorts", type=int, default=48)
+    ap.add_argument("--batch-snps", type=int, default=50000,
+                    help="SNPs per cohort in the mixed batched leg")
+    ap.add_argument("--batch-snps-fp64", type=int, default=2048,
+                    help="SNPs per cohort per step in the FP64 batched leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -233,6 +241,12 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
     gwas.gwas_factor(ctx, np.asfortranarray(cohort.phi), True, cohort.h, cohort.sigma2,
                      cohort.XL, cohort.Y)
     setup_ms = gwas.gwas_get_stats(ctx)["factor_ms"]
+    tune = None
+    if precision == "mixed" and not args.no_tune:
+        from paper_1304_2272_gb300 import autotune
+        t0 = time.perf_counter()
+        tune = autotune.tuned_tile_cfg(ctx, n, p, t, prec, limbs, mb)
+        tune["tune_s"] = round(time.perf_counter() - t0, 2)
     pool = [synth.genotypes_torch(1000 * rank + s, n, mb, dev) for s in range(args.pool)]
     b = torch.empty((mb, t, p), dtype=torch.float64, device=dev)
     w = torch.empty((mb, t), dtype=torch.float64, device=dev)
@@ -314,11 +328,80 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
                 "launch_ms": launch_ms, "peak_source": src,
                 "fp64_equivalent_tflops": flops_per_snp(n, q, t) * value / world / 1e12}
     res = {"value": value, "ms_per_step": el_ms / steps, "steps": steps, "warmup": warmup,
-           "setup_ms": setup_ms, "roofline": roof, "e2e": e2e,
+           "setup_ms": setup_ms, "roofline": roof, "e2e": e2e, "autotune": tune,
            "gpu_launches": int(stats["kernel_launches"]), "clocks": clk,
            "status_ok_last_block": status_ok}
     gwas.gwas_finalize(ctx)
     return res, cohort, pool
+
+
+def measure_batch(args, env, precision, snps, steps, warmup):
+    """Batched cohorts: args.batch_cohorts cohorts, n ~ U[1000, 8000], p = 4, 16
+    phenotypes, h ~ U(0.2, 0.8), `snps` SNPs per cohort per step; one step = one batched
+    solve (one grouped launch of the block kernel, replayed from a CUDA graph)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1304_2272_gb300 import gwas
+
+    rank, world, local, dev = env
+    rng = np.random.default_rng(2026)
+    ns = rng.integers(1000, 8001, size=args.batch_cohorts).tolist()
+    hs = rng.uniform(0.2, 0.8, size=args.batch_cohorts)
+    t, p = 16, 4
+    prec = gwas.GWAS_PREC_FP64 if precision == "fp64" else gwas.GWAS_PREC_MIXED
+    b = gwas.gwas_batch_init(ns, p, t, precision=prec, m_blk=snps, device=local, timing=1,
+                             n_limbs=args.limbs, use_graph=1)
+    for k, n in enumerate(ns):
+        c = synth.make_cohort(3000 + k, n, t=t, h=float(hs[k]), device=dev)
+        gwas.gwas_batch_factor(b, k, np.asfortranarray(c.phi), True, c.h, c.sigma2, c.XL, c.Y)
+        del c
+    setup_ms = gwas.gwas_batch_get_stats(b)["factor_ms"]
+    X = [synth.genotypes_torch(7000 + 100 * rank + k, n, snps, dev) for k, n in enumerate(ns)]
+    bo = [torch.empty((snps, t, p), dtype=torch.float64, device=dev) for _ in ns]
+    wo = [torch.empty((snps, t), dtype=torch.float64, device=dev) for _ in ns]
+    so = [torch.empty((snps,), dtype=torch.uint8, device=dev) for _ in ns]
+    mbs = [snps] * len(ns)
+    stream = torch.cuda.ExternalStream(gwas.gwas_batch_stream(b), device=dev)
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        gwas.gwas_batch_solve_device(b, X, mbs, bo, wo, so)
+    gwas.gwas_batch_sync(b)
+    gwas.gwas_batch_reset_stats(b)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    for _ in range(steps):
+        gwas.gwas_batch_solve_device(b, X, mbs, bo, wo, so)
+    ev1.record(stream)
+    gwas.gwas_batch_sync(b)
+    clk = clocks.stop()
+    el_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([el_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        el_ms = float(tt.item())
+    st = gwas.gwas_batch_get_stats(b)
+    ok = int(sum(int((x == 0).sum().item()) for x in so))
+    gwas.gwas_batch_finalize(b)
+    total = world * steps * snps * len(ns)
+    work = sum(n * (n + 1) + 2.0 * n * (3 + 1 + t) for n in ns) * snps
+    res = {"precision": precision, "cohorts": len(ns), "n_min": min(ns), "n_max": max(ns),
+           "phenotypes": t, "snps_per_cohort": snps, "steps": steps,
+           "value": total / (el_ms / 1e3), "unit": "cohort-SNP/s",
+           "snp_phenotypes_per_s": t * total / (el_ms / 1e3), "ms_per_step": el_ms / steps,
+           "fp64_equivalent_tflops": work * steps / (el_ms / 1e3) / 1e12,
+           "setup_ms": setup_ms, "graph": True, "gpu_launches": int(st["kernel_launches"]),
+           "status_ok": ok, "clocks": clk}
+    if precision == "mixed":
+        bf16 = sum(args.limbs * (n * (n + 1) + 2.0 * n * (3 + t)) for n in ns) * snps
+        res["bf16_tflops"] = bf16 * steps / (el_ms / 1e3) / 1e12
+    return res
 
 
 def main():
@@ -346,8 +429,12 @@ def main():
             mixed.append({"n": n_mx, "limbs": args.limbs, "value": r["value"], "unit": UNIT,
                           "ms_per_step": r["ms_per_step"], "steps": steps_mx,
                           "setup_ms": r["setup_ms"], "roofline": r["roofline"],
-                          "e2e": r["e2e"], "clocks": r["clocks"],
+                          "e2e": r["e2e"], "clocks": r["clocks"], "autotune": r["autotune"],
                           "gpu_launches": r["gpu_launches"]})
+    batched = []
+    if args.precision == "fp64" and not args.no_batch:
+        batched.append(measure_batch(args, env, "mixed", args.batch_snps, 5, 2))
+        batched.append(measure_batch(args, env, "fp64", args.batch_snps_fp64, 2, 1))
     if rank == 0:
         line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
                 "steps": res["steps"], "warmup": res["warmup"], "ms_per_step": res["ms_per_step"],
@@ -359,6 +446,8 @@ def main():
                 "status_ok_last_block": res["status_ok_last_block"]}
         if mixed:
             line["mixed"] = mixed
+        if batched:
+            line["batched"] = batched
         if not args.no_cpu_baseline:
             Xh = np.asfortranarray(pool[0][:4096].cpu().numpy().T)
             line["cpu_baseline"] = cpu_baseline(cohort, Xh, args.cpu_seconds)

@@ -88,6 +88,15 @@ typedef struct {
     int64_t factor_launches;   /* kernels launched by the last gwas_factor            */
 } gwas_stats;
 
+/* Result of gwas_autotune. */
+typedef struct {
+    int tile_cfg;        /* fastest tile configuration (see gwas_opts.tile_cfg)          */
+    int64_t m_blk;       /* SNPs per block at which it was fastest                       */
+    double ms_per_snp;   /* device time per SNP of the whole block path at that setting  */
+    double snps_per_s;
+    int candidates;      /* (tile_cfg, block size) pairs timed                            */
+} gwas_tune;
+
 /* Fill *opts with defaults: FP64, m_blk 16384, 3 limbs, default tiles, device 0,
  * no timing events, CUDA graphs on. */
 void gwas_default_opts(gwas_opts* opts);
@@ -171,6 +180,27 @@ gwas_status gwas_reset_stats(gwas_ctx* ctx);
 
 /* The context's compute stream, as a cudaStream_t cast to void*. */
 void* gwas_stream(const gwas_ctx* ctx);
+
+/*
+ * Change the kernel tile configuration of a context (see gwas_opts.tile_cfg). For a
+ * GWAS_PREC_MIXED context whose limb tile height changes, the BF16 limbs are re-split
+ * from the FP64 L^{-1} kept by gwas_factor (no new factorisation). Synchronises the
+ * context. Errors: GWAS_ERR_ARG, GWAS_ERR_CUDA, GWAS_ERR_OOM.
+ */
+gwas_status gwas_set_tile_cfg(gwas_ctx* ctx, int tile_cfg);
+
+/*
+ * Autotuner: on a factored context, time the whole block path (dosage conversion,
+ * dominant kernel, p x p solves) for every candidate tile configuration (mixed: one
+ * CTA or CTA pairs, pipeline stages, L2 group size) and block size (4096, 8192, 16384
+ * and mb_max SNPs, up to m_blk) with CUDA events, `reps` launches each; keep the
+ * fastest configuration on the context and report it in *out. X: n x mb_max DEVICE
+ * dosages to time with, or NULL for synthetic ones (timing does not depend on the
+ * values). Allocates temporary device memory; synchronises the context; does not add
+ * to the context's counters. Errors: GWAS_ERR_STATE (no factor), GWAS_ERR_CUDA.
+ */
+gwas_status gwas_autotune(gwas_ctx* ctx, const int8_t* X, int64_t mb_max, int reps,
+                          gwas_tune* out);
 
 /* ---------------------------------------------------------------------------------
  * Batches of cohorts. Many independent cohorts (each its own n, M, X_L and Y with t

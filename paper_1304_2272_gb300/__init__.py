@@ -10,6 +10,7 @@ from .gwas import (  # noqa: F401
     GWAS_PREC_FP64,
     GWAS_PREC_MIXED,
     GwasError,
+    gwas_autotune,
     gwas_batch_factor,
     gwas_batch_finalize,
     gwas_batch_get_stats,
@@ -31,6 +32,7 @@ from .gwas import (  # noqa: F401
     gwas_solve_block,
     gwas_solve_block_device,
     gwas_solve_block_noalloc,
+    gwas_set_tile_cfg,
     gwas_stream,
     gwas_sync,
     load,

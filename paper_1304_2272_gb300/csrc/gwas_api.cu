@@ -6,6 +6,7 @@
 // "compute block k" and "copy b of block k-1 out", which is the paper's
 // load_start/load_wait/store_start/store_wait pattern with the disk replaced by
 // pinned host memory and the second memory region by the second device slot.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -161,6 +162,32 @@ gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, doubl
     return GWAS_OK;
 }
 
+void apply_tile_cfg(MixedDev& m, int tile_cfg) {
+    m.cfg_stages = 0;
+    m.cfg_group_mb = 40;
+    m.cfg_single_cta = false;
+    m.cfg_pair = false;
+    if (tile_cfg >= 0) {
+        m.cfg_stages = tile_cfg & 0xF;
+        const int g = (tile_cfg >> 4) & 0xFF;
+        if (g > 0) m.cfg_group_mb = g;
+        m.cfg_single_cta = ((tile_cfg >> 12) & 1) != 0;
+        m.cfg_pair = ((tile_cfg >> 13) & 1) != 0;
+    }
+}
+
+// (Re)allocate the mixed path's buffers whose size depends on the tile height R.
+cudaError_t mixed_alloc_layout(MixedDev& m) {
+    cudaFree(m.WL); cudaFree(m.bits); cudaFree(m.E); cudaFree(m.sq_part); cudaFree(m.lin);
+    m.WL = nullptr; m.bits = nullptr; m.E = nullptr; m.sq_part = nullptr; m.lin = nullptr;
+    cudaError_t e;
+    if ((e = dmalloc(&m.WL, (size_t)m.rows_total * m.n_pad)) != cudaSuccess) return e;
+    if ((e = dmalloc(&m.bits, (size_t)(m.n_rt + m.R_e))) != cudaSuccess) return e;
+    if ((e = dmalloc(&m.E, (size_t)(m.n_rt + m.R_e))) != cudaSuccess) return e;
+    if ((e = dmalloc(&m.sq_part, (size_t)m.n_rt * m.ldp)) != cudaSuccess) return e;
+    return dmalloc(&m.lin, (size_t)m.R_e * m.ldp);
+}
+
 void free_all(gwas_ctx* c) {
     cudaFree(c->L); cudaFree(c->W); cudaFree(c->Dinv); cudaFree(c->XLbar); cudaFree(c->Ybar);
     cudaFree(c->S_TL); cudaFree(c->bbar_T); cudaFree(c->d_info); cudaFree(c->part);
@@ -248,22 +275,12 @@ gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx**
         CKI(dmalloc(&c->part, (size_t)nt * nred * c->ldp));
     } else {
         MixedDev& m = c->mx;
-        if (o.tile_cfg >= 0) {
-            m.cfg_stages = o.tile_cfg & 0xF;
-            const int g = (o.tile_cfg >> 4) & 0xFF;
-            if (g > 0) m.cfg_group_mb = g;
-            m.cfg_single_cta = ((o.tile_cfg >> 12) & 1) != 0;
-            m.cfg_pair = ((o.tile_cfg >> 13) & 1) != 0;
-        }
+        apply_tile_cfg(m, o.tile_cfg);
         mixed_layout(m, n, o.n_limbs, c->q + t, o.m_blk);
         CKI(dmalloc(&c->Z, (size_t)n * (c->q + t)));
-        CKI(dmalloc(&m.WL, (size_t)m.rows_total * m.n_pad));
-        CKI(dmalloc(&m.bits, (size_t)(m.n_rt + m.R_e)));
-        CKI(dmalloc(&m.E, (size_t)(m.n_rt + m.R_e)));
+        CKI(mixed_alloc_layout(m));
         CKI(dmalloc(&m.Xb, (size_t)m.mb_pad_max * m.n_pad));
         CKI(cudaMemset(m.Xb, 0, (size_t)m.mb_pad_max * m.n_pad * sizeof(uint16_t)));
-        CKI(dmalloc(&m.sq_part, (size_t)m.n_rt * m.ldp));
-        CKI(dmalloc(&m.lin, (size_t)m.R_e * m.ldp));
         CKI(dmalloc(&m.err, 1));
         CKI(cudaMemset(m.err, 0, sizeof(int)));
     }
@@ -526,6 +543,122 @@ gwas_status gwas_reset_stats(gwas_ctx* c) {
 }
 
 void* gwas_stream(const gwas_ctx* c) { return c ? (void*)c->s_comp : nullptr; }
+
+}  // extern "C"
+
+// ============================================================================
+// Tile configuration and the autotuner.
+// ============================================================================
+extern "C" {
+
+gwas_status gwas_set_tile_cfg(gwas_ctx* c, int tile_cfg) {
+    if (!c) return GWAS_ERR_ARG;
+    if (!c->mixed) {
+        c->opts.tile_cfg = tile_cfg;
+        return GWAS_OK;
+    }
+    DeviceGuard g(c->device);
+    CK(cudaStreamSynchronize(c->s_comp));
+    MixedDev& m = c->mx;
+    const int old_R = m.R;
+    const bool old_pair = m.pair;
+    apply_tile_cfg(m, tile_cfg);
+    mixed_layout(m, c->n, m.S, m.R_e, c->opts.m_blk);
+    c->opts.tile_cfg = tile_cfg;
+    if (m.R != old_R) {
+        CK(mixed_alloc_layout(m));
+    }
+    if (c->factored && (m.R != old_R || m.pair != old_pair)) {
+        int64_t nl = 0;
+        CK(mixed_prepare(m, c->W, c->ld, c->Z, c->s_comp, &nl));
+        CK(cudaStreamSynchronize(c->s_comp));
+    }
+    return GWAS_OK;
+}
+
+gwas_status gwas_autotune(gwas_ctx* c, const int8_t* X, int64_t mb_max, int reps, gwas_tune* out) {
+    if (!c || !out) return GWAS_ERR_ARG;
+    if (!c->factored) return fail(c, GWAS_ERR_STATE, "gwas_autotune before gwas_factor");
+    if (mb_max < 1 || mb_max > c->opts.m_blk) mb_max = c->opts.m_blk;
+    if (reps < 1) reps = 3;
+    DeviceGuard g(c->device);
+    // dosages: the caller's, or synthetic ones (the timing does not depend on the values)
+    TmpDev xbuf, outbuf;
+    const int8_t* Xd = X;
+    if (!Xd) {
+        CK(cudaMalloc(&xbuf.p, (size_t)c->n * mb_max));
+        CK(launch_fill_dosages((int8_t*)xbuf.p, (int64_t)c->n * mb_max, 0x9E3779B97F4A7C15ull,
+                               c->s_comp));
+        Xd = (const int8_t*)xbuf.p;
+    }
+    const size_t bbytes = (size_t)mb_max * c->t * c->p * sizeof(double);
+    CK(cudaMalloc(&outbuf.p, bbytes + (size_t)mb_max * c->t * sizeof(double) + mb_max + 256));
+    double* bo = (double*)outbuf.p;
+    double* wo = bo + (size_t)mb_max * c->t * c->p;
+    uint8_t* so = (uint8_t*)(wo + (size_t)mb_max * c->t);
+
+    std::vector<int> cfgs;
+    if (c->mixed) {
+        for (int variant : {1 << 12, 1 << 13})
+            for (int group : {20, 40, 80, 160})
+                for (int stages : {0, 4, 6}) cfgs.push_back(variant | (group << 4) | stages);
+    } else {
+        cfgs.push_back(-1);
+    }
+    std::vector<int64_t> mbs;
+    for (int64_t mb : {(int64_t)4096, (int64_t)8192, (int64_t)16384, mb_max})
+        if (mb <= mb_max && (mbs.empty() || mbs.back() != mb)) mbs.push_back(mb);
+    std::sort(mbs.begin(), mbs.end());
+    mbs.erase(std::unique(mbs.begin(), mbs.end()), mbs.end());
+
+    const int saved_cfg = c->opts.tile_cfg;
+    const int saved_timing = c->opts.timing;
+    const gwas_stats saved_stats = c->stats;
+    c->opts.timing = 0;
+    cudaEvent_t e0 = pooled_event(c), e1 = pooled_event(c);
+    double best = 1e300;
+    int best_cfg = saved_cfg;
+    int64_t best_mb = mbs.back();
+    int tried = 0;
+    gwas_status st = GWAS_OK;
+    for (int cfg : cfgs) {
+        if ((st = gwas_set_tile_cfg(c, cfg)) != GWAS_OK) break;
+        for (int64_t mb : mbs) {
+            // one untimed launch, then `reps` timed back-to-back
+            if ((st = run_block(c, Xd, mb, bo, wo, so)) != GWAS_OK) break;
+            CK(cudaEventRecord(e0, c->s_comp));
+            for (int r = 0; r < reps && st == GWAS_OK; ++r) st = run_block(c, Xd, mb, bo, wo, so);
+            if (st != GWAS_OK) break;
+            CK(cudaEventRecord(e1, c->s_comp));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            const double per_snp = ms / (reps * (double)mb);
+            ++tried;
+            if (per_snp < best) {
+                best = per_snp;
+                best_cfg = cfg;
+                best_mb = mb;
+            }
+        }
+        if (st != GWAS_OK) break;
+    }
+    c->ev_pool.push_back(e0);
+    c->ev_pool.push_back(e1);
+    c->opts.timing = saved_timing;
+    c->stats = saved_stats;  // runs made by the tuner are not the caller's work
+    const gwas_status st2 = gwas_set_tile_cfg(c, st == GWAS_OK ? best_cfg : saved_cfg);
+    if (st != GWAS_OK) return st;
+    if (st2 != GWAS_OK) return st2;
+    gwas_status sk = gwas_sync(c, -1);
+    if (sk != GWAS_OK) return sk;
+    out->tile_cfg = best_cfg;
+    out->m_blk = best_mb;
+    out->ms_per_snp = best;
+    out->snps_per_s = 1e3 / best;
+    out->candidates = tried;
+    return GWAS_OK;
+}
 
 }  // extern "C"
 

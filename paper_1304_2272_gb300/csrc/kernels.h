@@ -171,4 +171,7 @@ cudaError_t launch_geno_bf16_batch(const BatchJob* jobs, int n_jobs, int64_t n_s
 cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, bool mixed,
                                    cudaStream_t s);
 
+// ---- utilities (util.cu) ---------------------------------------------------------------
+cudaError_t launch_fill_dosages(int8_t* X, int64_t count, uint64_t seed, cudaStream_t s);
+
 }  // namespace gwas

@@ -50,6 +50,15 @@ class gwas_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gwas_tune(ctypes.Structure):
+    _fields_ = [("tile_cfg", ctypes.c_int), ("m_blk", ctypes.c_int64),
+                ("ms_per_snp", ctypes.c_double), ("snps_per_s", ctypes.c_double),
+                ("candidates", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class GwasError(RuntimeError):
     def __init__(self, status: int, message: str, index: int = -1):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -80,6 +89,8 @@ SIGNATURES = {
     "gwas_stream": (_vp, [_ctx_p]),
     "gwas_solve_block_noalloc": (_int, [_i64, _int, _int, _vp, _i64, _vp, _vp, _vp, _vp, _vp,
                                         _i64, _vp, _vp, _vp, _vp]),
+    "gwas_set_tile_cfg": (_int, [_ctx_p, _int]),
+    "gwas_autotune": (_int, [_ctx_p, _vp, _i64, _int, ctypes.POINTER(gwas_tune)]),
     "gwas_batch_init": (_int, [_int, ctypes.POINTER(_i64), _int, _int, ctypes.POINTER(gwas_opts),
                                ctypes.POINTER(_ctx_p)]),
     "gwas_batch_factor": (_int, [_ctx_p, _int, _vp, _int, _dbl, _dbl, _vp, _vp]),
@@ -238,6 +249,18 @@ def gwas_solve_block_noalloc(n: int, p: int, t: int, Linv, ld_linv: int, XLbar, 
         stream)
     if st != GWAS_OK:
         raise GwasError(st, "gwas_solve_block_noalloc failed")
+
+
+def gwas_set_tile_cfg(ctx, tile_cfg: int) -> None:
+    _check(ctx, load().gwas_set_tile_cfg(ctx, int(tile_cfg)))
+
+
+def gwas_autotune(ctx, X=None, mb_max: int = 0, reps: int = 3) -> dict:
+    """Time the candidate tile configurations and block sizes on a factored context,
+    keep the fastest on it and return {tile_cfg, m_blk, ms_per_snp, snps_per_s, ...}."""
+    out = gwas_tune()
+    _check(ctx, load().gwas_autotune(ctx, _addr(X), int(mb_max), int(reps), ctypes.byref(out)))
+    return out.as_dict()
 
 
 # ---- batches of cohorts -------------------------------------------------------------
