@@ -5,4 +5,4 @@ checked by eye against the paper. Only ``tests/``, ``__graft_entry__.smoke()`` a
 the CPU-baseline leg of ``bench.py`` may import this package; the CUDA library and
 its binding never do, and this package imports nothing from them.
 """
-from . import exact, gls  # noqa: F401
+from . import exact, gls, reml  # noqa: F401
