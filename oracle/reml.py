@@ -25,7 +25,7 @@ import math
 
 import numpy as np
 
-from .gls import build_M, genotype_status
+from .gls import build_M, genotype_status, spd_solve
 
 
 def _inv_spd(M: np.ndarray) -> np.ndarray:
@@ -104,6 +104,8 @@ def db_dh(phi, h: float, sigma2: float, XL, Y, X, closed_form: bool = False) -> 
             continue
         Xi = np.hstack([XL, Xg[:, i:i + 1].astype(np.float64)])
         S = Xi.T @ Minv @ Xi
+        if not spd_solve(S[None], (Xi.T @ Minv @ Y)[None])[2][0]:
+            continue  # singular S_i: the SNP's outputs stay NaN, as for b_i
         B = np.linalg.solve(S, Xi.T @ Minv @ Y)          # p x t
         R = Y - Xi @ B
         if closed_form:
