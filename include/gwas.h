@@ -97,6 +97,18 @@ typedef struct {
     int candidates;      /* (tile_cfg, block size) pairs timed                            */
 } gwas_tune;
 
+/* Result of gwas_reml (REML of the null model y = X_L beta + e, e ~ N(0, M)). */
+typedef struct {
+    double loglik;      /* l = -1/2[(n-q) log 2pi + log|M| + log|X_L^T M^-1 X_L| + y^T P y]  */
+    double dl_dh;       /* dl/dh at (h, sigma2)                                           */
+    double dl_dsigma2;  /* dl/dsigma2 at (h, sigma2)                                      */
+    double sigma2_hat;  /* sigma2 maximising l at this h: sigma2 y^T P y / (n - q)         */
+    double yPy;         /* y^T P y                                                        */
+    double logdet_M;    /* log|M|                                                         */
+    double logdet_A;    /* log|X_L^T M^-1 X_L|                                            */
+    double sigma2;      /* the sigma2 the values refer to (sigma2_hat when profiled)      */
+} gwas_reml_result;
+
 /* Fill *opts with defaults: FP64, m_blk 16384, 3 limbs, default tiles, device 0,
  * no timing events, CUDA graphs on. */
 void gwas_default_opts(gwas_opts* opts);
@@ -180,6 +192,35 @@ gwas_status gwas_reset_stats(gwas_ctx* ctx);
 
 /* The context's compute stream, as a cudaStream_t cast to void*. */
 void* gwas_stream(const gwas_ctx* ctx);
+
+/*
+ * REML log-likelihood of phenotype column `pheno` and its gradient with respect to h and
+ * sigma2, for M = sigma2 (h Phi + (1 - h) I). The paper takes M as given (Section 1);
+ * this is the standard variance-component likelihood behind it, with its hand-derived
+ * adjoint: the derivative of l with respect to M is -1/2 (P - P y y^T P), P =
+ * M^-1 - M^-1 X_L (X_L^T M^-1 X_L)^-1 X_L^T M^-1, contracted with dM/dh = sigma2 (Phi - I)
+ * and dM/dsigma2 = M / sigma2. Runs gwas_factor(ctx, Phi, 1, h, sigma2, XL, Y) first, then
+ * forms M^-1 = L^-T L^-1 and the small Gram matrices of Z = M^-1 [X_L | Y] on the GPU.
+ * Phi: the FULL n x n symmetric matrix (both triangles are read), host or device. With
+ * profile != 0 every value is reported at sigma2 = sigma2_hat(h) (so dl/dh is the
+ * derivative of the profiled likelihood). Afterwards the context is ready for
+ * gwas_solve_block_grad_device at this (h, sigma2). Synchronous.
+ * Errors: as gwas_factor; GWAS_ERR_ARG (pheno out of range).
+ */
+gwas_status gwas_reml(gwas_ctx* ctx, const double* Phi, double h, double sigma2, const double* XL,
+                      const double* Y, int pheno, int profile, gwas_reml_result* out);
+
+/*
+ * gwas_solve_block_device plus db_i/dh for every SNP and phenotype: differentiating the
+ * normal equations of Eq. (1) in h gives db_i/dh = (sigma2/h) S_i^-1 X_i^T M^-2 r_i with
+ * r_i = y - X_i b_i (h > 0). The per-SNP products M^-1 x_i are recomputed from the
+ * dosages by a second pass of the FP64 block kernel with M^-1 in place of L^-1.
+ * dbdh: DEVICE double[mb * t * p], laid out like b (NaN where status != 0).
+ * Needs a GWAS_PREC_FP64 context and a preceding gwas_reml (h > 0).
+ * Errors: GWAS_ERR_STATE, GWAS_ERR_UNSUPPORTED (mixed context), GWAS_ERR_ARG, GWAS_ERR_CUDA.
+ */
+gwas_status gwas_solve_block_grad_device(gwas_ctx* ctx, const int8_t* X, int64_t mb, double* b,
+                                         double* wald, uint8_t* status, double* dbdh);
 
 /*
  * Change the kernel tile configuration of a context (see gwas_opts.tile_cfg). For a

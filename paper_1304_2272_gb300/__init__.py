@@ -32,7 +32,9 @@ from .gwas import (  # noqa: F401
     gwas_solve_block,
     gwas_solve_block_device,
     gwas_solve_block_noalloc,
+    gwas_reml,
     gwas_set_tile_cfg,
+    gwas_solve_block_grad_device,
     gwas_stream,
     gwas_sync,
     load,

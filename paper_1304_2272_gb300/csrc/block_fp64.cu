@@ -29,7 +29,7 @@ __device__ __forceinline__ void block_fp64_unit(const CohortDev& c, const int8_t
     const int tx = tid % 16, ty = tid / 16;
     const int64_t n = c.n;
     const int64_t r0 = (int64_t)rt * T64, c0 = (int64_t)ct * T64;
-    const int64_t kend = min64(n, r0 + T64);
+    const int64_t kend = c.dense ? n : min64(n, r0 + T64);
     const bool check = (rt == n_rt - 1);  // this unit reads every dosage of its SNPs
     if (tid < T64) sbad[tid] = 0;
     __syncthreads();

@@ -8,6 +8,7 @@
 // pinned host memory and the second memory region by the second device slot.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -45,7 +46,14 @@ struct gwas_ctx {
     // mixed-precision path
     bool mixed = false;
     MixedDev mx;
-    double* Z = nullptr;          // n x (q + t): L^{-T} [Xbar_L | Ybar]
+    double* Z = nullptr;          // n x (q + t): L^{-T} [Xbar_L | Ybar] = M^{-1} [X_L | Y]
+    // REML and db/dh (allocated on first use)
+    double* Phi = nullptr;        // full Phi, ld
+    double* Minv = nullptr;       // M^{-1} = L^{-T} L^{-1}, ld
+    double* part2 = nullptr;      // adjoint partials, FP64 partial layout
+    double* small = nullptr;      // G1, G2, PhiZ and scalars
+    bool grad_ready = false;
+    double grad_h = 0.0, grad_s2 = 0.0;
     int num_sms = 0;
     cudaStream_t s_comp = nullptr, s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
@@ -192,6 +200,7 @@ void free_all(gwas_ctx* c) {
     cudaFree(c->L); cudaFree(c->W); cudaFree(c->Dinv); cudaFree(c->XLbar); cudaFree(c->Ybar);
     cudaFree(c->S_TL); cudaFree(c->bbar_T); cudaFree(c->d_info); cudaFree(c->part);
     cudaFree(c->bad);
+    cudaFree(c->Phi); cudaFree(c->Minv); cudaFree(c->part2); cudaFree(c->small);
     cudaFree(c->Z); cudaFree(c->mx.WL); cudaFree(c->mx.bits); cudaFree(c->mx.E);
     cudaFree(c->mx.Xb); cudaFree(c->mx.sq_part); cudaFree(c->mx.lin); cudaFree(c->mx.err);
     for (int s = 0; s < 2; ++s) {
@@ -306,6 +315,7 @@ gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double 
         return fail(c, GWAS_ERR_ARG, "gwas_factor: need 0 <= h <= 1 and sigma2 > 0");
     DeviceGuard g(c->device);
     c->factored = false;
+    c->grad_ready = false;
     c->err_index = -1;
     const int64_t n = c->n, ld = c->ld;
     cudaStream_t s = c->s_comp;
@@ -545,6 +555,136 @@ gwas_status gwas_reset_stats(gwas_ctx* c) {
 void* gwas_stream(const gwas_ctx* c) { return c ? (void*)c->s_comp : nullptr; }
 
 }  // extern "C"
+
+// ============================================================================
+// REML log-likelihood, its gradient, and db_i/dh.
+// ============================================================================
+namespace {
+
+// Layout of c->small: G1 and G2 ((q+t)^2 each), PhiZ (n x (q+t)), then scalars.
+struct SmallLayout {
+    int64_t nz, g1, g2, phiz, yy, logdet, frob, fpart, out, total;
+    explicit SmallLayout(const gwas_ctx* c) {
+        nz = c->q + c->t;
+        g1 = 0;
+        g2 = g1 + nz * nz;
+        phiz = g2 + nz * nz;
+        yy = phiz + c->n * nz;
+        logdet = yy + 1;
+        frob = logdet + 1;
+        fpart = frob + 2;
+        out = fpart + 2 * ceil_div(c->n, 256);
+        total = out + 8;
+    }
+};
+
+}  // namespace
+
+extern "C" gwas_status gwas_reml(gwas_ctx* c, const double* Phi, double h, double sigma2,
+                                 const double* XL, const double* Y, int pheno, int profile,
+                                 gwas_reml_result* out) {
+    if (!c || !out) return GWAS_ERR_ARG;
+    if (!Phi || !XL || !Y) return fail(c, GWAS_ERR_ARG, "gwas_reml: NULL input");
+    if (pheno < 0 || pheno >= c->t) return fail(c, GWAS_ERR_ARG, "gwas_reml: phenotype out of range");
+    gwas_status st = gwas_factor(c, Phi, 1, h, sigma2, XL, Y);
+    if (st != GWAS_OK) return st;
+    DeviceGuard g(c->device);
+    const int64_t n = c->n, ld = c->ld, nz = c->q + c->t;
+    cudaStream_t s = c->s_comp;
+    const SmallLayout sl(c);
+    if (!c->Phi) CK(dmalloc(&c->Phi, (size_t)ld * ld));
+    if (!c->Minv) CK(dmalloc(&c->Minv, (size_t)ld * ld));
+    if (!c->Z) CK(dmalloc(&c->Z, (size_t)n * nz));
+    if (!c->small) CK(dmalloc(&c->small, (size_t)sl.total));
+    double* sm = c->small;
+    // the full Phi (the Frobenius product reads both triangles)
+    CK(cudaMemcpy2DAsync(c->Phi, ld * sizeof(double), Phi, n * sizeof(double), n * sizeof(double), n,
+                         cudaMemcpyDefault, s));
+    // M^-1 = W^T W (W = L^-1 lower triangular)
+    GemmF64 mi;
+    mi.M = n; mi.N = n; mi.K = n; mi.A = c->W; mi.lda = ld; mi.transA = true; mi.a_upper = true;
+    mi.B = c->W; mi.ldb = ld; mi.b_lower = true; mi.C = c->Minv; mi.ldc = ld;
+    CK(gemm_f64(mi, s));
+    if (!c->mixed) {  // the mixed factor already formed Z
+        GemmF64 z;
+        z.M = n; z.N = c->q; z.K = n; z.A = c->W; z.lda = ld; z.transA = true; z.a_upper = true;
+        z.B = c->XLbar; z.ldb = n; z.C = c->Z; z.ldc = n;
+        CK(gemm_f64(z, s));
+        GemmF64 zy = z;
+        zy.N = c->t; zy.B = c->Ybar; zy.C = c->Z + (size_t)n * c->q;
+        CK(gemm_f64(zy, s));
+    }
+    // Phi Z, G1 = Z^T Z, G2 = Z^T Phi Z, |ybar_j|^2
+    GemmF64 pz;
+    pz.M = n; pz.N = nz; pz.K = n; pz.A = c->Phi; pz.lda = ld; pz.B = c->Z; pz.ldb = n;
+    pz.C = sm + sl.phiz; pz.ldc = n;
+    CK(gemm_f64(pz, s));
+    GemmF64 g1;
+    g1.M = nz; g1.N = nz; g1.K = n; g1.A = c->Z; g1.lda = n; g1.transA = true; g1.B = c->Z;
+    g1.ldb = n; g1.C = sm + sl.g1; g1.ldc = nz;
+    CK(gemm_f64(g1, s));
+    GemmF64 g2 = g1;
+    g2.B = sm + sl.phiz; g2.C = sm + sl.g2;
+    CK(gemm_f64(g2, s));
+    GemmF64 yy;
+    yy.M = 1; yy.N = 1; yy.K = n; yy.A = c->Ybar + (size_t)n * pheno; yy.lda = n; yy.transA = true;
+    yy.B = c->Ybar + (size_t)n * pheno; yy.ldb = n; yy.C = sm + sl.yy; yy.ldc = 1;
+    CK(gemm_f64(yy, s));
+    CK(launch_logdiag(c->L, ld, n, sm + sl.logdet, s));
+    CK(launch_frob_trace(c->Minv, c->Phi, ld, n, sm + sl.fpart, sm + sl.frob, s));
+    RemlDev r;
+    r.n = n; r.q = c->q; r.t = c->t; r.j = pheno; r.h = h; r.sigma2 = sigma2;
+    r.profile = profile ? 1 : 0;
+    r.S_TL = c->S_TL; r.bbar_T = c->bbar_T; r.G1 = sm + sl.g1; r.G2 = sm + sl.g2;
+    r.yy = sm + sl.yy; r.logdet_M = sm + sl.logdet; r.frob = sm + sl.frob; r.out = sm + sl.out;
+    CK(launch_reml_assemble(r, s));
+    double host[8];
+    CK(cudaMemcpyAsync(host, sm + sl.out, sizeof host, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out->loglik = host[0];
+    out->dl_dh = host[1];
+    out->dl_dsigma2 = host[2];
+    out->sigma2_hat = host[3];
+    out->yPy = host[4];
+    out->logdet_M = host[5];
+    out->logdet_A = host[6];
+    out->sigma2 = host[7];
+    c->grad_ready = true;
+    c->grad_h = h;
+    c->grad_s2 = sigma2;
+    if (!std::isfinite(host[0])) return fail(c, GWAS_ERR_NOT_SPD, "gwas_reml: X_L^T M^-1 X_L is not SPD");
+    return GWAS_OK;
+}
+
+extern "C" gwas_status gwas_solve_block_grad_device(gwas_ctx* c, const int8_t* X, int64_t mb,
+                                                    double* b, double* wald, uint8_t* status,
+                                                    double* dbdh) {
+    gwas_status st = check_block_args(c, X, mb, b, status);
+    if (st != GWAS_OK) return st;
+    if (!dbdh) return fail(c, GWAS_ERR_ARG, "gwas_solve_block_grad_device: NULL dbdh");
+    if (c->mixed) return fail(c, GWAS_ERR_UNSUPPORTED, "db/dh is built for GWAS_PREC_FP64 contexts");
+    if (!c->grad_ready) return fail(c, GWAS_ERR_STATE, "db/dh needs a gwas_reml at the current h");
+    if (!(c->grad_h > 0.0)) return fail(c, GWAS_ERR_ARG, "db/dh needs h > 0");
+    DeviceGuard g(c->device);
+    const int64_t n = c->n;
+    const int n_tiles = (int)ceil_div(n, T64);
+    if (!c->part2) CK(dmalloc(&c->part2, (size_t)n_tiles * (c->q + 1 + c->t) * c->ldp));
+    // forward: b_i, Wald, status, and the partials of S_i and bbar_i
+    if ((st = run_block(c, X, mb, b, wald, status)) != GWAS_OK) return st;
+    // adjoint: the same kernel with M^-1 (dense) and Z = M^-1 [X_L | Y]
+    CohortDev adj = cohort_view(c);
+    adj.W = c->Minv;
+    adj.ldw = c->ld;
+    adj.dense = true;
+    adj.XLbar = c->Z;
+    adj.Ybar = c->Z + (size_t)n * c->q;
+    CK(launch_block_fp64(adj, X, n, mb, c->part2, c->ldp, c->bad, c->s_comp));
+    const SmallLayout sl(c);
+    CK(launch_dbdh(cohort_view(c), c->part, c->part2, c->ldp, n_tiles, c->small + sl.g1,
+                   c->grad_s2 / c->grad_h, c->bad, mb, dbdh, c->s_comp));
+    c->stats.kernel_launches += 2;
+    return GWAS_OK;
+}
 
 // ============================================================================
 // Tile configuration and the autotuner.

@@ -55,6 +55,7 @@ struct CohortDev {
     const double* Ybar = nullptr;  // n x t, ld = n
     const double* S_TL = nullptr;  // q x q, ld = q
     const double* bbar_T = nullptr;// q x t, ld = q
+    bool dense = false;            // W is a full (not lower-triangular) matrix
 };
 
 // Number of per-SNP reduction values: q (S_BL) + 1 (S_BR) + t (bbar_B).
@@ -170,6 +171,39 @@ cudaError_t launch_geno_bf16_batch(const BatchJob* jobs, int n_jobs, int64_t n_s
                                    cudaStream_t s);
 cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, bool mixed,
                                    cudaStream_t s);
+
+// ---- REML and db/dh (reml.cu) -----------------------------------------------------------
+
+// Sum of log L_ii (ld = ldl) into *out (one block, fixed order).
+cudaError_t launch_logdiag(const double* L, int64_t ldl, int64_t n, double* out, cudaStream_t s);
+// out[0] = sum_ij A_ij B_ij, out[1] = sum_i A_ii for n x n column-major A, B (ld); the
+// partial sums use part[0 .. 2*ceil(n/256)) and are added in a fixed order.
+cudaError_t launch_frob_trace(const double* A, const double* B, int64_t ld, int64_t n,
+                              double* part, double* out, cudaStream_t s);
+
+// Inputs of the REML assembly (all device pointers; column-major, small).
+struct RemlDev {
+    int64_t n = 0;
+    int q = 0, t = 0, j = 0;       // phenotype column j of Y
+    double h = 0, sigma2 = 0;
+    int profile = 0;               // 1: evaluate at the profiled sigma^2
+    const double* S_TL = nullptr;  // q x q
+    const double* bbar_T = nullptr;// q x t
+    const double* G1 = nullptr;    // Zc^T Zc,      (q+t) x (q+t), Zc = M^-1 [X_L | Y]
+    const double* G2 = nullptr;    // Zc^T Phi Zc,  (q+t) x (q+t)
+    const double* yy = nullptr;    // ybar_j^T ybar_j
+    const double* logdet_M = nullptr;
+    const double* frob = nullptr;  // [<M^-1, Phi>, tr M^-1]
+    double* out = nullptr;         // 8 doubles, see gwas_reml_result
+};
+cudaError_t launch_reml_assemble(const RemlDev& r, cudaStream_t s);
+
+// db_i/dh from the forward partials (S_i, bbar_i) and the adjoint partials
+// (g_iL = X_L^T M^-2 x_i, g_ii = |M^-1 x_i|^2, g_iy = Y^T M^-2 x_i), both in the FP64
+// partial layout, and the Gram matrix G1 = Zc^T Zc. scale = sigma2 / h.
+cudaError_t launch_dbdh(const CohortDev& c, const double* part_fwd, const double* part_adj,
+                        int64_t ldp, int n_tiles, const double* G1, double scale,
+                        const uint8_t* bad, int64_t mb, double* dbdh, cudaStream_t s);
 
 // ---- utilities (util.cu) ---------------------------------------------------------------
 cudaError_t launch_fill_dosages(int8_t* X, int64_t count, uint64_t seed, cudaStream_t s);

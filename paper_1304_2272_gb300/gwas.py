@@ -59,6 +59,14 @@ class gwas_tune(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class gwas_reml_result(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("loglik", "dl_dh", "dl_dsigma2", "sigma2_hat",
+                                                "yPy", "logdet_M", "logdet_A", "sigma2")]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class GwasError(RuntimeError):
     def __init__(self, status: int, message: str, index: int = -1):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
@@ -90,6 +98,9 @@ SIGNATURES = {
     "gwas_solve_block_noalloc": (_int, [_i64, _int, _int, _vp, _i64, _vp, _vp, _vp, _vp, _vp,
                                         _i64, _vp, _vp, _vp, _vp]),
     "gwas_set_tile_cfg": (_int, [_ctx_p, _int]),
+    "gwas_reml": (_int, [_ctx_p, _vp, _dbl, _dbl, _vp, _vp, _int, _int,
+                         ctypes.POINTER(gwas_reml_result)]),
+    "gwas_solve_block_grad_device": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp, _vp]),
     "gwas_autotune": (_int, [_ctx_p, _vp, _i64, _int, ctypes.POINTER(gwas_tune)]),
     "gwas_batch_init": (_int, [_int, ctypes.POINTER(_i64), _int, _int, ctypes.POINTER(gwas_opts),
                                ctypes.POINTER(_ctx_p)]),
@@ -249,6 +260,22 @@ def gwas_solve_block_noalloc(n: int, p: int, t: int, Linv, ld_linv: int, XLbar, 
         stream)
     if st != GWAS_OK:
         raise GwasError(st, "gwas_solve_block_noalloc failed")
+
+
+def gwas_reml(ctx, Phi, h: float, sigma2: float, XL, Y, pheno: int = 0,
+              profile: bool = False) -> dict:
+    """REML log-likelihood and its gradient (see include/gwas.h); Phi is the full matrix."""
+    for a, nm in ((Phi, "Phi"), (XL, "XL"), (Y, "Y")):
+        _require(a, np.float64, nm)
+    out = gwas_reml_result()
+    _check(ctx, load().gwas_reml(ctx, _addr(Phi), float(h), float(sigma2), _addr(XL), _addr(Y),
+                                 int(pheno), int(bool(profile)), ctypes.byref(out)))
+    return out.as_dict()
+
+
+def gwas_solve_block_grad_device(ctx, X, mb: int, b, wald, status, dbdh) -> None:
+    _check(ctx, load().gwas_solve_block_grad_device(ctx, _addr(X), int(mb), _addr(b), _addr(wald),
+                                                    _addr(status), _addr(dbdh)))
 
 
 def gwas_set_tile_cfg(ctx, tile_cfg: int) -> None:

@@ -1,0 +1,116 @@
+"""REML fitting of h through the library's hand-written adjoint (marshalling only).
+
+``REMLFunction`` is a ``torch.autograd.Function`` whose forward calls ``gwas_reml`` (FP64
+Cholesky, L^-1 and M^-1 on the GPU) and whose backward returns the adjoint gradient the
+library computed with it, so the REML log-likelihood can be used like any other torch
+objective. ``fit_h`` maximises the profiled likelihood (sigma^2 profiled out) by a
+safeguarded secant iteration on its derivative dl/dh, starting from h0.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import gwas
+
+
+class REMLEngine:
+    """Holds a context and the cohort's inputs for repeated REML evaluations."""
+
+    def __init__(self, Phi, XL, Y, pheno: int = 0, **opts):
+        self.Phi = np.asfortranarray(np.asarray(Phi, dtype=np.float64))
+        self.XL = np.asfortranarray(np.asarray(XL, dtype=np.float64))
+        n = self.Phi.shape[0]
+        self.Y = np.asfortranarray(np.asarray(Y, dtype=np.float64).reshape(n, -1))
+        self.n, self.q, self.t = n, self.XL.shape[1], self.Y.shape[1]
+        self.pheno = pheno
+        self.ctx = gwas.gwas_init(n, self.q + 1, self.t, **opts)
+        self.evals = 0
+
+    def eval(self, h: float, sigma2: float, profile: bool = False) -> dict:
+        self.evals += 1
+        return gwas.gwas_reml(self.ctx, self.Phi, h, sigma2, self.XL, self.Y, self.pheno, profile)
+
+    def close(self):
+        if self.ctx:
+            gwas.gwas_finalize(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _make_function():
+    import torch
+
+    class REMLFunction(torch.autograd.Function):
+        """l(h, sigma^2) with its analytic gradient from the library."""
+
+        @staticmethod
+        def forward(ctx, h, sigma2, engine):
+            r = engine.eval(float(h), float(sigma2))
+            ctx.save_for_backward(torch.tensor([r["dl_dh"], r["dl_dsigma2"]], dtype=torch.float64))
+            return torch.tensor(r["loglik"], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g,) = ctx.saved_tensors
+            return grad_out * g[0], grad_out * g[1], None
+
+    return REMLFunction
+
+
+REMLFunction = None
+
+
+def reml_loglik(h, sigma2, engine):
+    """Differentiable REML log-likelihood (torch tensors h, sigma2 of dtype float64)."""
+    global REMLFunction
+    if REMLFunction is None:
+        REMLFunction = _make_function()
+    return REMLFunction.apply(h, sigma2, engine)
+
+
+def fit_h(engine: REMLEngine, h0: float = 0.1, lo: float = 1e-4, hi: float = 1 - 1e-4,
+          tol: float = 1e-10, max_iter: int = 60) -> dict:
+    """Maximise the profiled REML likelihood in h from h0 using dl/dh (gradient-based).
+
+    Secant steps on g(h) = dl_p/dh, kept inside a bracket [a, b] with g(a) > 0 > g(b)
+    once one is found (bisection when a secant step leaves it)."""
+    def g(h):
+        return engine.eval(h, 1.0, profile=True)["dl_dh"]
+
+    h_prev, g_prev = h0, g(h0)
+    a, b = (lo, hi)
+    ga, gb = None, None
+    if g_prev > 0:
+        a, ga = h0, g_prev
+    else:
+        b, gb = h0, g_prev
+    # first step: move along the gradient until the sign changes (bracket)
+    step = 0.05 if g_prev > 0 else -0.05
+    h = min(max(h0 + step, lo), hi)
+    history = [(h0, g_prev)]
+    for _ in range(max_iter):
+        gh = g(h)
+        history.append((h, gh))
+        if gh > 0:
+            a, ga = h, gh
+        else:
+            b, gb = h, gh
+        if abs(h - h_prev) < tol or gh == 0.0:
+            break
+        if ga is not None and gb is not None:
+            cand = h - gh * (h - h_prev) / (gh - g_prev) if gh != g_prev else 0.5 * (a + b)
+            if not (min(a, b) < cand < max(a, b)):
+                cand = 0.5 * (a + b)
+        else:
+            cand = h + (h - h_prev) * 2.0  # still looking for a sign change
+            cand = min(max(cand, lo), hi)
+        h_prev, g_prev = h, gh
+        h = cand
+    r = engine.eval(h, 1.0, profile=True)
+    return {"h": h, "sigma2": r["sigma2_hat"], "loglik": r["loglik"], "dl_dh": r["dl_dh"],
+            "evals": engine.evals, "history": history}
