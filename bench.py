@@ -53,6 +53,9 @@ def parse():
                     help="SNPs per cohort in the mixed batched leg")
     ap.add_argument("--batch-snps-fp64", type=int, default=2048,
                     help="SNPs per cohort per step in the FP64 batched leg")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the REML-fit and db/dh leg (n=10000, FP64)")
+    ap.add_argument("--adjoint-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -404,6 +407,63 @@ def measure_batch(args, env, precision, snps, steps, warmup):
     return res
 
 
+def measure_adjoint(args, env, steps, warmup):
+    """REML fit of h from h0 = 0.1 (profiled sigma^2, gradient from the library's
+    adjoint) and the gradient pass: b_i and db_i/dh for blocks of m_blk SNPs, n = 10,000,
+    FP64 (forward L^-1 x_i plus the recomputed M^-1 x_i of the adjoint)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1304_2272_gb300 import gwas
+    from paper_1304_2272_gb300.reml import REMLEngine, fit_h
+
+    rank, world, local, dev = env
+    n, mb, t, p = args.n, args.m_blk, 1, 4
+    c = synth.make_cohort(0, n, t=t, h=0.4, device=dev)
+    e = REMLEngine(c.phi, c.XL, c.Y, m_blk=mb, device=local, timing=1)
+    t0 = time.perf_counter()
+    fit = fit_h(e, h0=0.1)
+    fit_s = time.perf_counter() - t0
+    # the gradient pass at the fitted h
+    r = e.eval(fit["h"], fit["sigma2"])
+    X = [synth.genotypes_torch(900 + 10 * rank + s, n, mb, dev) for s in range(2)]
+    b = torch.empty((mb, t, p), dtype=torch.float64, device=dev)
+    st = torch.empty(mb, dtype=torch.uint8, device=dev)
+    d = torch.empty((mb, t, p), dtype=torch.float64, device=dev)
+    stream = torch.cuda.ExternalStream(gwas.gwas_stream(e.ctx), device=dev)
+    torch.cuda.synchronize()
+    for s in range(warmup):
+        gwas.gwas_solve_block_grad_device(e.ctx, X[s % 2], mb, b, None, st, d)
+    gwas.gwas_sync(e.ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    for s in range(steps):
+        gwas.gwas_solve_block_grad_device(e.ctx, X[s % 2], mb, b, None, st, d)
+    ev1.record(stream)
+    gwas.gwas_sync(e.ctx)
+    clk = clocks.stop()
+    el_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([el_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        el_ms = float(tt.item())
+    ok = int((st == 0).sum().item())
+    e.close()
+    q = p - 1
+    work = (n * (n + 1) + 2.0 * n * n + 4.0 * n * (q + 1 + t)) * mb * steps
+    return {"n": n, "m_blk": mb, "steps": steps, "value": world * steps * mb / (el_ms / 1e3),
+            "unit": "SNP/s (b_i and db_i/dh)", "ms_per_step": el_ms / steps,
+            "fp64_tflops": work / (el_ms / 1e3) / 1e12,
+            "reml_fit": {"h0": 0.1, "h": fit["h"], "sigma2": fit["sigma2"], "true_h": 0.4,
+                         "loglik": fit["loglik"], "dl_dh": fit["dl_dh"], "evals": fit["evals"],
+                         "seconds": round(fit_s, 2)},
+            "status_ok": ok, "clocks": clk}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -431,6 +491,9 @@ def main():
                           "setup_ms": r["setup_ms"], "roofline": r["roofline"],
                           "e2e": r["e2e"], "clocks": r["clocks"], "autotune": r["autotune"],
                           "gpu_launches": r["gpu_launches"]})
+    adjoint = None
+    if args.precision == "fp64" and not args.no_adjoint:
+        adjoint = measure_adjoint(args, env, args.adjoint_steps, 1)
     batched = []
     if args.precision == "fp64" and not args.no_batch:
         batched.append(measure_batch(args, env, "mixed", args.batch_snps, 5, 2))
@@ -448,6 +511,8 @@ def main():
             line["mixed"] = mixed
         if batched:
             line["batched"] = batched
+        if adjoint:
+            line["adjoint"] = adjoint
         if not args.no_cpu_baseline:
             Xh = np.asfortranarray(pool[0][:4096].cpu().numpy().T)
             line["cpu_baseline"] = cpu_baseline(cohort, Xh, args.cpu_seconds)
