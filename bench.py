@@ -46,6 +46,8 @@ def parse():
                     help="skip the mixed-precision legs (n and n=30000) of an FP64 run")
     ap.add_argument("--mixed-steps", type=int, default=240)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (mixed legs)")
+    ap.add_argument("--tile-cfg", type=int, default=None,
+                    help="fixed tile configuration for the mixed legs (skips the autotuner)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-cohorts legs (48 cohorts, 16 phenotypes)")
     ap.add_argument("--batch-cohorts", type=int, default=48)
@@ -136,6 +138,31 @@ def bf16_flops_per_snp(n: int, q: int, t: int, limbs: int) -> float:
     """Algorithmic BF16 tensor flops per SNP of the limb path: `limbs` lower-triangular
     products (n(n+1) flop each) plus the `limbs` x (q+t) linear rows (2n flop each)."""
     return limbs * (n * (n + 1) + 2.0 * n * (q + t))
+
+
+# DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the bench's own launch shape), valid only
+# while the kernel source is the one captured (first 16 hex digits of its sha256).
+TRAFFIC = {
+    "k_block_fp64": {"file": "block_fp64.cu", "sha": "17f101cf32e7945d", "n": 10000,
+                     "m_blk": 16384, "bytes": 8830753024 + 101610496},
+    "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "8fa211033a84d593", "n": 10000,
+                         "m_blk": 16384, "tile_cfg": 5376, "bytes": 4220531712 + 18793984},
+}
+
+
+def traffic_for(kernel: str, n: int, m_blk: int):
+    import hashlib
+    rec = TRAFFIC.get(kernel)
+    if not rec or rec["n"] != n or rec["m_blk"] != m_blk:
+        return None
+    path = os.path.join(ROOT, "paper_1304_2272_gb300", "csrc", rec["file"])
+    try:
+        with open(path, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["bytes"] if sha == rec["sha"] else None
 
 
 def measured_peaks() -> dict:
@@ -245,7 +272,10 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
                      cohort.XL, cohort.Y)
     setup_ms = gwas.gwas_get_stats(ctx)["factor_ms"]
     tune = None
-    if precision == "mixed" and not args.no_tune:
+    if precision == "mixed" and args.tile_cfg is not None:
+        gwas.gwas_set_tile_cfg(ctx, args.tile_cfg)
+        tune = {"tile_cfg": args.tile_cfg, "fixed": True}
+    elif precision == "mixed" and not args.no_tune:
         from paper_1304_2272_gb300 import autotune
         t0 = time.perf_counter()
         tune = autotune.tuned_tile_cfg(ctx, n, p, t, prec, limbs, mb)
@@ -316,7 +346,8 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
         peak, how = fp64_peak_tflops(clk.get("sm_mhz"))
         achieved = flops_per_snp(n, q, t) * mb / (launch_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_block_fp64",
+                "frac": achieved / peak, "traffic": traffic_for("k_block_fp64", n, mb),
+                "kernel": "k_block_fp64",
                 "launch_ms": launch_ms, "peak_source": how + " (derived, of nominal)"}
     else:
         pk = measured_peaks()
@@ -327,7 +358,9 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
         peak = peak or 1700.0
         achieved = bf16_flops_per_snp(n, q, t, limbs) * mb / (launch_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": f"k_block_mixed<{limbs}>",
+                "frac": achieved / peak,
+                "traffic": traffic_for(f"k_block_mixed<{limbs}>", n, mb),
+                "kernel": f"k_block_mixed<{limbs}>",
                 "launch_ms": launch_ms, "peak_source": src,
                 "fp64_equivalent_tflops": flops_per_snp(n, q, t) * value / world / 1e12}
     res = {"value": value, "ms_per_step": el_ms / steps, "steps": steps, "warmup": warmup,
