@@ -30,6 +30,14 @@ UNIT = "SNP/s"
 
 
 def parse():
+    return _parser().parse_args()
+
+
+def parse_args_for_test(argv):
+    return _parser().parse_args(argv)
+
+
+def _parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -59,7 +67,7 @@ def parse():
                     help="skip the REML-fit and db/dh leg (n=10000, FP64)")
     ap.add_argument("--adjoint-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    return ap.parse_args()
+    return ap
 
 
 def dist_env():
@@ -126,6 +134,24 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The largest value of x over the ranks of the process group (x itself for one rank):
+    every leg reports the slowest rank's time, as the whole job waits for it."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(units_per_rank: float, world: int, elapsed_s: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time
+    (replicas: each rank works on its own SNP blocks, no exchange on the data path)."""
+    return world * units_per_rank / elapsed_s
 
 
 def flops_per_snp(n: int, q: int, t: int) -> float:
@@ -292,13 +318,6 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if world > 1:
-            tt = torch.tensor([x], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            x = float(tt.item())
-        return x
-
     # ---- device-resident timing (value) --------------------------------------
     for s in range(warmup):
         gwas.gwas_solve_block_device(ctx, pool[s % args.pool], mb, b, w, st)
@@ -315,10 +334,10 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    el_ms = max_over_ranks(ev0.elapsed_time(ev1))
+    el_ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     stats = gwas.gwas_get_stats(ctx)
     status_ok = int((st == 0).sum().item())
-    value = world * steps * mb / (el_ms / 1e3)
+    value = job_rate(steps * mb, world, el_ms / 1e3)
 
     # ---- end to end from pinned host memory (e2e) ------------------------------
     e2e = None
@@ -336,8 +355,8 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
             gwas.gwas_solve_block(ctx, hpool[s % 2], mb, hb, hw, hs)
         gwas.gwas_sync(ctx)
         barrier()
-        e2e_s = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": world * steps * mb / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_rate(steps * mb, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": n * mb, "d2h_bytes_per_step": mb * (t * p * 8 + t * 8 + 1)}
 
     q = p - 1
@@ -417,11 +436,7 @@ def measure_batch(args, env, precision, snps, steps, warmup):
     ev1.record(stream)
     gwas.gwas_batch_sync(b)
     clk = clocks.stop()
-    el_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([el_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        el_ms = float(tt.item())
+    el_ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     st = gwas.gwas_batch_get_stats(b)
     ok = int(sum(int((x == 0).sum().item()) for x in so))
     gwas.gwas_batch_finalize(b)
@@ -479,11 +494,7 @@ def measure_adjoint(args, env, steps, warmup):
     ev1.record(stream)
     gwas.gwas_sync(e.ctx)
     clk = clocks.stop()
-    el_ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([el_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        el_ms = float(tt.item())
+    el_ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     ok = int((st == 0).sum().item())
     e.close()
     q = p - 1

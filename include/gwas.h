@@ -292,6 +292,15 @@ const char* gwas_batch_last_error(const gwas_batch* b);
 void* gwas_batch_stream(const gwas_batch* b);
 
 /*
+ * Self-test of the bounded waits used by the pipeline kernels (the paper has no
+ * counterpart): one GPU thread waits on an mbarrier phase that never completes, with a
+ * limit of timeout_ms (1..10000). Returns GWAS_ERR_TIMEOUT when the wait gave up as it
+ * must (the expected outcome; *waited_ms = device time spent waiting), GWAS_OK if it
+ * completed, GWAS_ERR_CUDA/GWAS_ERR_ARG otherwise. The device stays usable afterwards.
+ */
+gwas_status gwas_selftest_wait(int device, int timeout_ms, double* waited_ms);
+
+/*
  * Allocation-free FP64 block solve. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they call in -- their
  * GPU memory is already fully reserved by another allocator (a framework's caching

@@ -98,6 +98,7 @@ SIGNATURES = {
     "gwas_solve_block_noalloc": (_int, [_i64, _int, _int, _vp, _i64, _vp, _vp, _vp, _vp, _vp,
                                         _i64, _vp, _vp, _vp, _vp]),
     "gwas_set_tile_cfg": (_int, [_ctx_p, _int]),
+    "gwas_selftest_wait": (_int, [_int, _int, ctypes.POINTER(_dbl)]),
     "gwas_reml": (_int, [_ctx_p, _vp, _dbl, _dbl, _vp, _vp, _int, _int,
                          ctypes.POINTER(gwas_reml_result)]),
     "gwas_solve_block_grad_device": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp, _vp]),
@@ -276,6 +277,13 @@ def gwas_reml(ctx, Phi, h: float, sigma2: float, XL, Y, pheno: int = 0,
 def gwas_solve_block_grad_device(ctx, X, mb: int, b, wald, status, dbdh) -> None:
     _check(ctx, load().gwas_solve_block_grad_device(ctx, _addr(X), int(mb), _addr(b), _addr(wald),
                                                     _addr(status), _addr(dbdh)))
+
+
+def gwas_selftest_wait(device: int = 0, timeout_ms: int = 200) -> tuple[int, float]:
+    """Run the bounded-wait self-test; returns (status, waited_ms)."""
+    w = _dbl(0.0)
+    st = load().gwas_selftest_wait(int(device), int(timeout_ms), ctypes.byref(w))
+    return st, w.value
 
 
 def gwas_set_tile_cfg(ctx, tile_cfg: int) -> None:
