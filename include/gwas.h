@@ -67,8 +67,10 @@ typedef struct {
     int tile_cfg;  /* -1 = library default; for GWAS_PREC_MIXED, bits 0-3 = pipeline
                       stages (2..8, 0 = as many as fit), bits 4-11 = MB of BF16 dosages
                       per L2 group of SNP tiles (0 = 40), bit 12 = force one CTA per
-                      128-SNP tile, bit 13 = force CTA pairs (cta_group::2); by default
-                      the variant with the taller limb tile is used                     */
+                      128-SNP tile, bit 13 = force CTA pairs (cta_group::2), bit 14 = keep
+                      the linear rows in a separate tile instead of fusing them into
+                      the spare N of every limb tile; by default the linear rows are
+                      fused where they fit and the taller UMMA N wins                    */
     int device;    /* CUDA device ordinal                                             */
     int timing;    /* 1 = record CUDA events around each dominant-kernel launch       */
     int use_graph; /* batches: 1 = capture the batched solve in a CUDA graph and
@@ -233,7 +235,7 @@ gwas_status gwas_set_tile_cfg(gwas_ctx* ctx, int tile_cfg);
 /*
  * Autotuner: on a factored context, time the whole block path (dosage conversion,
  * dominant kernel, p x p solves) for every candidate tile configuration (mixed: one
- * CTA or CTA pairs, pipeline stages, L2 group size) and block size (4096, 8192, 16384
+ * CTA or CTA pairs, fused or separate linear rows, pipeline stages, L2 group size) and block size (4096, 8192, 16384
  * and mb_max SNPs, up to m_blk) with CUDA events, `reps` launches each; keep the
  * fastest configuration on the context and report it in *out. X: n x mb_max DEVICE
  * dosages to time with, or NULL for synthetic ones (timing does not depend on the

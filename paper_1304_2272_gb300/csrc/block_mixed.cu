@@ -61,9 +61,10 @@ struct MixedArgs {
 };
 
 // Unit u -> (rt, ct) inside one cohort. Groups of `group` SNP tiles; inside a group the
-// linear tile of every SNP tile comes first, then row tiles from the heaviest down.
+// linear tile of every SNP tile comes first (when there is one), then row tiles from the
+// heaviest down.
 __device__ __forceinline__ void decode_unit(const CohortMx& c, int u, int& rt, int& ct) {
-    const int levels = c.n_rt + 1;
+    const int levels = c.n_rt + c.extra;
     const int per_group = c.group * levels;
     const int g = u / per_group;
     const int w = u - g * per_group;
@@ -71,7 +72,8 @@ __device__ __forceinline__ void decode_unit(const CohortMx& c, int u, int& rt, i
     const int gsize = (g == ngroups - 1) ? c.n_ct - g * c.group : c.group;
     const int level = w / gsize;
     ct = g * c.group + (w - level * gsize);
-    rt = (level == 0) ? (int)mx::EXTRA : c.n_rt - level;
+    if (c.extra) rt = (level == 0) ? (int)mx::EXTRA : c.n_rt - level;
+    else rt = c.n_rt - 1 - level;
 }
 
 __device__ __forceinline__ void record_error(int* err, volatile int* abort_flag, int code) {
@@ -117,9 +119,10 @@ struct SrcBatch {
 };
 
 // Epilogue of one unit for the SNP held in TMEM lane `tb` (one thread = one SNP):
-// row tiles -> sum over the tile's R rows of xbar^2, exact in 128-bit integers;
+// row tiles -> sum over the tile's R rows of xbar^2, exact in 128-bit integers, plus (when
+// NT > R*S) the tile's partial linear reductions from the fused columns;
 // the linear tile -> the q + t linear reductions.
-template <int S, int R>
+template <int S, int R, int NT>
 __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32_t tb, int rt,
                                               int64_t snp) {
     using namespace tc;
@@ -146,6 +149,22 @@ __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32
         const double lo = (double)(unsigned long long)acc;
         const double val = ldexp(fma(hi, 18446744073709551616.0, lo), 2 * (a.E_w[rt] - shift0));
         if (snp < a.mb) a.sq_part[(int64_t)rt * a.ldp + snp] = val;
+        if (NT > R * S) {
+            // fused linear rows: Z limbs of this tile's k-range, one partial per (rt, j)
+#pragma unroll 1
+            for (int j = 0; j < R_e; ++j) {
+                long long T = 0;
+#pragma unroll
+                for (int l = 0; l < S; ++l) {
+                    uint32_t x;
+                    tmem_ld1(tb + (uint32_t)(R * S + l * R_e + j), x);
+                    tmem_wait_ld();
+                    T = T * 512 + (long long)__float2int_rn(__uint_as_float(x));
+                }
+                const int64_t e = (int64_t)rt * R_e + j;
+                if (snp < a.mb) a.lin[e * a.ldp + snp] = ldexp((double)T, a.E_e[e] - shift0);
+            }
+        }
     } else {
 #pragma unroll 1
         for (int j = 0; j < R_e; ++j) {
@@ -162,11 +181,11 @@ __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32
     }
 }
 
-template <int S, int R, class Src>
+template <int S, int R, int NT, class Src>
 __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ Src src) {
     using namespace tc;
     const MixedArgs& a = src.a;
-    constexpr int N = R * S;
+    constexpr int N = NT;  // UMMA N of a row tile (limb rows + fused linear rows)
     constexpr uint32_t A_BYTES = mx::BM * mx::BK * 2;
     const int NB = N > a.N_e ? N : a.N_e;
     const uint32_t B_BYTES = (uint32_t)NB * mx::BK * 2;
@@ -320,7 +339,7 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
             }
             fence_after_sync();
             const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
-            epilogue_unit<S, R>(cm, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
+            epilogue_unit<S, R, NT>(cm, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[abuf]);
@@ -347,12 +366,12 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
 // accumulator buffer on the even CTA's barrier (8 warp arrivals).
 // In this kernel a.n_ct counts pairs of 128-SNP tiles.
 // ----------------------------------------------------------------------------
-template <int S, int R>
+template <int S, int R, int NT>
 __global__ void __launch_bounds__(256, 1)
 k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
                const __grid_constant__ CUtensorMap tmE, const MixedArgs a) {
     using namespace tc;
-    constexpr int N = R * S;
+    constexpr int N = NT;
     constexpr int NH = N / 2;
     constexpr uint32_t A_BYTES = mx::BM * mx::BK * 2;
     const int NeH = a.N_e / 2;
@@ -508,7 +527,7 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             fence_after_sync();
             const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
             const int ct = 2 * ctp + (int)rank;
-            epilogue_unit<S, R>(a.c, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
+            epilogue_unit<S, R, NT>(a.c, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[abuf]), 0));
@@ -644,12 +663,12 @@ __device__ __forceinline__ void split_limbs(double w, int E, uint16_t (&out)[S])
     }
 }
 
-// Lower triangle of W (column-major) -> limb rows rt*R*S + l*R + i of WL (k contiguous),
-// R rows of L^{-1} per tile.
+// Lower triangle of W (column-major) -> limb rows rt*NT + l*R + i of WL (k contiguous),
+// R rows of L^{-1} per tile, row tiles NT rows apart.
 template <int S>
 __global__ void __launch_bounds__(256)
-k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, const int* __restrict__ E_w,
-          uint16_t* __restrict__ WL, int64_t n_pad) {
+k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int NT,
+          const int* __restrict__ E_w, uint16_t* __restrict__ WL, int64_t n_pad) {
     __shared__ double tile[32][33];
     const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
     if (k0 > r0 + 31) return;  // strictly upper tile: stays zero
@@ -659,7 +678,7 @@ k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, const int
         tile[j][tx] = (r < n && k < n && k <= r) ? W[r + k * ldw] : 0.0;
     }
     __syncthreads();
-    const int64_t N = (int64_t)R * S;
+    const int64_t N = NT;
     for (int j = ty; j < 32; j += 8) {
         const int64_t r = r0 + j, k = k0 + tx;
         if (r >= n || k >= n || k > r) continue;
@@ -683,6 +702,42 @@ k_split_z(const double* __restrict__ Z, int64_t n, int R_e, const int* __restric
         split_limbs<S>(Z[k + (int64_t)j * n], E_e[j], limbs);
 #pragma unroll
         for (int l = 0; l < S; ++l) WL[(base_row + (int64_t)l * R_e + j) * n_pad + k] = limbs[l];
+    }
+}
+
+// Fused linear rows: exponent per (row tile rt, linear row j) over k in the tile's range.
+__global__ void __launch_bounds__(256)
+k_absmax_zf(const double* __restrict__ Z, int64_t n, int R, unsigned long long* bits) {
+    const int rt = blockIdx.x, j = blockIdx.y, R_e = gridDim.y;
+    const int64_t k0 = (int64_t)rt * R, k1 = min64(n, k0 + R);
+    double m = 0.0;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) m = fmax(m, fabs(Z[k + (int64_t)j * n]));
+    __shared__ double red[256];
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && red[0] > 0.0)
+        atomicMax(&bits[(int64_t)rt * R_e + j], (unsigned long long)__double_as_longlong(red[0]));
+}
+
+// Z (n x R_e) -> for every k, limb rows rt*NT + R*S + l*R_e + j of row tile rt = k / R:
+// each tile carries Z only on its own k-range, so the tiles' partial sums add up to Z^T x.
+template <int S>
+__global__ void __launch_bounds__(256)
+k_split_zf(const double* __restrict__ Z, int64_t n, int R, int NT, int R_e,
+           const int* __restrict__ E_e, uint16_t* __restrict__ WL, int64_t n_pad) {
+    const int j = blockIdx.y;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t rt = k / R;
+        uint16_t limbs[S];
+        split_limbs<S>(Z[k + (int64_t)j * n], E_e[rt * R_e + j], limbs);
+#pragma unroll
+        for (int l = 0; l < S; ++l)
+            WL[(rt * NT + (int64_t)R * S + (int64_t)l * R_e + j) * n_pad + k] = limbs[l];
     }
 }
 
@@ -740,17 +795,27 @@ int mixed_linear_n(int S, int R_e) { return (int)std::max<int64_t>(32, round_up(
 cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk) {
     m.S = S;
     m.n = n;
-    // kernel variant and tile height: the taller UMMA N wins; CTA pairs on a tie
+    // Tile height and kernel variant. When the limb rows of the single-CTA tile leave
+    // room for the S x R_e linear rows, they ride in the same UMMA (N = 256, which also
+    // suits CTA pairs); otherwise the taller UMMA N wins, CTA pairs on a tie.
     const int rs = mx::rows_single(S), rp = mx::rows_pair(S);
-    if (m.cfg_single_cta) m.pair = false;
-    else if (m.cfg_pair) m.pair = true;
-    else m.pair = (rp >= rs);
-    m.R = m.pair ? rp : rs;
-    m.n_rt = (int)ceil_div(n, m.R);
-    m.n_pad = round_up(n, 64);
     m.R_e = R_e;
     m.N_e = mixed_linear_n(S, R_e);
-    m.rows_total = (int64_t)m.n_rt * m.R * S + m.N_e;
+    m.fused = !m.cfg_no_fuse && rs * S < 256 && S * R_e <= 256 - rs * S;
+    if (m.fused) {
+        m.R = rs;
+        m.NT = 256;
+        m.pair = !m.cfg_single_cta;
+    } else {
+        if (m.cfg_single_cta) m.pair = false;
+        else if (m.cfg_pair) m.pair = true;
+        else m.pair = (rp >= rs);
+        m.R = m.pair ? rp : rs;
+        m.NT = m.R * S;
+    }
+    m.n_rt = (int)ceil_div(n, m.R);
+    m.n_pad = round_up(n, 64);
+    m.rows_total = (int64_t)m.n_rt * m.NT + (m.fused ? 0 : m.N_e);
     m.mb_pad_max = round_up(m_blk, 2 * mx::BM);
     m.ldp = round_up(m_blk, 32);
     return cudaSuccess;
@@ -761,34 +826,35 @@ cudaError_t mixed_prepare(MixedDev& m, const double* W, int64_t ldw, const doubl
     cudaError_t e;
     const int64_t n = m.n;
     if ((e = cudaMemsetAsync(m.WL, 0, (size_t)m.rows_total * m.n_pad * 2, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(m.bits, 0, (size_t)(m.n_rt + m.R_e) * 8, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m.bits, 0, (size_t)m.n_exp() * 8, s)) != cudaSuccess) return e;
     k_absmax_w<<<dim3((unsigned)ceil_div(n, 256), (unsigned)m.n_rt), 256, 0, s>>>(W, ldw, n, m.R,
                                                                                  m.bits);
-    k_absmax_z<<<dim3(64, (unsigned)m.R_e), 256, 0, s>>>(Z, n, m.bits + m.n_rt);
-    k_exponents<<<(unsigned)ceil_div(m.n_rt + m.R_e, 128), 128, 0, s>>>(m.bits, m.n_rt + m.R_e, m.E);
+    if (m.fused)
+        k_absmax_zf<<<dim3((unsigned)m.n_rt, (unsigned)m.R_e), 256, 0, s>>>(Z, n, m.R, m.bits + m.n_rt);
+    else
+        k_absmax_z<<<dim3(64, (unsigned)m.R_e), 256, 0, s>>>(Z, n, m.bits + m.n_rt);
+    k_exponents<<<(unsigned)ceil_div(m.n_exp(), 128), 128, 0, s>>>(m.bits, m.n_exp(), m.E);
     const dim3 gw((unsigned)ceil_div(n, 32), (unsigned)ceil_div((int64_t)m.n_rt * m.R, 32));
     const dim3 gz(64, (unsigned)m.R_e);
-    const int64_t zbase = (int64_t)m.n_rt * m.R * m.S;
+    const int64_t zbase = (int64_t)m.n_rt * m.NT;
+#define GWAS_SPLIT(SS)                                                                       \
+    k_split_w<SS><<<gw, 256, 0, s>>>(W, ldw, n, m.R, m.NT, m.E, m.WL, m.n_pad);              \
+    if (m.fused)                                                                             \
+        k_split_zf<SS><<<gz, 256, 0, s>>>(Z, n, m.R, m.NT, m.R_e, m.E + m.n_rt, m.WL, m.n_pad); \
+    else                                                                                     \
+        k_split_z<SS><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
     switch (m.S) {
-        case 2:
-            k_split_w<2><<<gw, 256, 0, s>>>(W, ldw, n, m.R, m.E, m.WL, m.n_pad);
-            k_split_z<2><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
-            break;
-        case 3:
-            k_split_w<3><<<gw, 256, 0, s>>>(W, ldw, n, m.R, m.E, m.WL, m.n_pad);
-            k_split_z<3><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
-            break;
-        case 4:
-            k_split_w<4><<<gw, 256, 0, s>>>(W, ldw, n, m.R, m.E, m.WL, m.n_pad);
-            k_split_z<4><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
-            break;
+        case 2: GWAS_SPLIT(2) break;
+        case 3: GWAS_SPLIT(3) break;
+        case 4: GWAS_SPLIT(4) break;
         default:
             return cudaErrorInvalidValue;
     }
+#undef GWAS_SPLIT
     if (launches) *launches += 6;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // tensor maps over the fixed buffers
-    const int N = m.R * m.S;
+    const int N = m.NT;
     if (!tmap_bf16_2d(&m.tmX, m.Xb, (uint64_t)m.n_pad, (uint64_t)m.mb_pad_max, mx::BK, mx::BM) ||
         !tmap_bf16_2d(&m.tmW, m.WL, (uint64_t)m.n_pad, (uint64_t)m.rows_total, mx::BK, (uint32_t)N) ||
         !tmap_bf16_2d(&m.tmE, m.WL, (uint64_t)m.n_pad, (uint64_t)m.rows_total, mx::BK,
@@ -812,6 +878,7 @@ static CohortMx make_cohort(const MixedDev& m, int64_t mb, bool pair) {
     c.mb = mb;
     c.ldp = m.ldp;
     c.unit_base = 0;
+    c.extra = m.fused ? 0 : 1;
     c.E_w = m.E;
     c.E_e = m.E + m.n_rt;
     c.sq_part = m.sq_part;
@@ -824,34 +891,35 @@ static MixedArgs make_args(const MixedDev& m, int64_t mb, bool pair) {
     a.c = make_cohort(m, mb, pair);
     a.R_e = m.R_e;
     a.N_e = m.N_e;
-    a.stages = stage_count(m.R * m.S, m.N_e, pair);
+    a.stages = stage_count(m.NT, m.N_e, pair);
     if (m.cfg_stages >= 2) a.stages = std::min(a.stages, m.cfg_stages);
-    a.n_units = a.c.n_ct * (a.c.n_rt + 1);
+    a.n_units = a.c.n_ct * (a.c.n_rt + a.c.extra);
     a.err = m.err;
     return a;
 }
 
-template <int S, int R>
+template <int S, int R, int NT>
 static cudaError_t launch_single_t(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
     SrcOne src;
     src.tmX = m.tmX;
     src.tmW = m.tmW;
     src.tmE = m.tmE;
     src.a = make_args(m, mb, false);
-    const size_t smem = smem_bytes(R * S, m.N_e, false, src.a.stages);
-    cudaError_t e = cudaFuncSetAttribute(k_block_mixed<S, R, SrcOne>,
+    const size_t smem = smem_bytes(NT, m.N_e, false, src.a.stages);
+    cudaError_t e = cudaFuncSetAttribute(k_block_mixed<S, R, NT, SrcOne>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(num_sms, src.a.n_units));
-    k_block_mixed<S, R, SrcOne><<<grid, 256, smem, s>>>(src);
+    k_block_mixed<S, R, NT, SrcOne><<<grid, 256, smem, s>>>(src);
     return cudaGetLastError();
 }
 
-template <int S, int R>
+template <int S, int R, int NT>
 static cudaError_t launch_pair_t(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
+    static_assert(NT % 32 == 0, "CTA pairs need N a multiple of 32");
     const MixedArgs a = make_args(m, mb, true);
-    const size_t smem = smem_bytes(R * S, m.N_e, true, a.stages);
-    cudaError_t e = cudaFuncSetAttribute(k_block_mixed2<S, R>,
+    const size_t smem = smem_bytes(NT, m.N_e, true, a.stages);
+    cudaError_t e = cudaFuncSetAttribute(k_block_mixed2<S, R, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -868,13 +936,13 @@ static cudaError_t launch_pair_t(const MixedDev& m, int64_t mb, int num_sms, cud
     // as many CTA pairs as can be resident at once (persistent), at most one per unit
     cfg.gridDim = dim3((unsigned)(2 * std::max(1, num_sms / 2)), 1, 1);
     int clusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&clusters, k_block_mixed2<S, R>, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&clusters, k_block_mixed2<S, R, NT>, &cfg);
     if (e != cudaSuccess) return e;
     if (clusters < 1) return cudaErrorLaunchOutOfResources;
     clusters = std::min(clusters, std::max(1, num_sms / 2));
     clusters = std::min(clusters, a.n_units);
     cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
-    e = cudaLaunchKernelEx(&cfg, k_block_mixed2<S, R>, m.tmX, m.tmWh, m.tmEh, a);
+    e = cudaLaunchKernelEx(&cfg, k_block_mixed2<S, R, NT>, m.tmX, m.tmWh, m.tmEh, a);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -894,25 +962,33 @@ cudaError_t launch_geno_bf16_batch(const BatchJob* jobs, int n_jobs, int64_t n_s
     return cudaGetLastError();
 }
 
+// The (S, R, NT) combinations the layout can choose (see mixed_layout).
+#define GWAS_MIXED_SHAPES(X)                                        \
+    X(2, mx::rows_single(2), 2 * mx::rows_single(2))                \
+    X(3, mx::rows_single(3), 3 * mx::rows_single(3))                \
+    X(3, mx::rows_single(3), 256)                                   \
+    X(3, mx::rows_pair(3), 3 * mx::rows_pair(3))                    \
+    X(4, mx::rows_single(4), 4 * mx::rows_single(4))
+
 cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
     if (mb < 1 || mb > m.mb_pad_max) return cudaErrorInvalidValue;
-    using namespace mx;
-    if (m.pair) {
-        if (m.S == 2 && m.R == rows_pair(2)) return launch_pair_t<2, rows_pair(2)>(m, mb, num_sms, s);
-        if (m.S == 3 && m.R == rows_pair(3)) return launch_pair_t<3, rows_pair(3)>(m, mb, num_sms, s);
-        if (m.S == 4 && m.R == rows_pair(4)) return launch_pair_t<4, rows_pair(4)>(m, mb, num_sms, s);
-    } else {
-        if (m.S == 2 && m.R == rows_single(2)) return launch_single_t<2, rows_single(2)>(m, mb, num_sms, s);
-        if (m.S == 3 && m.R == rows_single(3)) return launch_single_t<3, rows_single(3)>(m, mb, num_sms, s);
-        if (m.S == 4 && m.R == rows_single(4)) return launch_single_t<4, rows_single(4)>(m, mb, num_sms, s);
+#define GWAS_TRY(SS, RR, NN)                                                                  \
+    if (m.S == SS && m.R == RR && m.NT == NN) {                                               \
+        if (m.pair) {                                                                         \
+            if constexpr ((NN) % 32 == 0) return launch_pair_t<SS, RR, NN>(m, mb, num_sms, s); \
+            return cudaErrorInvalidValue;                                                     \
+        }                                                                                     \
+        return launch_single_t<SS, RR, NN>(m, mb, num_sms, s);                                \
     }
+    GWAS_MIXED_SHAPES(GWAS_TRY)
+#undef GWAS_TRY
     return cudaErrorInvalidValue;
 }
 
 // ---- batched cohorts: one persistent launch over a device table of cohorts ----------
 
 int mixed_stage_count(const MixedDev& m) {
-    int st = stage_count(m.R * m.S, m.N_e, false);
+    int st = stage_count(m.NT, m.N_e, false);
     if (m.cfg_stages >= 2) st = std::min(st, m.cfg_stages);
     return st;
 }
@@ -925,17 +1001,17 @@ CohortMx mixed_cohort_entry(const MixedDev& m, int64_t mb, int64_t unit_base) {
 
 int64_t mixed_cohort_units(const MixedDev& m, int64_t mb) {
     const CohortMx c = make_cohort(m, mb, false);
-    return (int64_t)c.n_ct * (c.n_rt + 1);
+    return (int64_t)c.n_ct * (c.n_rt + c.extra);
 }
 
-template <int S, int R>
-static cudaError_t batch_prepare_t(int R_e, int N_e, int stages) {
-    const size_t smem = smem_bytes(R * S, N_e, false, stages);
-    return cudaFuncSetAttribute(k_block_mixed<S, R, SrcBatch>,
+template <int S, int R, int NT>
+static cudaError_t batch_prepare_t(int N_e, int stages) {
+    const size_t smem = smem_bytes(NT, N_e, false, stages);
+    return cudaFuncSetAttribute(k_block_mixed<S, R, NT, SrcBatch>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <int S, int R>
+template <int S, int R, int NT>
 static cudaError_t batch_launch_t(const CohortMx* tab, const CUtensorMap* maps, int n_cohorts,
                                   int n_units, int R_e, int N_e, int stages, int* err, int num_sms,
                                   cudaStream_t s) {
@@ -949,34 +1025,32 @@ static cudaError_t batch_launch_t(const CohortMx* tab, const CUtensorMap* maps, 
     src.a.stages = stages;
     src.a.n_units = n_units;
     src.a.err = err;
-    const size_t smem = smem_bytes(R * S, N_e, false, stages);
+    const size_t smem = smem_bytes(NT, N_e, false, stages);
     const int grid = std::max(1, std::min(num_sms, n_units));
-    k_block_mixed<S, R, SrcBatch><<<grid, 256, smem, s>>>(src);
+    k_block_mixed<S, R, NT, SrcBatch><<<grid, 256, smem, s>>>(src);
     return cudaGetLastError();
 }
 
-cudaError_t mixed_batch_prepare(int S, int R_e, int N_e, int stages) {
-    using namespace mx;
-    switch (S) {
-        case 2: return batch_prepare_t<2, rows_single(2)>(R_e, N_e, stages);
-        case 3: return batch_prepare_t<3, rows_single(3)>(R_e, N_e, stages);
-        case 4: return batch_prepare_t<4, rows_single(4)>(R_e, N_e, stages);
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t mixed_batch_prepare(const MixedDev& m, int stages) {
+#define GWAS_TRY(SS, RR, NN) \
+    if (m.S == SS && m.R == RR && m.NT == NN) return batch_prepare_t<SS, RR, NN>(m.N_e, stages);
+    GWAS_MIXED_SHAPES(GWAS_TRY)
+#undef GWAS_TRY
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_block_mixed_batch(const CohortMx* tab, const CUtensorMap* maps, int n_cohorts,
-                                     int64_t n_units, int S, int R_e, int N_e, int stages,
-                                     int* err, int num_sms, cudaStream_t s) {
-    using namespace mx;
+                                     int64_t n_units, const MixedDev& m, int stages, int* err,
+                                     int num_sms, cudaStream_t s) {
     if (n_units <= 0) return cudaSuccess;
     if (n_units > 0x7fffffffLL) return cudaErrorInvalidValue;
-    switch (S) {
-        case 2: return batch_launch_t<2, rows_single(2)>(tab, maps, n_cohorts, (int)n_units, R_e, N_e, stages, err, num_sms, s);
-        case 3: return batch_launch_t<3, rows_single(3)>(tab, maps, n_cohorts, (int)n_units, R_e, N_e, stages, err, num_sms, s);
-        case 4: return batch_launch_t<4, rows_single(4)>(tab, maps, n_cohorts, (int)n_units, R_e, N_e, stages, err, num_sms, s);
-        default: return cudaErrorInvalidValue;
-    }
+#define GWAS_TRY(SS, RR, NN)                                                                   \
+    if (m.S == SS && m.R == RR && m.NT == NN)                                                  \
+        return batch_launch_t<SS, RR, NN>(tab, maps, n_cohorts, (int)n_units, m.R_e, m.N_e,    \
+                                          stages, err, num_sms, s);
+    GWAS_MIXED_SHAPES(GWAS_TRY)
+#undef GWAS_TRY
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace gwas

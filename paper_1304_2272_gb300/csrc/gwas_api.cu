@@ -175,12 +175,14 @@ void apply_tile_cfg(MixedDev& m, int tile_cfg) {
     m.cfg_group_mb = 40;
     m.cfg_single_cta = false;
     m.cfg_pair = false;
+    m.cfg_no_fuse = false;
     if (tile_cfg >= 0) {
         m.cfg_stages = tile_cfg & 0xF;
         const int g = (tile_cfg >> 4) & 0xFF;
         if (g > 0) m.cfg_group_mb = g;
         m.cfg_single_cta = ((tile_cfg >> 12) & 1) != 0;
         m.cfg_pair = ((tile_cfg >> 13) & 1) != 0;
+        m.cfg_no_fuse = ((tile_cfg >> 14) & 1) != 0;
     }
 }
 
@@ -190,10 +192,10 @@ cudaError_t mixed_alloc_layout(MixedDev& m) {
     m.WL = nullptr; m.bits = nullptr; m.E = nullptr; m.sq_part = nullptr; m.lin = nullptr;
     cudaError_t e;
     if ((e = dmalloc(&m.WL, (size_t)m.rows_total * m.n_pad)) != cudaSuccess) return e;
-    if ((e = dmalloc(&m.bits, (size_t)(m.n_rt + m.R_e))) != cudaSuccess) return e;
-    if ((e = dmalloc(&m.E, (size_t)(m.n_rt + m.R_e))) != cudaSuccess) return e;
+    if ((e = dmalloc(&m.bits, (size_t)m.n_exp())) != cudaSuccess) return e;
+    if ((e = dmalloc(&m.E, (size_t)m.n_exp())) != cudaSuccess) return e;
     if ((e = dmalloc(&m.sq_part, (size_t)m.n_rt * m.ldp)) != cudaSuccess) return e;
-    return dmalloc(&m.lin, (size_t)m.R_e * m.ldp);
+    return dmalloc(&m.lin, (size_t)m.lin_tiles() * m.R_e * m.ldp);
 }
 
 void free_all(gwas_ctx* c) {
@@ -700,15 +702,16 @@ gwas_status gwas_set_tile_cfg(gwas_ctx* c, int tile_cfg) {
     DeviceGuard g(c->device);
     CK(cudaStreamSynchronize(c->s_comp));
     MixedDev& m = c->mx;
-    const int old_R = m.R;
-    const bool old_pair = m.pair;
+    const int old_R = m.R, old_NT = m.NT;
+    const bool old_pair = m.pair, old_fused = m.fused;
     apply_tile_cfg(m, tile_cfg);
     mixed_layout(m, c->n, m.S, m.R_e, c->opts.m_blk);
     c->opts.tile_cfg = tile_cfg;
-    if (m.R != old_R) {
+    const bool relayout = m.R != old_R || m.NT != old_NT || m.fused != old_fused;
+    if (relayout) {
         CK(mixed_alloc_layout(m));
     }
-    if (c->factored && (m.R != old_R || m.pair != old_pair)) {
+    if (c->factored && (relayout || m.pair != old_pair)) {
         int64_t nl = 0;
         CK(mixed_prepare(m, c->W, c->ld, c->Z, c->s_comp, &nl));
         CK(cudaStreamSynchronize(c->s_comp));
@@ -739,9 +742,9 @@ gwas_status gwas_autotune(gwas_ctx* c, const int8_t* X, int64_t mb_max, int reps
 
     std::vector<int> cfgs;
     if (c->mixed) {
-        for (int variant : {1 << 12, 1 << 13})
-            for (int group : {20, 40, 80, 160})
-                for (int stages : {0, 4, 6}) cfgs.push_back(variant | (group << 4) | stages);
+        for (int variant : {1 << 12, 1 << 13, (1 << 14) | (1 << 12), (1 << 14) | (1 << 13)})
+            for (int group : {40, 80, 160})
+                for (int stages : {0, 4}) cfgs.push_back(variant | (group << 4) | stages);
     } else {
         cfgs.push_back(-1);
     }
@@ -861,9 +864,8 @@ gwas_status batch_enqueue(gwas_batch* b) {
     const int nc = b->n_cohorts;
     if (b->mixed) {
         CKB(launch_geno_bf16_batch(b->d_jobs, nc, b->total_snps, b->s));
-        CKB(launch_block_mixed_batch(b->d_tab, b->d_maps, nc, b->units_mx, b->ctx[0]->mx.S,
-                                     b->ctx[0]->mx.R_e, b->ctx[0]->mx.N_e, b->stages, b->d_err,
-                                     b->ctx[0]->num_sms, b->s));
+        CKB(launch_block_mixed_batch(b->d_tab, b->d_maps, nc, b->units_mx, b->ctx[0]->mx,
+                                     b->stages, b->d_err, b->ctx[0]->num_sms, b->s));
         CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, true, b->s));
     } else {
         CKB(launch_block_fp64_batch(b->d_jobs, nc, b->units_fp64, b->s));
@@ -920,7 +922,7 @@ gwas_status gwas_batch_init(int n_cohorts, const int64_t* n, int p, int t, const
     if (b->mixed) {
         const MixedDev& m = b->ctx[0]->mx;
         b->stages = mixed_stage_count(m);
-        if ((e = mixed_batch_prepare(m.S, m.R_e, m.N_e, b->stages)) != cudaSuccess) return bail(e);
+        if ((e = mixed_batch_prepare(m, b->stages)) != cudaSuccess) return bail(e);
     }
     *out = b;
     return GWAS_OK;
@@ -988,6 +990,7 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
                 j.sq_part = cx->mx.sq_part;
                 j.lin = cx->mx.lin;
                 j.n_tiles_mx = cx->mx.n_rt;
+                j.lin_tiles = cx->mx.lin_tiles();
                 tab[c] = mixed_cohort_entry(cx->mx, mb[c], umx);
                 umx += mixed_cohort_units(cx->mx, mb[c]);
                 maps[3 * c + 0] = cx->mx.tmX;

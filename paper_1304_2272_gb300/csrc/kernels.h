@@ -84,36 +84,42 @@ struct CohortMx {
     int64_t mb;         // SNPs
     int64_t ldp;        // leading dimension of sq_part / lin
     int64_t unit_base;  // first unit of this cohort in a batched launch
+    int extra;          // 1: a separate linear tile per SNP tile; 0: linear rows fused
     const int* E_w;     // exponent per row tile
-    const int* E_e;     // exponent per linear row
+    const int* E_e;     // exponent per linear row (fused: per (row tile, linear row))
     double* sq_part;    // [n_rt][ldp]
-    double* lin;        // [R_e][ldp]
+    double* lin;        // [R_e][ldp]; fused: [n_rt][R_e][ldp]
 };
 
 // Device buffers and tensor maps of the BF16-limb path for one cohort.
 struct MixedDev {
     int S = 3;                  // BF16 limbs per element of L^{-1} and Z
     int64_t n = 0;
-    int R = 64;                 // rows of L^{-1} per tile (UMMA N = R * S)
+    int R = 64;                 // rows of L^{-1} per tile
+    int NT = 256;               // UMMA N (limb rows, plus fused linear rows) of a row tile
+    bool fused = false;         // linear rows ride in the spare N of every row tile
     bool pair = true;           // CTA-pair kernel (cta_group::2) instead of one CTA per tile
     int n_rt = 0;               // R-row tiles of L^{-1}
     int64_t n_pad = 0;          // n rounded up to 64 (k extent of every BF16 row)
     int R_e = 0;                // linear rows q + t (Z = L^{-T} [Xbar_L | Ybar])
     int N_e = 0;                // UMMA N of the linear tile (S * R_e rounded up to 16)
-    int64_t rows_total = 0;     // rows of WL: n_rt * R * S + N_e
+    int64_t rows_total = 0;     // rows of WL: n_rt * NT (+ N_e for a separate linear tile)
     int64_t mb_pad_max = 0;     // rows of Xb
     int64_t ldp = 0;            // leading dimension of sq_part / lin
     uint16_t* WL = nullptr;     // BF16 limbs, [rows_total][n_pad], k contiguous
     unsigned long long* bits = nullptr;  // max |.| per row tile / linear row (FP64 bits)
-    int* E = nullptr;           // exponents: n_rt row tiles, then R_e linear rows
+    int* E = nullptr;           // exponents: n_rt row tiles, then the linear rows
     uint16_t* Xb = nullptr;     // BF16 dosages, [mb_pad_max][n_pad]
     double* sq_part = nullptr;  // [n_rt][ldp] row-tile partials of S_BRi
-    double* lin = nullptr;      // [R_e][ldp] S_BLi (q rows) then bbar_Bi (t rows)
+    double* lin = nullptr;      // [lin_tiles][R_e][ldp] S_BLi (q rows) then bbar_Bi (t rows)
     int* err = nullptr;         // kernel wait-timeout code (0 = none)
     int cfg_stages = 0;         // pipeline stages (0 = as many as fit)
     int cfg_group_mb = 40;      // MB of BF16 dosages per L2 group of SNP tiles
     bool cfg_single_cta = false;  // force one CTA per 128-SNP tile
     bool cfg_pair = false;        // force CTA pairs
+    bool cfg_no_fuse = false;     // keep the linear rows in a separate tile
+    int lin_tiles() const { return fused ? n_rt : 1; }
+    int n_exp() const { return n_rt + (fused ? n_rt * R_e : R_e); }
     CUtensorMap tmX, tmW, tmE;  // TMA maps of Xb, WL (row tiles), WL (linear tile)
     CUtensorMap tmWh, tmEh;     // the same WL maps with half-height boxes (CTA pairs)
 };
@@ -137,10 +143,10 @@ cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const 
 int mixed_stage_count(const MixedDev& m);
 CohortMx mixed_cohort_entry(const MixedDev& m, int64_t mb, int64_t unit_base);
 int64_t mixed_cohort_units(const MixedDev& m, int64_t mb);
-cudaError_t mixed_batch_prepare(int S, int R_e, int N_e, int stages);
+cudaError_t mixed_batch_prepare(const MixedDev& m, int stages);
 cudaError_t launch_block_mixed_batch(const CohortMx* tab, const CUtensorMap* maps, int n_cohorts,
-                                     int64_t n_units, int S, int R_e, int N_e, int stages,
-                                     int* err, int num_sms, cudaStream_t s);
+                                     int64_t n_units, const MixedDev& m, int stages, int* err,
+                                     int num_sms, cudaStream_t s);
 
 // ---- batched FP64 path, dosage conversion and p x p solves (batch.cu) ------------------
 
@@ -160,6 +166,7 @@ struct BatchJob {
     const double* sq_part = nullptr;  // mixed partials
     const double* lin = nullptr;
     int n_tiles_mx = 0;
+    int lin_tiles = 1;
     double* b = nullptr;
     double* wald = nullptr;
     uint8_t* status = nullptr;

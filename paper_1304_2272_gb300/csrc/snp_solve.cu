@@ -33,6 +33,8 @@ struct RedMixed {
     int64_t ldp;
     int n_tiles;
     int q;
+    int lin_tiles;  // 1: whole linear values; n_tiles: one partial per row tile
+    int R_e;
     __device__ double operator()(int v, int64_t i) const {
         if (v == q) {
             double s = 0.0;
@@ -40,7 +42,9 @@ struct RedMixed {
             return s;
         }
         const int j = v < q ? v : v - 1;
-        return lin[(int64_t)j * ldp + i];
+        double s = 0.0;
+        for (int r = 0; r < lin_tiles; ++r) s += lin[((int64_t)r * R_e + j) * ldp + i];
+        return s;
     }
 };
 
@@ -116,7 +120,7 @@ k_snp_solve_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps)
     const int64_t i = g - j.snp_base;
     if (i >= j.mb) return;
     if (MIXED) {
-        RedMixed red{j.sq_part, j.lin, j.ldp, j.n_tiles_mx, j.c.q};
+        RedMixed red{j.sq_part, j.lin, j.ldp, j.n_tiles_mx, j.c.q, j.lin_tiles, j.c.q + j.c.t};
         solve_snp(j.c, red, j.bad, i, j.b, j.wald, j.status);
     } else {
         RedFp64 red{j.part, j.ldp, j.n_rt64, n_red(j.c)};
@@ -146,7 +150,7 @@ cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const 
                                    int64_t mb, double* b, double* wald, uint8_t* status,
                                    cudaStream_t s) {
     if (mb <= 0) return cudaSuccess;
-    RedMixed red{m.sq_part, m.lin, m.ldp, m.n_rt, c.q};
+    RedMixed red{m.sq_part, m.lin, m.ldp, m.n_rt, c.q, m.lin_tiles(), m.R_e};
     k_snp_solve<<<(unsigned)ceil_div(mb, 128), 128, 0, s>>>(c, red, bad, mb, b, wald, status);
     return cudaGetLastError();
 }

@@ -16,7 +16,9 @@ pytestmark = pytest.mark.gpu
 
 TOL = {2: 1e-4, 3: 1e-6, 4: 1e-6}
 # tile_cfg bits: 12 forces one CTA per 128-SNP tile, 13 forces CTA pairs (cta_group::2)
-VARIANTS = {"default": -1, "single": 1 << 12, "pair": 1 << 13}
+# 14 keeps the linear rows in a separate tile (no fusion into the limb tiles)
+VARIANTS = {"default": -1, "single": 1 << 12, "pair": 1 << 13,
+            "single_sep": (1 << 14) | (1 << 12), "pair_sep": (1 << 14) | (1 << 13)}
 
 
 def rel_b(b, ref):
@@ -60,14 +62,14 @@ def oracle(c, X):
     return G.gls(c.phi, c.h, c.sigma2, c.XL, c.Y, X)
 
 
-@pytest.mark.parametrize("variant", ["single", "pair", "default"])
+@pytest.mark.parametrize("variant", ["single_sep", "single", "pair", "pair_sep", "default"])
 def test_mixed_small_first(gwas, variant):
     c = synth.make_cohort(3, 128, n_markers=200)
     X = c.snps(130)
     check(run(gwas, c, X, m_blk=256, tile_cfg=VARIANTS[variant]), oracle(c, X), 3)
 
 
-@pytest.mark.parametrize("variant", ["default", "pair", "single"])
+@pytest.mark.parametrize("variant", ["default", "pair", "single", "pair_sep", "single_sep"])
 def test_mixed_small_workload_full(gwas, variant):
     # n = 1000, p = 4, m = 10,000 (the oracle-sized workload), 3 limbs
     c = synth.make_cohort(0, 1000)
@@ -76,9 +78,10 @@ def test_mixed_small_workload_full(gwas, variant):
     print(f"n=1000 mixed x3 ({variant}): max rel b err {eb:.2e}, Wald err {ew:.2e}")
 
 
-@pytest.mark.parametrize("limbs", [2, 4])
+@pytest.mark.parametrize("limbs", [2, 3, 4])
 def test_pair_and_single_cta_bitwise(gwas, limbs):
-    # with 2 or 4 limbs both variants use the same tile height, hence the same limbs
+    # both variants use the same tile height (and, for 3 limbs, the same fused linear
+    # rows), hence the same limbs and the same partial sums
     c = synth.make_cohort(23, 700, n_markers=700)
     X = c.snps(777)
     b1, w1, _ = run(gwas, c, X, limbs=limbs, m_blk=1024, tile_cfg=VARIANTS["pair"])
@@ -87,7 +90,7 @@ def test_pair_and_single_cta_bitwise(gwas, limbs):
     np.testing.assert_array_equal(w1, w2)
 
 
-@pytest.mark.parametrize("variant", ["pair", "single"])
+@pytest.mark.parametrize("variant", ["pair", "single", "pair_sep", "single_sep"])
 @pytest.mark.parametrize("limbs", [2, 3, 4])
 @pytest.mark.parametrize("n,m,p,t,mblk", [
     (64, 1, 4, 1, 64), (65, 127, 4, 1, 128), (130, 129, 3, 2, 128), (1003, 300, 4, 3, 512),
