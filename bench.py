@@ -168,20 +168,39 @@ def bf16_flops_per_snp(n: int, q: int, t: int, limbs: int) -> float:
 
 # DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the bench's own launch shape), valid only
-# while the kernel source is the one captured (first 16 hex digits of its sha256).
+# while the kernel source is the one captured (first 16 hex digits of its sha256) and, for
+# the limb kernel, while the L2 group size and the CTA-pair / fused-row choice are the
+# captured ones (the traffic depends on those, not on the pipeline depth).
 TRAFFIC = {
     "k_block_fp64": {"file": "block_fp64.cu", "sha": "17f101cf32e7945d", "n": 10000,
                      "m_blk": 16384, "bytes": 8830753024 + 101610496},
-    "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "8fa211033a84d593", "n": 10000,
-                         "m_blk": 16384, "tile_cfg": 5376, "bytes": 4220531712 + 18793984},
+    "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "7e05f9937583b122", "n": 10000,
+                         "m_blk": 16384, "group_mb": 40, "single_cta": False, "no_fuse": False,
+                         "bytes": 4054284032 + 81043456},
 }
 
 
-def traffic_for(kernel: str, n: int, m_blk: int):
+def tile_cfg_fields(tile_cfg) -> dict:
+    """The tile_cfg bit fields as the library reads them (a negative value = defaults)."""
+    d = {"stages": 0, "group_mb": 40, "single_cta": False, "pair": False, "no_fuse": False}
+    if tile_cfg is not None and tile_cfg >= 0:
+        d["stages"] = tile_cfg & 0xF
+        d["group_mb"] = ((tile_cfg >> 4) & 0xFF) or 40
+        d["single_cta"] = bool((tile_cfg >> 12) & 1)
+        d["pair"] = bool((tile_cfg >> 13) & 1)
+        d["no_fuse"] = bool((tile_cfg >> 14) & 1)
+    return d
+
+
+def traffic_for(kernel: str, n: int, m_blk: int, tile_cfg=None):
     import hashlib
     rec = TRAFFIC.get(kernel)
     if not rec or rec["n"] != n or rec["m_blk"] != m_blk:
         return None
+    if "group_mb" in rec:
+        f = tile_cfg_fields(tile_cfg)
+        if any(f[k] != rec[k] for k in ("group_mb", "single_cta", "no_fuse")):
+            return None
     path = os.path.join(ROOT, "paper_1304_2272_gb300", "csrc", rec["file"])
     try:
         with open(path, "rb") as f:
@@ -378,7 +397,8 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
         achieved = bf16_flops_per_snp(n, q, t, limbs) * mb / (launch_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": traffic_for(f"k_block_mixed<{limbs}>", n, mb),
+                "traffic": traffic_for(f"k_block_mixed<{limbs}>", n, mb,
+                                       (tune or {}).get("tile_cfg")),
                 "kernel": f"k_block_mixed<{limbs}>",
                 "launch_ms": launch_ms, "peak_source": src,
                 "fp64_equivalent_tflops": flops_per_snp(n, q, t) * value / world / 1e12}

@@ -63,7 +63,7 @@ typedef enum {
 typedef struct {
     int precision; /* gwas_precision                                                  */
     int m_blk;     /* largest block of SNPs one solve call may pass (device slot size) */
-    int n_limbs;   /* GWAS_PREC_MIXED: BF16 limbs L^{-1} is split into (2..7)          */
+    int n_limbs;   /* GWAS_PREC_MIXED: BF16 limbs L^{-1} is split into (2..4)          */
     int tile_cfg;  /* -1 = library default; for GWAS_PREC_MIXED, bits 0-3 = pipeline
                       stages (2..8, 0 = as many as fit), bits 4-11 = MB of BF16 dosages
                       per L2 group of SNP tiles (0 = 40), bit 12 = force one CTA per

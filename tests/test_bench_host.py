@@ -1,0 +1,32 @@
+"""Host-side logic of the benchmark: flop counts, tile_cfg decoding, the traffic guard."""
+import bench
+
+
+def test_flops_per_snp_counts_the_triangle_and_the_linear_rows():
+    n, q, t = 10, 3, 2
+    # n(n+1) flops for W x (lower triangle incl. diagonal), 2n per row of [X_L|Y]
+    assert bench.flops_per_snp(n, q, t) == n * (n + 1) + 2 * n * (q + 1 + t)
+    assert bench.bf16_flops_per_snp(n, q, t, 3) == 3 * (n * (n + 1) + 2 * n * (q + t))
+
+
+def test_tile_cfg_fields_match_the_bit_layout():
+    assert bench.tile_cfg_fields(None) == bench.tile_cfg_fields(-1)
+    d = bench.tile_cfg_fields(8832)           # pair forced, group 40 MB, stages auto
+    assert d == {"stages": 0, "group_mb": 40, "single_cta": False, "pair": True,
+                 "no_fuse": False}
+    d = bench.tile_cfg_fields(4 | (160 << 4) | (1 << 12) | (1 << 14))
+    assert d["stages"] == 4 and d["group_mb"] == 160 and d["single_cta"] and d["no_fuse"]
+    assert bench.tile_cfg_fields(0)["group_mb"] == 40   # group 0 = the default
+
+
+def test_traffic_guard_rejects_other_shapes_and_groupings():
+    rec = bench.TRAFFIC["k_block_mixed<3>"]
+    n, mb = rec["n"], rec["m_blk"]
+    assert bench.traffic_for("k_block_mixed<3>", n + 1, mb) is None
+    assert bench.traffic_for("k_block_mixed<3>", n, mb // 2) is None
+    assert bench.traffic_for("k_block_mixed<3>", n, mb, 160 << 4) is None
+    assert bench.traffic_for("k_block_mixed<3>", n, mb, 1 << 12) is None
+    assert bench.traffic_for("k_block_mixed<9>", n, mb) is None
+    got = bench.traffic_for("k_block_mixed<3>", n, mb, 8832)
+    assert got is None or got == rec["bytes"]   # None once the kernel source changes
+    assert got == bench.traffic_for("k_block_mixed<3>", n, mb, -1)
