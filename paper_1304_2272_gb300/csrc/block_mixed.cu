@@ -547,42 +547,70 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 // ----------------------------------------------------------------------------
 // Dosages -> BF16 rows (one SNP per row, k contiguous), flags for bad dosages.
 // ----------------------------------------------------------------------------
-// One SNP row: n dosages -> BF16, returns nonzero (block-wide) if a dosage is not in {0,1,2}.
-__device__ __forceinline__ int geno_row(const int8_t* __restrict__ src, int64_t n,
-                                        uint16_t* __restrict__ dst) {
-    int flag = 0;
-    for (int64_t k = 4 * (int64_t)threadIdx.x; k < n; k += 4 * (int64_t)blockDim.x) {
-        uint16_t o[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int v = (k + e < n) ? (int)src[k + e] : 0;
-            flag |= (unsigned)v > 2u;
-            o[e] = v == 1 ? 0x3F80u : (v == 2 ? 0x4000u : 0u);
-        }
-        if (k + 3 < n) {
-            *reinterpret_cast<uint2*>(dst + k) =
-                make_uint2((uint32_t)o[0] | ((uint32_t)o[1] << 16),
-                           (uint32_t)o[2] | ((uint32_t)o[3] << 16));
-        } else {
-            for (int e = 0; k + e < n; ++e) dst[k + e] = o[e];
-        }
-    }
-    return __syncthreads_or(flag);
+// One warp converts one SNP row: n dosages -> BF16 (0 -> 0x0000, 1 -> 0x3F80, 2 -> 0x4000),
+// returns nonzero (warp-wide) if a dosage is not in {0,1,2}. A row that starts on a
+// 16-byte boundary is read 16 dosages per lane (coalesced 512-byte warp loads); the
+// remainder, or a whole unaligned row, one dosage per lane.
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t v) {
+    // v holds two 16-bit lanes with values in {0,1,2}: each becomes v * 0x80 + (v != 0) * 0x3F00
+    const uint32_t nz = (v | (v >> 1)) & 0x00010001u;
+    return v * 0x80u + nz * 0x3F00u;
 }
 
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ uint32_t bad_bytes(uint32_t w) {
+    // nonzero iff a byte of w is >= 3: some bit above bit 1 set, or bits 0 and 1 both set
+    return (w & 0xFCFCFCFCu) | (w & (w >> 1) & 0x01010101u);
+}
+
+__device__ __forceinline__ int geno_row_warp(const int8_t* __restrict__ src, int64_t n,
+                                             uint16_t* __restrict__ dst) {
+    const int lane = threadIdx.x % 32;
+    uint32_t flag = 0;
+    int64_t k0 = 0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const int64_t nv = n / 16;
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        uint4* d4 = reinterpret_cast<uint4*>(dst);  // BF16 rows start on 128-byte boundaries
+        for (int64_t v = lane; v < nv; v += 32) {
+            const uint4 w = __ldg(s4 + v);
+            const uint32_t in[4] = {w.x, w.y, w.z, w.w};
+            uint32_t o[8];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                flag |= bad_bytes(in[e]);
+                o[2 * e] = bf16_pair(__byte_perm(in[e], 0u, 0x4140));
+                o[2 * e + 1] = bf16_pair(__byte_perm(in[e], 0u, 0x4342));
+            }
+            d4[2 * v] = make_uint4(o[0], o[1], o[2], o[3]);
+            d4[2 * v + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+        }
+        k0 = nv * 16;
+    }
+    for (int64_t k = k0 + lane; k < n; k += 32) {
+        const uint32_t v = (uint32_t)(uint8_t)src[k];
+        flag |= v > 2u ? 1u : 0u;
+        dst[k] = (uint16_t)bf16_pair(v);
+    }
+    return __any_sync(0xffffffffu, flag != 0);
+}
+
+constexpr int GENO_WARPS = 8;
+
+__global__ void __launch_bounds__(GENO_WARPS * 32)
 k_geno_bf16(const int8_t* __restrict__ X, int64_t ldx, int64_t n, int64_t mb,
             uint16_t* __restrict__ Xb, int64_t n_pad, uint8_t* __restrict__ bad) {
-    for (int64_t j = blockIdx.x; j < mb; j += gridDim.x) {
-        const int flag = geno_row(X + j * ldx, n, Xb + j * n_pad);
-        if (threadIdx.x == 0) bad[j] = (uint8_t)(flag != 0);
+    const int64_t w0 = (int64_t)blockIdx.x * GENO_WARPS + threadIdx.x / 32;
+    for (int64_t j = w0; j < mb; j += (int64_t)gridDim.x * GENO_WARPS) {
+        const int flag = geno_row_warp(X + j * ldx, n, Xb + j * n_pad);
+        if (threadIdx.x % 32 == 0) bad[j] = (uint8_t)(flag != 0);
     }
 }
 
-// Batched cohorts: one block per SNP of every cohort.
-__global__ void __launch_bounds__(256)
+// Batched cohorts: one warp per SNP of every cohort.
+__global__ void __launch_bounds__(GENO_WARPS * 32)
 k_geno_bf16_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps) {
-    for (int64_t g = blockIdx.x; g < n_snps; g += gridDim.x) {
+    const int64_t w0 = (int64_t)blockIdx.x * GENO_WARPS + threadIdx.x / 32;
+    for (int64_t g = w0; g < n_snps; g += (int64_t)gridDim.x * GENO_WARPS) {
         int lo = 0, hi = n_jobs - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) / 2;
@@ -591,9 +619,9 @@ k_geno_bf16_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps)
         }
         const BatchJob& jb = jobs[lo];
         const int64_t j = g - jb.snp_base;
-        if (j >= jb.mb) continue;  // uniform across the block
-        const int flag = geno_row(jb.X + j * jb.c.n, jb.c.n, jb.Xb + j * jb.n_pad);
-        if (threadIdx.x == 0) jb.bad[j] = (uint8_t)(flag != 0);
+        if (j >= jb.mb) continue;  // uniform across the warp
+        const int flag = geno_row_warp(jb.X + j * jb.c.n, jb.c.n, jb.Xb + j * jb.n_pad);
+        if (threadIdx.x % 32 == 0) jb.bad[j] = (uint8_t)(flag != 0);
     }
 }
 
@@ -949,16 +977,16 @@ static cudaError_t launch_pair_t(const MixedDev& m, int64_t mb, int num_sms, cud
 
 cudaError_t launch_geno_bf16(const MixedDev& m, const int8_t* X, int64_t ldx, int64_t mb,
                              uint8_t* bad, cudaStream_t s) {
-    const unsigned grid = (unsigned)std::min<int64_t>(mb, 65535);
-    k_geno_bf16<<<grid, 256, 0, s>>>(X, ldx, m.n, mb, m.Xb, m.n_pad, bad);
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(mb, GENO_WARPS), 1 << 20);
+    k_geno_bf16<<<grid, GENO_WARPS * 32, 0, s>>>(X, ldx, m.n, mb, m.Xb, m.n_pad, bad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_geno_bf16_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps,
                                    cudaStream_t s) {
     if (n_snps <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)std::min<int64_t>(n_snps, 1 << 20);
-    k_geno_bf16_batch<<<grid, 256, 0, s>>>(jobs, n_jobs, n_snps);
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n_snps, GENO_WARPS), 1 << 20);
+    k_geno_bf16_batch<<<grid, GENO_WARPS * 32, 0, s>>>(jobs, n_jobs, n_snps);
     return cudaGetLastError();
 }
 

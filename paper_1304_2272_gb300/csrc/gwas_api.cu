@@ -158,10 +158,11 @@ gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, doubl
     }
     if (c->mixed) {
         CK(launch_snp_solve_mixed(cv, c->mx, c->bad, mb, b, wald, status, c->s_comp));
-        c->stats.kernel_launches += 1;
+        c->stats.kernel_launches += 2;
     } else {
         CK(launch_snp_solve(cv, c->part, c->ldp, (int)ceil_div(c->n, T64), c->bad, mb, b, wald,
                             status, c->s_comp));
+        c->stats.kernel_launches += 1;
     }
     c->stats.kernel_launches += 2;
     c->stats.trsm_launches += 1;
@@ -684,7 +685,7 @@ extern "C" gwas_status gwas_solve_block_grad_device(gwas_ctx* c, const int8_t* X
     const SmallLayout sl(c);
     CK(launch_dbdh(cohort_view(c), c->part, c->part2, c->ldp, n_tiles, c->small + sl.g1,
                    c->grad_s2 / c->grad_h, c->bad, mb, dbdh, c->s_comp));
-    c->stats.kernel_launches += 2;
+    c->stats.kernel_launches += 3;
     return GWAS_OK;
 }
 
@@ -866,10 +867,10 @@ gwas_status batch_enqueue(gwas_batch* b) {
         CKB(launch_geno_bf16_batch(b->d_jobs, nc, b->total_snps, b->s));
         CKB(launch_block_mixed_batch(b->d_tab, b->d_maps, nc, b->units_mx, b->ctx[0]->mx,
                                      b->stages, b->d_err, b->ctx[0]->num_sms, b->s));
-        CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, true, b->s));
+        CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, b->q + 1 + b->t, true, b->s));
     } else {
         CKB(launch_block_fp64_batch(b->d_jobs, nc, b->units_fp64, b->s));
-        CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, false, b->s));
+        CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, b->q + 1 + b->t, false, b->s));
     }
     return GWAS_OK;
 }
@@ -1041,7 +1042,7 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
     }
     b->stats.blocks += 1;
     b->stats.snps += b->total_snps;
-    b->stats.kernel_launches += b->mixed ? 3 : 2;
+    b->stats.kernel_launches += b->mixed ? 4 : 3;
     b->stats.trsm_launches += 1;
     return GWAS_OK;
 }

@@ -67,9 +67,15 @@ __host__ __device__ inline int n_red(const CohortDev& c) { return c.q + 1 + c.t;
 cudaError_t launch_block_fp64(const CohortDev& c, const int8_t* X, int64_t ldx, int64_t mb,
                               double* part, int64_t ldp, uint8_t* bad, cudaStream_t s);
 
-// Sums the row-tile partials of each SNP in a fixed order, assembles S_i and bbar_i
-// (Algorithm 1), solves by p x p Cholesky, writes b, wald (may be null), status.
-cudaError_t launch_snp_solve(const CohortDev& c, const double* part, int64_t ldp, int n_tiles,
+// Sums the n_tiles row-tile partials of every value of each SNP in a fixed order and
+// writes the total over the first partial (row tile 0).
+cudaError_t launch_reduce_fp64(const CohortDev& c, double* part, int64_t ldp, int n_tiles,
+                               int64_t mb, cudaStream_t s);
+
+// Reduces the row-tile partials (as launch_reduce_fp64: the totals replace row tile 0),
+// assembles S_i and bbar_i (Algorithm 1), solves by p x p Cholesky, writes b, wald (may
+// be null), status.
+cudaError_t launch_snp_solve(const CohortDev& c, double* part, int64_t ldp, int n_tiles,
                              const uint8_t* bad, int64_t mb, double* b, double* wald,
                              uint8_t* status, cudaStream_t s);
 
@@ -176,8 +182,9 @@ cudaError_t launch_block_fp64_batch(const BatchJob* jobs, int n_jobs, int64_t n_
                                     cudaStream_t s);
 cudaError_t launch_geno_bf16_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps,
                                    cudaStream_t s);
-cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, bool mixed,
-                                   cudaStream_t s);
+// max_nred: the largest q + 1 + t over the jobs.
+cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, int max_nred,
+                                   bool mixed, cudaStream_t s);
 
 // ---- REML and db/dh (reml.cu) -----------------------------------------------------------
 
@@ -207,8 +214,9 @@ cudaError_t launch_reml_assemble(const RemlDev& r, cudaStream_t s);
 
 // db_i/dh from the forward partials (S_i, bbar_i) and the adjoint partials
 // (g_iL = X_L^T M^-2 x_i, g_ii = |M^-1 x_i|^2, g_iy = Y^T M^-2 x_i), both in the FP64
-// partial layout, and the Gram matrix G1 = Zc^T Zc. scale = sigma2 / h.
-cudaError_t launch_dbdh(const CohortDev& c, const double* part_fwd, const double* part_adj,
+// partial layout, and the Gram matrix G1 = Zc^T Zc. scale = sigma2 / h. part_fwd holds
+// the totals in row tile 0 (left there by launch_snp_solve); part_adj is reduced here.
+cudaError_t launch_dbdh(const CohortDev& c, const double* part_fwd, double* part_adj,
                         int64_t ldp, int n_tiles, const double* G1, double scale,
                         const uint8_t* bad, int64_t mb, double* dbdh, cudaStream_t s);
 

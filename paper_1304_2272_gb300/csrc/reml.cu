@@ -196,7 +196,7 @@ cudaError_t launch_reml_assemble(const RemlDev& r, cudaStream_t s) {
 }
 
 // ----------------------------------------------------------------------------
-// db_i/dh, one thread per SNP.
+// db_i/dh, one thread per SNP (partials already reduced: n_tiles = 1).
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(128)
 k_dbdh(CohortDev c, const double* __restrict__ pf, const double* __restrict__ pa, int64_t ldp,
@@ -253,11 +253,13 @@ k_dbdh(CohortDev c, const double* __restrict__ pf, const double* __restrict__ pa
     }
 }
 
-cudaError_t launch_dbdh(const CohortDev& c, const double* part_fwd, const double* part_adj,
+cudaError_t launch_dbdh(const CohortDev& c, const double* part_fwd, double* part_adj,
                         int64_t ldp, int n_tiles, const double* G1, double scale,
                         const uint8_t* bad, int64_t mb, double* dbdh, cudaStream_t s) {
     if (mb <= 0) return cudaSuccess;
-    k_dbdh<<<(unsigned)ceil_div(mb, 128), 128, 0, s>>>(c, part_fwd, part_adj, ldp, n_tiles, G1,
+    cudaError_t e = launch_reduce_fp64(c, part_adj, ldp, n_tiles, mb, s);
+    if (e != cudaSuccess) return e;
+    k_dbdh<<<(unsigned)ceil_div(mb, 128), 128, 0, s>>>(c, part_fwd, part_adj, ldp, 1, G1,
                                                        scale, bad, mb, dbdh);
     return cudaGetLastError();
 }

@@ -1,7 +1,8 @@
 // Per-SNP tail of Algorithm 1's loop (Section 2.1): add the row-tile partial sums,
 // set S_i = [[S_TL, *], [S_BLi, S_BRi]] and bbar_i = [bbar_T; bbar_Bi], and solve
 // S_i b_i = bbar_i through a p x p Cholesky factorisation (Section 2, sixth step).
-// One thread per SNP, everything in FP64.
+// The row-tile partials are first added by k_reduce_partials (many warps per SNP group,
+// fixed order), then one thread per SNP forms and solves S_i, everything in FP64.
 #include <math.h>
 
 #include "common.cuh"
@@ -12,13 +13,24 @@ namespace gwas {
 // Singular S_i: a Cholesky pivot at or below this fraction of max_j S_jj.
 constexpr double SINGULAR_RTOL = 1e-12;
 
+// The row-tile partials of one reduction value: value v of SNP i is
+// sum_{r < count} base[r * stride + i].
+struct PartialSet {
+    double* base;
+    int64_t stride;
+    int count;
+};
+
 // Reduction value v of SNP i (v < q: S_BLi[v]; v == q: S_BRi; v > q: bbar_Bi[v-q-1]).
-// FP64 path: every value is a sum of per-row-tile partials, added in ascending order.
+// FP64 path: every value is a sum of per-row-tile partials.
 struct RedFp64 {
     const double* part;
     int64_t ldp;
     int n_tiles;
     int nred;
+    __device__ PartialSet set(int v) const {
+        return {const_cast<double*>(part) + (int64_t)v * ldp, (int64_t)nred * ldp, n_tiles};
+    }
     __device__ double operator()(int v, int64_t i) const {
         double s = 0.0;
         for (int r = 0; r < n_tiles; ++r) s += part[((int64_t)r * nred + v) * ldp + i];
@@ -35,6 +47,11 @@ struct RedMixed {
     int q;
     int lin_tiles;  // 1: whole linear values; n_tiles: one partial per row tile
     int R_e;
+    __device__ PartialSet set(int v) const {
+        if (v == q) return {const_cast<double*>(sq), ldp, n_tiles};
+        const int j = v < q ? v : v - 1;
+        return {const_cast<double*>(lin) + (int64_t)j * ldp, (int64_t)R_e * ldp, lin_tiles};
+    }
     __device__ double operator()(int v, int64_t i) const {
         if (v == q) {
             double s = 0.0;
@@ -95,6 +112,67 @@ __device__ __forceinline__ void solve_snp(const CohortDev& c, const Red& red,
     status[i] = st;
 }
 
+// Adds the row-tile partials of every reduction value and writes the total over the first
+// partial (r = 0), so that the solve reads one value. A block covers 32 consecutive SNPs of
+// one value: warp w adds rows r = w, w + 8, ... in ascending order, then warp 0 adds the
+// eight warp sums in warp order. The order depends only on the row-tile count, never on
+// the block size or the SNP's position, so results stay reproducible bit for bit.
+constexpr int RED_WARPS = 8;
+
+__device__ __forceinline__ void reduce_set(const PartialSet& ps, int64_t i, bool valid,
+                                           double (*sh)[32]) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    double s = 0.0;
+    if (valid)
+        for (int r = warp; r < ps.count; r += RED_WARPS) s += ps.base[(int64_t)r * ps.stride + i];
+    sh[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && valid) {
+        double tot = sh[0][lane];
+#pragma unroll
+        for (int w = 1; w < RED_WARPS; ++w) tot += sh[w][lane];
+        ps.base[i] = tot;
+    }
+}
+
+template <class Red>
+__global__ void __launch_bounds__(RED_WARPS * 32)
+k_reduce_partials(Red red, int64_t mb) {
+    __shared__ double sh[RED_WARPS][32];
+    const int64_t i = blockIdx.x * 32LL + threadIdx.x % 32;
+    reduce_set(red.set((int)blockIdx.y), i, i < mb, sh);
+}
+
+__device__ __forceinline__ int find_job(const BatchJob* __restrict__ jobs, int n_jobs, int64_t g) {
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (jobs[mid].snp_base <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(RED_WARPS * 32)
+k_reduce_partials_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps) {
+    __shared__ double sh[RED_WARPS][32];
+    const int64_t g = blockIdx.x * 32LL + threadIdx.x % 32;
+    const int v = (int)blockIdx.y;
+    const BatchJob& j = jobs[find_job(jobs, n_jobs, g < n_snps ? g : n_snps - 1)];
+    const int64_t i = g - j.snp_base;
+    const bool valid = g < n_snps && i < j.mb && v < n_red(j.c);
+    PartialSet ps{nullptr, 0, 0};
+    if (MIXED) {
+        RedMixed red{j.sq_part, j.lin, j.ldp, j.n_tiles_mx, j.c.q, j.lin_tiles, j.c.q + j.c.t};
+        if (valid) ps = red.set(v);
+    } else {
+        RedFp64 red{j.part, j.ldp, j.n_rt64, n_red(j.c)};
+        if (valid) ps = red.set(v);
+    }
+    reduce_set(ps, i, valid, sh);
+}
+
 template <class Red>
 __global__ void __launch_bounds__(128)
 k_snp_solve(CohortDev c, Red red, const uint8_t* __restrict__ bad, int64_t mb,
@@ -104,42 +182,56 @@ k_snp_solve(CohortDev c, Red red, const uint8_t* __restrict__ bad, int64_t mb,
     solve_snp(c, red, bad, i, b, wald, status);
 }
 
-// Batched cohorts: one thread per SNP of every cohort.
+// Batched cohorts: one thread per SNP of every cohort (partials already reduced).
 template <bool MIXED>
 __global__ void __launch_bounds__(128)
 k_snp_solve_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= n_snps) return;
-    int lo = 0, hi = n_jobs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) / 2;
-        if (jobs[mid].snp_base <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    const BatchJob& j = jobs[lo];
+    const BatchJob& j = jobs[find_job(jobs, n_jobs, g)];
     const int64_t i = g - j.snp_base;
     if (i >= j.mb) return;
     if (MIXED) {
-        RedMixed red{j.sq_part, j.lin, j.ldp, j.n_tiles_mx, j.c.q, j.lin_tiles, j.c.q + j.c.t};
+        RedMixed red{j.sq_part, j.lin, j.ldp, 1, j.c.q, 1, j.c.q + j.c.t};
         solve_snp(j.c, red, j.bad, i, j.b, j.wald, j.status);
     } else {
-        RedFp64 red{j.part, j.ldp, j.n_rt64, n_red(j.c)};
+        RedFp64 red{j.part, j.ldp, 1, n_red(j.c)};
         solve_snp(j.c, red, j.bad, i, j.b, j.wald, j.status);
     }
 }
 
-cudaError_t launch_snp_solve(const CohortDev& c, const double* part, int64_t ldp, int n_tiles,
+template <class Red>
+cudaError_t reduce_partials(const Red& red, int nred, int64_t mb, cudaStream_t s) {
+    k_reduce_partials<<<dim3((unsigned)ceil_div(mb, 32), (unsigned)nred), RED_WARPS * 32, 0, s>>>(
+        red, mb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_fp64(const CohortDev& c, double* part, int64_t ldp, int n_tiles,
+                               int64_t mb, cudaStream_t s) {
+    if (mb <= 0) return cudaSuccess;
+    return reduce_partials(RedFp64{part, ldp, n_tiles, n_red(c)}, n_red(c), mb, s);
+}
+
+cudaError_t launch_snp_solve(const CohortDev& c, double* part, int64_t ldp, int n_tiles,
                              const uint8_t* bad, int64_t mb, double* b, double* wald,
                              uint8_t* status, cudaStream_t s) {
     if (mb <= 0) return cudaSuccess;
-    RedFp64 red{part, ldp, n_tiles, n_red(c)};
+    cudaError_t e = launch_reduce_fp64(c, part, ldp, n_tiles, mb, s);
+    if (e != cudaSuccess) return e;
+    RedFp64 red{part, ldp, 1, n_red(c)};
     k_snp_solve<<<(unsigned)ceil_div(mb, 128), 128, 0, s>>>(c, red, bad, mb, b, wald, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, bool mixed,
-                                   cudaStream_t s) {
+cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, int max_nred,
+                                   bool mixed, cudaStream_t s) {
     if (n_snps <= 0) return cudaSuccess;
+    const dim3 gr((unsigned)ceil_div(n_snps, 32), (unsigned)max_nred);
+    if (mixed) k_reduce_partials_batch<true><<<gr, RED_WARPS * 32, 0, s>>>(jobs, n_jobs, n_snps);
+    else k_reduce_partials_batch<false><<<gr, RED_WARPS * 32, 0, s>>>(jobs, n_jobs, n_snps);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)ceil_div(n_snps, 128);
     if (mixed) k_snp_solve_batch<true><<<grid, 128, 0, s>>>(jobs, n_jobs, n_snps);
     else k_snp_solve_batch<false><<<grid, 128, 0, s>>>(jobs, n_jobs, n_snps);
@@ -150,7 +242,11 @@ cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const 
                                    int64_t mb, double* b, double* wald, uint8_t* status,
                                    cudaStream_t s) {
     if (mb <= 0) return cudaSuccess;
-    RedMixed red{m.sq_part, m.lin, m.ldp, m.n_rt, c.q, m.lin_tiles(), m.R_e};
+    const int q = c.q;
+    cudaError_t e = reduce_partials(RedMixed{m.sq_part, m.lin, m.ldp, m.n_rt, q, m.lin_tiles(), m.R_e},
+                                    n_red(c), mb, s);
+    if (e != cudaSuccess) return e;
+    RedMixed red{m.sq_part, m.lin, m.ldp, 1, q, 1, m.R_e};
     k_snp_solve<<<(unsigned)ceil_div(mb, 128), 128, 0, s>>>(c, red, bad, mb, b, wald, status);
     return cudaGetLastError();
 }
