@@ -63,7 +63,8 @@ typedef enum {
 typedef struct {
     int precision; /* gwas_precision                                                  */
     int m_blk;     /* largest block of SNPs one solve call may pass (device slot size) */
-    int n_limbs;   /* GWAS_PREC_MIXED: BF16 limbs L^{-1} is split into (2..4)          */
+    int n_limbs;   /* GWAS_PREC_MIXED: BF16 limbs L^{-1} is split into (2..5); each adds
+                      9 bits: 3 keep b within ~1e-8 of FP64, 5 within ~1e-13           */
     int tile_cfg;  /* -1 = library default; for GWAS_PREC_MIXED, bits 0-3 = pipeline
                       stages (2..8, 0 = as many as fit), bits 4-11 = MB of BF16 dosages
                       per L2 group of SNP tiles (0 = 40), bit 12 = force one CTA per
@@ -235,9 +236,11 @@ gwas_status gwas_set_tile_cfg(gwas_ctx* ctx, int tile_cfg);
 /*
  * Autotuner: on a factored context, time the whole block path (dosage conversion,
  * dominant kernel, p x p solves) for every candidate tile configuration (mixed: one
- * CTA or CTA pairs, fused or separate linear rows, pipeline stages, L2 group size) and block size (4096, 8192, 16384
- * and mb_max SNPs, up to m_blk) with CUDA events, `reps` launches each; keep the
- * fastest configuration on the context and report it in *out. X: n x mb_max DEVICE
+ * CTA or CTA pairs, fused or separate linear rows, pipeline stages, L2 group size) and
+ * block size (4096, 8192, 16384 and mb_max SNPs, up to m_blk) with CUDA events, `reps`
+ * launches each; time the four fastest again (three interleaved rounds of 2 x reps
+ * launches, best round each); keep the fastest of those on the context and report it
+ * in *out. X: n x mb_max DEVICE
  * dosages to time with, or NULL for synthetic ones (timing does not depend on the
  * values). Allocates temporary device memory; synchronises the context; does not add
  * to the context's counters. Errors: GWAS_ERR_STATE (no factor), GWAS_ERR_CUDA.

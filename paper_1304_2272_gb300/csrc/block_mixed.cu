@@ -545,231 +545,6 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 }
 
 // ----------------------------------------------------------------------------
-// Dosages -> BF16 rows (one SNP per row, k contiguous), flags for bad dosages.
-// ----------------------------------------------------------------------------
-// One warp converts one SNP row: n dosages -> BF16 (0 -> 0x0000, 1 -> 0x3F80, 2 -> 0x4000),
-// returns nonzero (warp-wide) if a dosage is not in {0,1,2}. A row that starts on a
-// 16-byte boundary is read 16 dosages per lane (coalesced 512-byte warp loads); the
-// remainder, or a whole unaligned row, one dosage per lane.
-__device__ __forceinline__ uint32_t bf16_pair(uint32_t v) {
-    // v holds two 16-bit lanes with values in {0,1,2}: each becomes v * 0x80 + (v != 0) * 0x3F00
-    const uint32_t nz = (v | (v >> 1)) & 0x00010001u;
-    return v * 0x80u + nz * 0x3F00u;
-}
-
-__device__ __forceinline__ uint32_t bad_bytes(uint32_t w) {
-    // nonzero iff a byte of w is >= 3: some bit above bit 1 set, or bits 0 and 1 both set
-    return (w & 0xFCFCFCFCu) | (w & (w >> 1) & 0x01010101u);
-}
-
-__device__ __forceinline__ int geno_row_warp(const int8_t* __restrict__ src, int64_t n,
-                                             uint16_t* __restrict__ dst) {
-    const int lane = threadIdx.x % 32;
-    uint32_t flag = 0;
-    int64_t k0 = 0;
-    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-        const int64_t nv = n / 16;
-        const uint4* s4 = reinterpret_cast<const uint4*>(src);
-        uint4* d4 = reinterpret_cast<uint4*>(dst);  // BF16 rows start on 128-byte boundaries
-        for (int64_t v = lane; v < nv; v += 32) {
-            const uint4 w = __ldg(s4 + v);
-            const uint32_t in[4] = {w.x, w.y, w.z, w.w};
-            uint32_t o[8];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                flag |= bad_bytes(in[e]);
-                o[2 * e] = bf16_pair(__byte_perm(in[e], 0u, 0x4140));
-                o[2 * e + 1] = bf16_pair(__byte_perm(in[e], 0u, 0x4342));
-            }
-            d4[2 * v] = make_uint4(o[0], o[1], o[2], o[3]);
-            d4[2 * v + 1] = make_uint4(o[4], o[5], o[6], o[7]);
-        }
-        k0 = nv * 16;
-    }
-    for (int64_t k = k0 + lane; k < n; k += 32) {
-        const uint32_t v = (uint32_t)(uint8_t)src[k];
-        flag |= v > 2u ? 1u : 0u;
-        dst[k] = (uint16_t)bf16_pair(v);
-    }
-    return __any_sync(0xffffffffu, flag != 0);
-}
-
-constexpr int GENO_WARPS = 8;
-
-__global__ void __launch_bounds__(GENO_WARPS * 32)
-k_geno_bf16(const int8_t* __restrict__ X, int64_t ldx, int64_t n, int64_t mb,
-            uint16_t* __restrict__ Xb, int64_t n_pad, uint8_t* __restrict__ bad) {
-    const int64_t w0 = (int64_t)blockIdx.x * GENO_WARPS + threadIdx.x / 32;
-    for (int64_t j = w0; j < mb; j += (int64_t)gridDim.x * GENO_WARPS) {
-        const int flag = geno_row_warp(X + j * ldx, n, Xb + j * n_pad);
-        if (threadIdx.x % 32 == 0) bad[j] = (uint8_t)(flag != 0);
-    }
-}
-
-// Batched cohorts: one warp per SNP of every cohort.
-__global__ void __launch_bounds__(GENO_WARPS * 32)
-k_geno_bf16_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps) {
-    const int64_t w0 = (int64_t)blockIdx.x * GENO_WARPS + threadIdx.x / 32;
-    for (int64_t g = w0; g < n_snps; g += (int64_t)gridDim.x * GENO_WARPS) {
-        int lo = 0, hi = n_jobs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) / 2;
-            if (jobs[mid].snp_base <= g) lo = mid;
-            else hi = mid - 1;
-        }
-        const BatchJob& jb = jobs[lo];
-        const int64_t j = g - jb.snp_base;
-        if (j >= jb.mb) continue;  // uniform across the warp
-        const int flag = geno_row_warp(jb.X + j * jb.c.n, jb.c.n, jb.Xb + j * jb.n_pad);
-        if (threadIdx.x % 32 == 0) jb.bad[j] = (uint8_t)(flag != 0);
-    }
-}
-
-// ----------------------------------------------------------------------------
-// Exponents and limb split of L^{-1} (row tiles) and of Z (linear rows).
-// ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_absmax_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, unsigned long long* bits) {
-    // grid: x = k chunks of 256, y = row tile of R rows; elements (i, k) of the tile's
-    // lower part, i fastest (coalesced along the column-major rows)
-    const int rt = blockIdx.y;
-    const int64_t r0 = (int64_t)rt * R, k0 = (int64_t)blockIdx.x * 256;
-    double m = 0.0;
-    for (int e = threadIdx.x; e < R * 256; e += blockDim.x) {
-        const int64_t r = r0 + e % R, k = k0 + e / R;
-        if (r < n && k <= r) m = fmax(m, fabs(W[r + k * ldw]));
-    }
-    __shared__ double red[256];
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && red[0] > 0.0)
-        atomicMax(&bits[rt], (unsigned long long)__double_as_longlong(red[0]));
-}
-
-__global__ void __launch_bounds__(256)
-k_absmax_z(const double* __restrict__ Z, int64_t n, unsigned long long* bits) {
-    const int j = blockIdx.y;
-    double m = 0.0;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x)
-        m = fmax(m, fabs(Z[k + (int64_t)j * n]));
-    __shared__ double red[256];
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && red[0] > 0.0)
-        atomicMax(&bits[j], (unsigned long long)__double_as_longlong(red[0]));
-}
-
-// E with max|.| <= 2^E (frexp exponent); 0 for an all-zero tile.
-__global__ void k_exponents(const unsigned long long* bits, int count, int* E) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    int e = 0;
-    const double m = __longlong_as_double((long long)bits[i]);
-    if (m > 0.0) frexp(m, &e);
-    E[i] = e;
-}
-
-template <int S>
-__device__ __forceinline__ void split_limbs(double w, int E, uint16_t (&out)[S]) {
-    double r = ldexp(w, 8 - E);  // |r| <= 256
-#pragma unroll
-    for (int l = 0; l < S; ++l) {
-        const double a = rint(r);
-        r = (r - a) * 512.0;  // exact: |r - a| <= 1/2
-        // |a| <= 256 has at most 9 significant bits: the top half of its FP32 pattern
-        // is its exact BF16 pattern
-        out[l] = (uint16_t)(__float_as_uint((float)a) >> 16);
-    }
-}
-
-// Lower triangle of W (column-major) -> limb rows rt*NT + l*R + i of WL (k contiguous),
-// R rows of L^{-1} per tile, row tiles NT rows apart.
-template <int S>
-__global__ void __launch_bounds__(256)
-k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int NT,
-          const int* __restrict__ E_w, uint16_t* __restrict__ WL, int64_t n_pad) {
-    __shared__ double tile[32][33];
-    const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
-    if (k0 > r0 + 31) return;  // strictly upper tile: stays zero
-    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
-    for (int j = ty; j < 32; j += 8) {
-        const int64_t r = r0 + tx, k = k0 + j;
-        tile[j][tx] = (r < n && k < n && k <= r) ? W[r + k * ldw] : 0.0;
-    }
-    __syncthreads();
-    const int64_t N = NT;
-    for (int j = ty; j < 32; j += 8) {
-        const int64_t r = r0 + j, k = k0 + tx;
-        if (r >= n || k >= n || k > r) continue;
-        const int64_t rt = r / R, i = r % R;
-        uint16_t limbs[S];
-        split_limbs<S>(tile[tx][j], E_w[rt], limbs);
-#pragma unroll
-        for (int l = 0; l < S; ++l) WL[(rt * N + (int64_t)l * R + i) * n_pad + k] = limbs[l];
-    }
-}
-
-// Z (n x R_e, column-major) -> limb rows base + l*R_e + j of WL.
-template <int S>
-__global__ void __launch_bounds__(256)
-k_split_z(const double* __restrict__ Z, int64_t n, int R_e, const int* __restrict__ E_e,
-          uint16_t* __restrict__ WL, int64_t n_pad, int64_t base_row) {
-    const int j = blockIdx.y;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        uint16_t limbs[S];
-        split_limbs<S>(Z[k + (int64_t)j * n], E_e[j], limbs);
-#pragma unroll
-        for (int l = 0; l < S; ++l) WL[(base_row + (int64_t)l * R_e + j) * n_pad + k] = limbs[l];
-    }
-}
-
-// Fused linear rows: exponent per (row tile rt, linear row j) over k in the tile's range.
-__global__ void __launch_bounds__(256)
-k_absmax_zf(const double* __restrict__ Z, int64_t n, int R, unsigned long long* bits) {
-    const int rt = blockIdx.x, j = blockIdx.y, R_e = gridDim.y;
-    const int64_t k0 = (int64_t)rt * R, k1 = min64(n, k0 + R);
-    double m = 0.0;
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) m = fmax(m, fabs(Z[k + (int64_t)j * n]));
-    __shared__ double red[256];
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && red[0] > 0.0)
-        atomicMax(&bits[(int64_t)rt * R_e + j], (unsigned long long)__double_as_longlong(red[0]));
-}
-
-// Z (n x R_e) -> for every k, limb rows rt*NT + R*S + l*R_e + j of row tile rt = k / R:
-// each tile carries Z only on its own k-range, so the tiles' partial sums add up to Z^T x.
-template <int S>
-__global__ void __launch_bounds__(256)
-k_split_zf(const double* __restrict__ Z, int64_t n, int R, int NT, int R_e,
-           const int* __restrict__ E_e, uint16_t* __restrict__ WL, int64_t n_pad) {
-    const int j = blockIdx.y;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t rt = k / R;
-        uint16_t limbs[S];
-        split_limbs<S>(Z[k + (int64_t)j * n], E_e[rt * R_e + j], limbs);
-#pragma unroll
-        for (int l = 0; l < S; ++l)
-            WL[(rt * NT + (int64_t)R * S + (int64_t)l * R_e + j) * n_pad + k] = limbs[l];
-    }
-}
-
-// ----------------------------------------------------------------------------
 // Host side.
 // ----------------------------------------------------------------------------
 namespace {
@@ -851,36 +626,8 @@ cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk) 
 
 cudaError_t mixed_prepare(MixedDev& m, const double* W, int64_t ldw, const double* Z,
                           cudaStream_t s, int64_t* launches) {
-    cudaError_t e;
-    const int64_t n = m.n;
-    if ((e = cudaMemsetAsync(m.WL, 0, (size_t)m.rows_total * m.n_pad * 2, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(m.bits, 0, (size_t)m.n_exp() * 8, s)) != cudaSuccess) return e;
-    k_absmax_w<<<dim3((unsigned)ceil_div(n, 256), (unsigned)m.n_rt), 256, 0, s>>>(W, ldw, n, m.R,
-                                                                                 m.bits);
-    if (m.fused)
-        k_absmax_zf<<<dim3((unsigned)m.n_rt, (unsigned)m.R_e), 256, 0, s>>>(Z, n, m.R, m.bits + m.n_rt);
-    else
-        k_absmax_z<<<dim3(64, (unsigned)m.R_e), 256, 0, s>>>(Z, n, m.bits + m.n_rt);
-    k_exponents<<<(unsigned)ceil_div(m.n_exp(), 128), 128, 0, s>>>(m.bits, m.n_exp(), m.E);
-    const dim3 gw((unsigned)ceil_div(n, 32), (unsigned)ceil_div((int64_t)m.n_rt * m.R, 32));
-    const dim3 gz(64, (unsigned)m.R_e);
-    const int64_t zbase = (int64_t)m.n_rt * m.NT;
-#define GWAS_SPLIT(SS)                                                                       \
-    k_split_w<SS><<<gw, 256, 0, s>>>(W, ldw, n, m.R, m.NT, m.E, m.WL, m.n_pad);              \
-    if (m.fused)                                                                             \
-        k_split_zf<SS><<<gz, 256, 0, s>>>(Z, n, m.R, m.NT, m.R_e, m.E + m.n_rt, m.WL, m.n_pad); \
-    else                                                                                     \
-        k_split_z<SS><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
-    switch (m.S) {
-        case 2: GWAS_SPLIT(2) break;
-        case 3: GWAS_SPLIT(3) break;
-        case 4: GWAS_SPLIT(4) break;
-        default:
-            return cudaErrorInvalidValue;
-    }
-#undef GWAS_SPLIT
-    if (launches) *launches += 6;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    cudaError_t e = launch_limb_split(m, W, ldw, Z, s, launches);
+    if (e != cudaSuccess) return e;
     // tensor maps over the fixed buffers
     const int N = m.NT;
     if (!tmap_bf16_2d(&m.tmX, m.Xb, (uint64_t)m.n_pad, (uint64_t)m.mb_pad_max, mx::BK, mx::BM) ||
@@ -975,28 +722,15 @@ static cudaError_t launch_pair_t(const MixedDev& m, int64_t mb, int num_sms, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_geno_bf16(const MixedDev& m, const int8_t* X, int64_t ldx, int64_t mb,
-                             uint8_t* bad, cudaStream_t s) {
-    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(mb, GENO_WARPS), 1 << 20);
-    k_geno_bf16<<<grid, GENO_WARPS * 32, 0, s>>>(X, ldx, m.n, mb, m.Xb, m.n_pad, bad);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_geno_bf16_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps,
-                                   cudaStream_t s) {
-    if (n_snps <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n_snps, GENO_WARPS), 1 << 20);
-    k_geno_bf16_batch<<<grid, GENO_WARPS * 32, 0, s>>>(jobs, n_jobs, n_snps);
-    return cudaGetLastError();
-}
-
 // The (S, R, NT) combinations the layout can choose (see mixed_layout).
 #define GWAS_MIXED_SHAPES(X)                                        \
     X(2, mx::rows_single(2), 2 * mx::rows_single(2))                \
     X(3, mx::rows_single(3), 3 * mx::rows_single(3))                \
     X(3, mx::rows_single(3), 256)                                   \
     X(3, mx::rows_pair(3), 3 * mx::rows_pair(3))                    \
-    X(4, mx::rows_single(4), 4 * mx::rows_single(4))
+    X(4, mx::rows_single(4), 4 * mx::rows_single(4))                \
+    X(5, mx::rows_single(5), 5 * mx::rows_single(5))                \
+    X(5, mx::rows_pair(5), 5 * mx::rows_pair(5))
 
 cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
     if (mb < 1 || mb > m.mb_pad_max) return cudaErrorInvalidValue;

@@ -245,8 +245,9 @@ gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx**
     if (n > (int64_t)1 << 31) return GWAS_ERR_ARG;
     if (o.precision == GWAS_PREC_MIXED) {
         // exact FP32 accumulation of integer limb products needs 512 n < 2^24; the
-        // linear tile must fit one UMMA (N <= 256)
-        if (o.n_limbs < 2 || o.n_limbs > 4 || n >= 32768 ||
+        // linear tile must fit one UMMA (N <= 256); with 5 limbs the recombined value
+        // stays below 2^61 and a tile's sum of R <= 48 squares below 2^126 (int64, int128)
+        if (o.n_limbs < 2 || o.n_limbs > 5 || n >= 32768 ||
             o.n_limbs * ((p - 1) + t) > 256)
             return GWAS_ERR_UNSUPPORTED;
     }
@@ -760,32 +761,60 @@ gwas_status gwas_autotune(gwas_ctx* c, const int8_t* X, int64_t mb_max, int reps
     const gwas_stats saved_stats = c->stats;
     c->opts.timing = 0;
     cudaEvent_t e0 = pooled_event(c), e1 = pooled_event(c);
-    double best = 1e300;
-    int best_cfg = saved_cfg;
-    int64_t best_mb = mbs.back();
+    // time `runs` back-to-back block solves of mb SNPs after one untimed one: ms per SNP
+    auto time_cfg = [&](int64_t mb, int runs, double* per_snp) -> gwas_status {
+        gwas_status s2 = run_block(c, Xd, mb, bo, wo, so);
+        if (s2 != GWAS_OK) return s2;
+        CK(cudaEventRecord(e0, c->s_comp));
+        for (int r = 0; r < runs; ++r)
+            if ((s2 = run_block(c, Xd, mb, bo, wo, so)) != GWAS_OK) return s2;
+        CK(cudaEventRecord(e1, c->s_comp));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        *per_snp = ms / (runs * (double)mb);
+        return GWAS_OK;
+    };
+    // coarse sweep over every (configuration, block size), then the four fastest are
+    // timed again, interleaved over three rounds with twice the launches; the choice is
+    // the fastest of those (best round each), which keeps one lucky short timing from
+    // deciding between near-equal candidates
+    struct Cand { double per_snp; int cfg; int64_t mb; };
+    std::vector<Cand> coarse;
     int tried = 0;
     gwas_status st = GWAS_OK;
     for (int cfg : cfgs) {
         if ((st = gwas_set_tile_cfg(c, cfg)) != GWAS_OK) break;
         for (int64_t mb : mbs) {
-            // one untimed launch, then `reps` timed back-to-back
-            if ((st = run_block(c, Xd, mb, bo, wo, so)) != GWAS_OK) break;
-            CK(cudaEventRecord(e0, c->s_comp));
-            for (int r = 0; r < reps && st == GWAS_OK; ++r) st = run_block(c, Xd, mb, bo, wo, so);
-            if (st != GWAS_OK) break;
-            CK(cudaEventRecord(e1, c->s_comp));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            const double per_snp = ms / (reps * (double)mb);
+            double v = 0.0;
+            if ((st = time_cfg(mb, reps, &v)) != GWAS_OK) break;
             ++tried;
-            if (per_snp < best) {
-                best = per_snp;
-                best_cfg = cfg;
-                best_mb = mb;
-            }
+            coarse.push_back({v, cfg, mb});
         }
         if (st != GWAS_OK) break;
+    }
+    std::stable_sort(coarse.begin(), coarse.end(),
+                     [](const Cand& a, const Cand& b) { return a.per_snp < b.per_snp; });
+    if (coarse.size() > 4) coarse.resize(4);
+    std::vector<double> fine(coarse.size(), 1e300);
+    for (int round = 0; round < 3 && st == GWAS_OK && coarse.size() > 1; ++round) {
+        for (size_t k = 0; k < coarse.size() && st == GWAS_OK; ++k) {
+            double v = 0.0;
+            if ((st = gwas_set_tile_cfg(c, coarse[k].cfg)) != GWAS_OK) break;
+            if ((st = time_cfg(coarse[k].mb, 2 * reps, &v)) != GWAS_OK) break;
+            fine[k] = std::min(fine[k], v);
+        }
+    }
+    double best = 1e300;
+    int best_cfg = saved_cfg;
+    int64_t best_mb = mbs.back();
+    for (size_t k = 0; k < coarse.size(); ++k) {
+        const double v = coarse.size() > 1 ? fine[k] : coarse[k].per_snp;
+        if (v < best) {
+            best = v;
+            best_cfg = coarse[k].cfg;
+            best_mb = coarse[k].mb;
+        }
     }
     c->ev_pool.push_back(e0);
     c->ev_pool.push_back(e1);

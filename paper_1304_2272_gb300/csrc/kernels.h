@@ -132,10 +132,14 @@ struct MixedDev {
 
 int mixed_linear_n(int S, int R_e);
 cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk);
-// Exponents and BF16 limbs of W = L^{-1} (lower triangle) and Z (n x R_e), tensor maps.
+// Exponents and BF16 limbs of W = L^{-1} (lower triangle) and Z (n x R_e) into m.WL / m.E
+// (limbs.cu).
+cudaError_t launch_limb_split(MixedDev& m, const double* W, int64_t ldw, const double* Z,
+                              cudaStream_t s, int64_t* launches);
+// launch_limb_split, then the tensor maps over m's buffers.
 cudaError_t mixed_prepare(MixedDev& m, const double* W, int64_t ldw, const double* Z,
                           cudaStream_t s, int64_t* launches);
-// Dosages (n x mb int8, column-major) -> BF16 rows of m.Xb and bad-dosage flags.
+// Dosages (n x mb int8, column-major) -> BF16 rows of m.Xb and bad-dosage flags (limbs.cu).
 cudaError_t launch_geno_bf16(const MixedDev& m, const int8_t* X, int64_t ldx, int64_t mb,
                              uint8_t* bad, cudaStream_t s);
 // The tcgen05 kernel: row-tile partials of S_BRi into m.sq_part, S_BLi / bbar_Bi into m.lin.
