@@ -215,6 +215,18 @@ def traffic_for(kernel: str, n: int, m_blk: int, tile_cfg=None):
     return rec["bytes"] if sha == rec["sha"] else None
 
 
+def pack_2bit_torch(Xd):
+    """(mb, n) device dosages in {0,1,2} -> (mb, ceil(n/4)) uint8 2-bit calls, four
+    individuals per byte (individual k in bits 2(k%4), 2(k%4)+1 of byte k/4)."""
+    import torch
+    mb, n = Xd.shape
+    nb = -(-n // 4)
+    pad = torch.zeros((mb, 4 * nb), dtype=torch.uint8, device=Xd.device)
+    pad[:, :n] = Xd.to(torch.uint8)
+    q = pad.view(mb, nb, 4)
+    return (q[..., 0] | (q[..., 1] << 2) | (q[..., 2] << 4) | (q[..., 3] << 6)).contiguous()
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -382,6 +394,25 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
         e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
         e2e = {"value": job_rate(steps * mb, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": n * mb, "d2h_bytes_per_step": mb * (t * p * 8 + t * 8 + 1)}
+        # secondary roofline: the dosage stream's H2D rate, and how much of the
+        # device-resident rate survives streaming (1.0 = copies fully hidden)
+        e2e["h2d_gbs"] = n * mb * steps * world / e2e_s / 1e9
+        e2e["streamed_over_resident"] = e2e["value"] / value
+        # the same stream as 2-bit calls (n/4 bytes per SNP), unpacked on the GPU
+        ppool = [pack_2bit_torch(x).cpu().pin_memory() for x in pool[:2]]
+        for s in range(warmup):
+            gwas.gwas_solve_block_packed(ctx, ppool[s % 2], mb, gwas.CODE_DOSAGE, hb, hw, hs)
+        gwas.gwas_sync(ctx)
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(steps):
+            gwas.gwas_solve_block_packed(ctx, ppool[s % 2], mb, gwas.CODE_DOSAGE, hb, hw, hs)
+        gwas.gwas_sync(ctx)
+        barrier()
+        pk_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e["packed_2bit"] = {"value": job_rate(steps * mb, world, pk_s), "unit": UNIT,
+                              "h2d_bytes_per_step": ppool[0].numel(),
+                              "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]}
 
     q = p - 1
     launch_ms = stats["trsm_ms"] / max(1, stats["trsm_launches"])

@@ -165,6 +165,32 @@ gwas_status gwas_solve_block_device(gwas_ctx* ctx, const int8_t* X, int64_t mb, 
                                     double* wald, uint8_t* status);
 
 /*
+ * 2-bit packed genotype calls (the paper streams FP64 genotypes; this packs four calls
+ * per byte, so a block's host -> device copy is n/4 bytes per SNP instead of n). Xp
+ * holds mb SNP columns of ceil(n/4) bytes each; individual k of a column sits in bits
+ * 2(k%4) and 2(k%4)+1 of byte k/4 (the unused bits of a column's last byte are
+ * ignored). A call c in {0,1,2,3} stands for dosage code[c]; a code outside {0,1,2}
+ * marks a missing or invalid call and gives the SNP status 2 with NaN outputs, like a
+ * bad int8 dosage (e.g. {0,1,2,-1} for calls that are dosages, or {2,-1,1,0} for a
+ * SNP-major PLINK .bed block with the dosage of its first allele). code: host array of
+ * 4 int8, read during the call. The calls are unpacked on the GPU into the int8 layout
+ * of gwas_solve_block, after which everything is identical, so results equal those of
+ * gwas_solve_block on the unpacked dosages bit for bit.
+ * gwas_solve_block_packed: Xp and the outputs in HOST memory, asynchronous and double
+ * buffered as gwas_solve_block. gwas_solve_block_packed_device: every pointer in DEVICE
+ * memory, ordered on gwas_stream() as gwas_solve_block_device; the unpacked block goes to
+ * a device buffer of n x m_blk bytes allocated on first use.
+ * Errors: GWAS_ERR_ARG (NULL pointer or code, mb out of 1..m_blk), GWAS_ERR_STATE (no
+ * factor), GWAS_ERR_OOM, GWAS_ERR_CUDA.
+ */
+gwas_status gwas_solve_block_packed(gwas_ctx* ctx, const uint8_t* Xp, int64_t mb,
+                                    const int8_t* code, double* b, double* wald,
+                                    uint8_t* status);
+gwas_status gwas_solve_block_packed_device(gwas_ctx* ctx, const uint8_t* Xp, int64_t mb,
+                                           const int8_t* code, double* b, double* wald,
+                                           uint8_t* status);
+
+/*
  * Algorithm 2 end to end on host memory: m SNPs (n x m int8, column-major) in
  * blocks of m_blk, double-buffered, then gwas_sync(-1). Outputs as above with m
  * in place of mb. Errors as gwas_solve_block.
@@ -229,7 +255,8 @@ gwas_status gwas_solve_block_grad_device(gwas_ctx* ctx, const int8_t* X, int64_t
  * Change the kernel tile configuration of a context (see gwas_opts.tile_cfg). For a
  * GWAS_PREC_MIXED context whose limb tile height changes, the BF16 limbs are re-split
  * from the FP64 L^{-1} kept by gwas_factor (no new factorisation). Synchronises the
- * context. Errors: GWAS_ERR_ARG, GWAS_ERR_CUDA, GWAS_ERR_OOM.
+ * context. Errors: GWAS_ERR_ARG, GWAS_ERR_CUDA, GWAS_ERR_OOM, GWAS_ERR_UNSUPPORTED (no kernel
+ * is built for the layout the bits select; the previous configuration stays).
  */
 gwas_status gwas_set_tile_cfg(gwas_ctx* ctx, int tile_cfg);
 

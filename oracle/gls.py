@@ -362,3 +362,17 @@ def gls(phi_or_M, h, sigma2, XL, Y, X, is_phi: bool = True, route: str = "hoiste
     if route == "per_snp":
         return gls_per_snp(L, XL, Y, X)
     return gls_hoisted(L, XL, Y, X)
+
+
+def gls_multitrait(phi, hs, sigma2s, XL, Y, X, route: str = "hoisted"):
+    """Section 5's multi-trait problem, b_ij = (X_i^T M_j^-1 X_i)^-1 X_i^T M_j^-1 y_j with
+    M_j = sigma2_j (h_j Phi + (1 - h_j) I): every trait j is Eq. (1) with its own M_j and
+    phenotype column y_j, for the same SNPs. Returns b (m x t x p), wald (m x t) and
+    status (m x t), one column per trait."""
+    Y = np.asarray(Y, dtype=np.float64).reshape(np.asarray(XL).shape[0], -1)
+    outs = [gls(phi, h, s2, XL, Y[:, j:j + 1], X, route=route)
+            for j, (h, s2) in enumerate(zip(hs, sigma2s))]
+    b = np.concatenate([o[0] for o in outs], axis=1)
+    wald = np.concatenate([o[1] for o in outs], axis=1)
+    status = np.stack([o[2] for o in outs], axis=1)
+    return b, wald, status

@@ -32,6 +32,8 @@ from .gwas import (  # noqa: F401
     gwas_solve_block,
     gwas_solve_block_device,
     gwas_solve_block_noalloc,
+    gwas_solve_block_packed,
+    gwas_solve_block_packed_device,
     gwas_reml,
     gwas_set_tile_cfg,
     gwas_solve_block_grad_device,

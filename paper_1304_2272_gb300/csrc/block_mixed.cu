@@ -730,6 +730,7 @@ static cudaError_t launch_pair_t(const MixedDev& m, int64_t mb, int num_sms, cud
     X(3, mx::rows_pair(3), 3 * mx::rows_pair(3))                    \
     X(4, mx::rows_single(4), 4 * mx::rows_single(4))                \
     X(5, mx::rows_single(5), 5 * mx::rows_single(5))                \
+    X(5, mx::rows_single(5), 256)                                   \
     X(5, mx::rows_pair(5), 5 * mx::rows_pair(5))
 
 cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
@@ -745,6 +746,14 @@ cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaS
     GWAS_MIXED_SHAPES(GWAS_TRY)
 #undef GWAS_TRY
     return cudaErrorInvalidValue;
+}
+
+bool mixed_shape_built(const MixedDev& m) {
+#define GWAS_HAS(SS, RR, NN) \
+    if (m.S == SS && m.R == RR && m.NT == NN) return !m.pair || (NN) % 32 == 0;
+    GWAS_MIXED_SHAPES(GWAS_HAS)
+#undef GWAS_HAS
+    return false;
 }
 
 // ---- batched cohorts: one persistent launch over a device table of cohorts ----------

@@ -40,6 +40,8 @@ struct gwas_ctx {
     double* bslot[2] = {nullptr, nullptr};
     double* wslot[2] = {nullptr, nullptr};
     uint8_t* sslot[2] = {nullptr, nullptr};
+    uint8_t* Pslot[2] = {nullptr, nullptr};  // 2-bit packed host blocks (first use)
+    int8_t* Xunpack = nullptr;    // unpacked dosages of gwas_solve_block_packed_device
     double* part = nullptr;       // row-tile partial sums
     int64_t ldp = 0;
     uint8_t* bad = nullptr;
@@ -54,6 +56,7 @@ struct gwas_ctx {
     double* small = nullptr;      // G1, G2, PhiZ and scalars
     bool grad_ready = false;
     double grad_h = 0.0, grad_s2 = 0.0;
+    bool ones_singular = false;   // the all-ones SNP is collinear with X_L (mixed path)
     int num_sms = 0;
     cudaStream_t s_comp = nullptr, s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
@@ -106,6 +109,7 @@ CohortDev cohort_view(const gwas_ctx* c) {
     v.n = c->n; v.q = c->q; v.t = c->t;
     v.W = c->W; v.ldw = c->ld;
     v.XLbar = c->XLbar; v.Ybar = c->Ybar; v.S_TL = c->S_TL; v.bbar_T = c->bbar_T;
+    v.ones_singular = c->ones_singular;
     return v;
 }
 
@@ -202,12 +206,13 @@ cudaError_t mixed_alloc_layout(MixedDev& m) {
 void free_all(gwas_ctx* c) {
     cudaFree(c->L); cudaFree(c->W); cudaFree(c->Dinv); cudaFree(c->XLbar); cudaFree(c->Ybar);
     cudaFree(c->S_TL); cudaFree(c->bbar_T); cudaFree(c->d_info); cudaFree(c->part);
-    cudaFree(c->bad);
+    cudaFree(c->bad); cudaFree(c->Xunpack);
     cudaFree(c->Phi); cudaFree(c->Minv); cudaFree(c->part2); cudaFree(c->small);
     cudaFree(c->Z); cudaFree(c->mx.WL); cudaFree(c->mx.bits); cudaFree(c->mx.E);
     cudaFree(c->mx.Xb); cudaFree(c->mx.sq_part); cudaFree(c->mx.lin); cudaFree(c->mx.err);
     for (int s = 0; s < 2; ++s) {
         cudaFree(c->Xslot[s]); cudaFree(c->bslot[s]); cudaFree(c->wslot[s]); cudaFree(c->sslot[s]);
+        cudaFree(c->Pslot[s]);
         if (c->ev_h2d[s]) cudaEventDestroy(c->ev_h2d[s]);
         if (c->ev_comp[s]) cudaEventDestroy(c->ev_comp[s]);
         if (c->ev_d2h[s]) cudaEventDestroy(c->ev_d2h[s]);
@@ -290,6 +295,11 @@ gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx**
         MixedDev& m = c->mx;
         apply_tile_cfg(m, o.tile_cfg);
         mixed_layout(m, n, o.n_limbs, c->q + t, o.m_blk);
+        if (!mixed_shape_built(m)) {
+            free_all(c);
+            delete c;
+            return GWAS_ERR_UNSUPPORTED;
+        }
         CKI(dmalloc(&c->Z, (size_t)n * (c->q + t)));
         CKI(mixed_alloc_layout(m));
         CKI(dmalloc(&m.Xb, (size_t)m.mb_pad_max * m.n_pad));
@@ -379,9 +389,36 @@ gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double 
             CK(mixed_prepare(c->mx, c->W, ld, c->Z, s, &nl));
         }
     }
+    // Mixed path: a SNP whose dosages are all equal is exactly collinear with X_L when the
+    // all-ones column is, a pivot the limb arithmetic cannot resolve against the
+    // 1e-12 threshold. Decide it once the way the FP64 path decides any SNP: one FP64
+    // block solve of a column of ones.
+    TmpDev probe_buf;
+    uint8_t* probe_st = nullptr;
+    if (c->mixed) {
+        const int64_t nt = ceil_div(n, T64), nred = c->q + 1 + c->t, ldp = 32;
+        const size_t part_b = (size_t)nt * nred * ldp * sizeof(double);
+        const size_t b_b = round_up((int64_t)c->t * c->p * sizeof(double), 256);
+        const size_t ones_b = round_up(n, 256);
+        CK(cudaMalloc(&probe_buf.p, part_b + b_b + ones_b + 512));
+        double* part = (double*)probe_buf.p;
+        double* bo = (double*)((char*)probe_buf.p + part_b);
+        int8_t* ones = (int8_t*)((char*)probe_buf.p + part_b + b_b);
+        uint8_t* flags = (uint8_t*)ones + ones_b;
+        probe_st = flags + 256;
+        CK(cudaMemsetAsync(ones, 1, (size_t)n, s));
+        CohortDev cv = cohort_view(c);
+        cv.ones_singular = false;
+        CK(launch_block_fp64(cv, ones, n, 1, part, ldp, flags, s));
+        CK(launch_snp_solve(cv, part, ldp, (int)nt, flags, 1, bo, nullptr, probe_st, s));
+        nl += 3;
+    }
     CK(cudaEventRecord(f1, s));
     int info = 0;
+    uint8_t ones_status = 0;
     CK(cudaMemcpyAsync(&info, c->d_info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (probe_st)
+        CK(cudaMemcpyAsync(&ones_status, probe_st, 1, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, f0, f1);
@@ -389,6 +426,7 @@ gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double 
     c->ev_pool.push_back(f1);
     c->stats.factor_ms = ms;
     c->stats.factor_launches = nl;
+    c->ones_singular = (ones_status == 1);
     if (info != init) {
         c->err_index = info;
         char buf[128];
@@ -422,22 +460,33 @@ static gwas_status ensure_host_slots(gwas_ctx* c) {
     return GWAS_OK;
 }
 
-gwas_status gwas_solve_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, double* wald,
-                             uint8_t* status) {
-    gwas_status st = check_block_args(c, X, mb, b, status);
-    if (st != GWAS_OK) return st;
+// One block from HOST memory through the double-buffered slots: the upload (int8
+// dosages, or 2-bit calls unpacked on the compute stream) overlaps the previous
+// block's compute, whose outputs leave on the D2H stream.
+static gwas_status host_block(gwas_ctx* c, const void* X, bool packed, const int8_t* code,
+                              int64_t mb, double* b, double* wald, uint8_t* status) {
     DeviceGuard g(c->device);
+    gwas_status st;
     if ((st = ensure_host_slots(c)) != GWAS_OK) return st;
+    const int64_t pbytes = ceil_div(c->n, 4);
+    if (packed && !c->Pslot[0])
+        for (int k = 0; k < 2; ++k) CK(dmalloc(&c->Pslot[k], (size_t)pbytes * c->opts.m_blk));
     const int s = c->slot;
     c->slot ^= 1;
     const int64_t t = c->t, p = c->p;
+    const size_t in_bytes = packed ? (size_t)(pbytes * mb) : (size_t)(c->n * mb);
     // load_start: the slot's previous block must be consumed by the compute stream
     CK(cudaStreamWaitEvent(c->s_h2d, c->ev_comp[s], 0));
-    CK(cudaMemcpyAsync(c->Xslot[s], X, (size_t)c->n * mb, cudaMemcpyHostToDevice, c->s_h2d));
+    CK(cudaMemcpyAsync(packed ? (void*)c->Pslot[s] : (void*)c->Xslot[s], X, in_bytes,
+                       cudaMemcpyHostToDevice, c->s_h2d));
     CK(cudaEventRecord(c->ev_h2d[s], c->s_h2d));
     // load_wait, and the slot's previous outputs must have left for the host
     CK(cudaStreamWaitEvent(c->s_comp, c->ev_h2d[s], 0));
     CK(cudaStreamWaitEvent(c->s_comp, c->ev_d2h[s], 0));
+    if (packed) {
+        CK(launch_unpack_2bit(c->Pslot[s], c->n, mb, code, c->Xslot[s], c->s_comp));
+        c->stats.kernel_launches += 1;
+    }
     st = run_block(c, c->Xslot[s], mb, c->bslot[s], wald ? c->wslot[s] : nullptr, c->sslot[s]);
     if (st != GWAS_OK) return st;
     CK(cudaEventRecord(c->ev_comp[s], c->s_comp));
@@ -450,9 +499,38 @@ gwas_status gwas_solve_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b
                            cudaMemcpyDeviceToHost, c->s_d2h));
     CK(cudaMemcpyAsync(status, c->sslot[s], (size_t)mb, cudaMemcpyDeviceToHost, c->s_d2h));
     CK(cudaEventRecord(c->ev_d2h[s], c->s_d2h));
-    c->stats.h2d_bytes += c->n * mb;
+    c->stats.h2d_bytes += (int64_t)in_bytes;
     c->stats.d2h_bytes += mb * t * p * 8 + (wald ? mb * t * 8 : 0) + mb;
     return GWAS_OK;
+}
+
+gwas_status gwas_solve_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, double* wald,
+                             uint8_t* status) {
+    gwas_status st = check_block_args(c, X, mb, b, status);
+    if (st != GWAS_OK) return st;
+    return host_block(c, X, false, nullptr, mb, b, wald, status);
+}
+
+gwas_status gwas_solve_block_packed(gwas_ctx* c, const uint8_t* Xp, int64_t mb,
+                                    const int8_t* code, double* b, double* wald,
+                                    uint8_t* status) {
+    gwas_status st = check_block_args(c, (const int8_t*)Xp, mb, b, status);
+    if (st != GWAS_OK) return st;
+    if (!code) return fail(c, GWAS_ERR_ARG, "solve_block_packed: NULL code table");
+    return host_block(c, Xp, true, code, mb, b, wald, status);
+}
+
+gwas_status gwas_solve_block_packed_device(gwas_ctx* c, const uint8_t* Xp, int64_t mb,
+                                           const int8_t* code, double* b, double* wald,
+                                           uint8_t* status) {
+    gwas_status st = check_block_args(c, (const int8_t*)Xp, mb, b, status);
+    if (st != GWAS_OK) return st;
+    if (!code) return fail(c, GWAS_ERR_ARG, "solve_block_packed_device: NULL code table");
+    DeviceGuard g(c->device);
+    if (!c->Xunpack) CK(dmalloc(&c->Xunpack, (size_t)c->n * c->opts.m_blk));
+    CK(launch_unpack_2bit(Xp, c->n, mb, code, c->Xunpack, c->s_comp));
+    c->stats.kernel_launches += 1;
+    return run_block(c, c->Xunpack, mb, b, wald, status);
 }
 
 gwas_status gwas_solve_block_device(gwas_ctx* c, const int8_t* X, int64_t mb, double* b,
@@ -708,6 +786,11 @@ gwas_status gwas_set_tile_cfg(gwas_ctx* c, int tile_cfg) {
     const bool old_pair = m.pair, old_fused = m.fused;
     apply_tile_cfg(m, tile_cfg);
     mixed_layout(m, c->n, m.S, m.R_e, c->opts.m_blk);
+    if (!mixed_shape_built(m)) {
+        apply_tile_cfg(m, c->opts.tile_cfg);
+        mixed_layout(m, c->n, m.S, m.R_e, c->opts.m_blk);
+        return fail(c, GWAS_ERR_UNSUPPORTED, "gwas_set_tile_cfg: no kernel for that layout");
+    }
     c->opts.tile_cfg = tile_cfg;
     const bool relayout = m.R != old_R || m.NT != old_NT || m.fused != old_fused;
     if (relayout) {
@@ -784,7 +867,11 @@ gwas_status gwas_autotune(gwas_ctx* c, const int8_t* X, int64_t mb_max, int reps
     int tried = 0;
     gwas_status st = GWAS_OK;
     for (int cfg : cfgs) {
-        if ((st = gwas_set_tile_cfg(c, cfg)) != GWAS_OK) break;
+        if ((st = gwas_set_tile_cfg(c, cfg)) == GWAS_ERR_UNSUPPORTED) {
+            st = GWAS_OK;
+            continue;
+        }
+        if (st != GWAS_OK) break;
         for (int64_t mb : mbs) {
             double v = 0.0;
             if ((st = time_cfg(mb, reps, &v)) != GWAS_OK) break;
@@ -1017,13 +1104,26 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
             if (b->mixed) {
                 j.Xb = cx->mx.Xb;
                 j.n_pad = cx->mx.n_pad;
+                // cohorts given the same dosages (several traits of one cohort, each with
+                // its own M) convert them once and share the BF16 rows and flags
+                int src = c;
+                for (int e = 0; e < c; ++e) {
+                    if (X[e] == X[c] && mb[e] == mb[c] && b->ctx[e]->n == cx->n &&
+                        jobs[e].convert) {
+                        j.Xb = jobs[e].Xb;
+                        j.bad = jobs[e].bad;
+                        j.convert = 0;
+                        src = e;
+                        break;
+                    }
+                }
                 j.sq_part = cx->mx.sq_part;
                 j.lin = cx->mx.lin;
                 j.n_tiles_mx = cx->mx.n_rt;
                 j.lin_tiles = cx->mx.lin_tiles();
                 tab[c] = mixed_cohort_entry(cx->mx, mb[c], umx);
                 umx += mixed_cohort_units(cx->mx, mb[c]);
-                maps[3 * c + 0] = cx->mx.tmX;
+                maps[3 * c + 0] = b->ctx[src]->mx.tmX;
                 maps[3 * c + 1] = cx->mx.tmW;
                 maps[3 * c + 2] = cx->mx.tmE;
             } else {

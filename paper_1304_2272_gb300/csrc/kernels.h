@@ -56,7 +56,15 @@ struct CohortDev {
     const double* S_TL = nullptr;  // q x q, ld = q
     const double* bbar_T = nullptr;// q x t, ld = q
     bool dense = false;            // W is a full (not lower-triangular) matrix
+    // The all-ones SNP is collinear with X_L (decided once in FP64 by gwas_factor): a
+    // SNP whose dosages are all equal (bad-flag bit 1, set by the mixed path's dosage
+    // conversion) then gets status 1 without relying on the limb arithmetic's pivot.
+    bool ones_singular = false;
 };
+
+// Per-SNP dosage flags (the `bad` arrays): bit 0 = a dosage outside {0,1,2} (status 2);
+// bit 1 = every dosage equal (mixed path only).
+constexpr uint8_t FLAG_BAD_DOSAGE = 1, FLAG_CONSTANT = 2;
 
 // Number of per-SNP reduction values: q (S_BL) + 1 (S_BR) + t (bbar_B).
 __host__ __device__ inline int n_red(const CohortDev& c) { return c.q + 1 + c.t; }
@@ -131,6 +139,8 @@ struct MixedDev {
 };
 
 int mixed_linear_n(int S, int R_e);
+// true when a kernel for m's (S, R, NT, pair) layout is compiled in
+bool mixed_shape_built(const MixedDev& m);
 cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk);
 // Exponents and BF16 limbs of W = L^{-1} (lower triangle) and Z (n x R_e) into m.WL / m.E
 // (limbs.cu).
@@ -173,6 +183,7 @@ struct BatchJob {
     uint8_t* bad = nullptr;
     uint16_t* Xb = nullptr;      // mixed: BF16 rows [mb_pad][n_pad]
     int64_t n_pad = 0;
+    int convert = 1;             // mixed: 0 = Xb and bad are an earlier job's (same dosages)
     const double* sq_part = nullptr;  // mixed partials
     const double* lin = nullptr;
     int n_tiles_mx = 0;
@@ -223,6 +234,12 @@ cudaError_t launch_reml_assemble(const RemlDev& r, cudaStream_t s);
 cudaError_t launch_dbdh(const CohortDev& c, const double* part_fwd, double* part_adj,
                         int64_t ldp, int n_tiles, const double* G1, double scale,
                         const uint8_t* bad, int64_t mb, double* dbdh, cudaStream_t s);
+
+// ---- 2-bit packed genotypes (packed.cu) -------------------------------------------------
+// Xp: mb columns of ceil(n/4) bytes (4 calls per byte, individual k in bits 2(k%4)..+1
+// of byte k/4); call c becomes dosage code[c]. X: n x mb int8, ld = n.
+cudaError_t launch_unpack_2bit(const uint8_t* Xp, int64_t n, int64_t mb, const int8_t code[4],
+                               int8_t* X, cudaStream_t s);
 
 // ---- utilities (util.cu) ---------------------------------------------------------------
 cudaError_t launch_fill_dosages(int8_t* X, int64_t count, uint64_t seed, cudaStream_t s);

@@ -13,9 +13,10 @@ namespace gwas {
 // Dosages -> BF16 rows (one SNP per row, k contiguous), flags for bad dosages.
 // ----------------------------------------------------------------------------
 // One warp converts one SNP row: n dosages -> BF16 (0 -> 0x0000, 1 -> 0x3F80, 2 -> 0x4000),
-// returns nonzero (warp-wide) if a dosage is not in {0,1,2}. A row that starts on a
-// 16-byte boundary is read 16 dosages per lane (coalesced 512-byte warp loads); the
-// remainder, or a whole unaligned row, one dosage per lane.
+// returns the row's flags (warp-wide): FLAG_BAD_DOSAGE if a dosage is not in {0,1,2},
+// FLAG_CONSTANT if every dosage equals the first. A row that starts on a 16-byte
+// boundary is read 16 dosages per lane (coalesced 512-byte warp loads); the remainder,
+// or a whole unaligned row, one dosage per lane.
 __device__ __forceinline__ uint32_t bf16_pair(uint32_t v) {
     // v holds two 16-bit lanes with values in {0,1,2}: each becomes v * 0x80 + (v != 0) * 0x3F00
     const uint32_t nz = (v | (v >> 1)) & 0x00010001u;
@@ -30,7 +31,9 @@ __device__ __forceinline__ uint32_t bad_bytes(uint32_t w) {
 __device__ __forceinline__ int geno_row_warp(const int8_t* __restrict__ src, int64_t n,
                                              uint16_t* __restrict__ dst) {
     const int lane = threadIdx.x % 32;
-    uint32_t flag = 0;
+    const uint32_t first = (uint32_t)(uint8_t)src[0];
+    const uint32_t first4 = first * 0x01010101u;
+    uint32_t flag = 0, differ = 0;
     int64_t k0 = 0;
     if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
         const int64_t nv = n / 16;
@@ -43,6 +46,7 @@ __device__ __forceinline__ int geno_row_warp(const int8_t* __restrict__ src, int
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 flag |= bad_bytes(in[e]);
+                differ |= in[e] ^ first4;
                 o[2 * e] = bf16_pair(__byte_perm(in[e], 0u, 0x4140));
                 o[2 * e + 1] = bf16_pair(__byte_perm(in[e], 0u, 0x4342));
             }
@@ -54,9 +58,12 @@ __device__ __forceinline__ int geno_row_warp(const int8_t* __restrict__ src, int
     for (int64_t k = k0 + lane; k < n; k += 32) {
         const uint32_t v = (uint32_t)(uint8_t)src[k];
         flag |= v > 2u ? 1u : 0u;
+        differ |= v ^ first;
         dst[k] = (uint16_t)bf16_pair(v);
     }
-    return __any_sync(0xffffffffu, flag != 0);
+    const bool bad = __any_sync(0xffffffffu, flag != 0);
+    const bool varies = __any_sync(0xffffffffu, differ != 0);
+    return (bad ? FLAG_BAD_DOSAGE : 0) | (varies ? 0 : FLAG_CONSTANT);
 }
 
 constexpr int GENO_WARPS = 8;
@@ -66,12 +73,12 @@ k_geno_bf16(const int8_t* __restrict__ X, int64_t ldx, int64_t n, int64_t mb,
             uint16_t* __restrict__ Xb, int64_t n_pad, uint8_t* __restrict__ bad) {
     const int64_t w0 = (int64_t)blockIdx.x * GENO_WARPS + threadIdx.x / 32;
     for (int64_t j = w0; j < mb; j += (int64_t)gridDim.x * GENO_WARPS) {
-        const int flag = geno_row_warp(X + j * ldx, n, Xb + j * n_pad);
-        if (threadIdx.x % 32 == 0) bad[j] = (uint8_t)(flag != 0);
+        const int flags = geno_row_warp(X + j * ldx, n, Xb + j * n_pad);
+        if (threadIdx.x % 32 == 0) bad[j] = (uint8_t)flags;
     }
 }
 
-// Batched cohorts: one warp per SNP of every cohort.
+// Batched cohorts: one warp per SNP of every cohort that owns its BF16 rows.
 __global__ void __launch_bounds__(GENO_WARPS * 32)
 k_geno_bf16_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps) {
     const int64_t w0 = (int64_t)blockIdx.x * GENO_WARPS + threadIdx.x / 32;
@@ -84,9 +91,9 @@ k_geno_bf16_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps)
         }
         const BatchJob& jb = jobs[lo];
         const int64_t j = g - jb.snp_base;
-        if (j >= jb.mb) continue;  // uniform across the warp
-        const int flag = geno_row_warp(jb.X + j * jb.c.n, jb.c.n, jb.Xb + j * jb.n_pad);
-        if (threadIdx.x % 32 == 0) jb.bad[j] = (uint8_t)(flag != 0);
+        if (j >= jb.mb || !jb.convert) continue;  // uniform across the warp
+        const int flags = geno_row_warp(jb.X + j * jb.c.n, jb.c.n, jb.Xb + j * jb.n_pad);
+        if (threadIdx.x % 32 == 0) jb.bad[j] = (uint8_t)flags;
     }
 }
 

@@ -90,7 +90,9 @@ __device__ __forceinline__ void solve_snp(const CohortDev& c, const Red& red,
             C[r][j] = s / C[j][j];
         }
     }
-    const uint8_t st = bad[i] ? 2 : (ok ? 0 : 1);
+    const uint8_t fl = bad[i];
+    const bool collinear = (fl & FLAG_CONSTANT) && c.ones_singular;
+    const uint8_t st = (fl & FLAG_BAD_DOSAGE) ? 2 : ((ok && !collinear) ? 0 : 1);
     const double nanv = nan("");
     const double cpp2 = C[p - 1][p - 1] * C[p - 1][p - 1];  // 1 / (S_i^{-1})_pp
     for (int j = 0; j < t; ++j) {

@@ -87,6 +87,8 @@ SIGNATURES = {
     "gwas_factor": (_int, [_ctx_p, _vp, _int, _dbl, _dbl, _vp, _vp]),
     "gwas_solve_block": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp]),
     "gwas_solve_block_device": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp]),
+    "gwas_solve_block_packed": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "gwas_solve_block_packed_device": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp, _vp]),
     "gwas_solve_all": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp]),
     "gwas_sync": (_int, [_ctx_p, _int]),
     "gwas_finalize": (_int, [_ctx_p]),
@@ -206,6 +208,31 @@ def gwas_solve_block(ctx, X, mb: int, b, wald, status) -> None:
 def gwas_solve_block_device(ctx, X, mb: int, b, wald, status) -> None:
     _check(ctx, load().gwas_solve_block_device(ctx, _addr(X), int(mb), _addr(b), _addr(wald),
                                                _addr(status)))
+
+
+# 2-bit call -> dosage tables: calls that are dosages (3 = missing), and SNP-major PLINK
+# .bed calls (00 two copies of the first allele, 01 missing, 10 one copy, 11 none).
+CODE_DOSAGE = (0, 1, 2, -1)
+CODE_PLINK_BED = (2, -1, 1, 0)
+
+
+def _code(code) -> ctypes.Array:
+    vals = [int(v) for v in code]
+    if len(vals) != 4 or any(v < -128 or v > 127 for v in vals):
+        raise ValueError("code: four int8 dosages, one per 2-bit call")
+    return (ctypes.c_int8 * 4)(*vals)
+
+
+def gwas_solve_block_packed(ctx, Xp, mb: int, code, b, wald, status) -> None:
+    """Xp: HOST uint8 array of mb columns of ceil(n/4) bytes (F-order ceil(n/4) x mb)."""
+    _require(Xp, np.uint8, "Xp")
+    _check(ctx, load().gwas_solve_block_packed(ctx, _addr(Xp), int(mb), _code(code), _addr(b),
+                                               _addr(wald), _addr(status)))
+
+
+def gwas_solve_block_packed_device(ctx, Xp, mb: int, code, b, wald, status) -> None:
+    _check(ctx, load().gwas_solve_block_packed_device(ctx, _addr(Xp), int(mb), _code(code),
+                                                      _addr(b), _addr(wald), _addr(status)))
 
 
 def gwas_solve_all(ctx, X, m: int, b, wald, status) -> None:

@@ -141,3 +141,21 @@ def genotypes_torch(seed: int, n: int, m: int, device, freqs=None):
     a = (torch.rand((m, n), generator=g, device=device) < f).to(torch.int8)
     a += (torch.rand((m, n), generator=g, device=device) < f).to(torch.int8)
     return a
+
+
+def pack_2bit(X: np.ndarray, call_of=(0, 1, 2), missing_call: int = 3) -> np.ndarray:
+    """Pack int8 dosages (n x m) into 2-bit calls, four individuals per byte: column j
+    becomes ceil(n/4) bytes, individual k in bits 2(k%4), 2(k%4)+1 of byte k/4. Dosage d
+    in {0,1,2} becomes call ``call_of[d]``; any other value becomes ``missing_call``.
+    Returns a (ceil(n/4) x m) uint8 array in F-order."""
+    X = np.asarray(X)
+    n, m = X.shape
+    calls = np.full(X.shape, missing_call, dtype=np.uint8)
+    for d in range(3):
+        calls[X == d] = call_of[d]
+    nb = -(-n // 4)
+    padded = np.zeros((4 * nb, m), dtype=np.uint8)
+    padded[:n] = calls
+    q = padded.reshape(nb, 4, m)
+    out = q[:, 0] | (q[:, 1] << 2) | (q[:, 2] << 4) | (q[:, 3] << 6)
+    return np.asfortranarray(out.astype(np.uint8))

@@ -30,3 +30,21 @@ def test_traffic_guard_rejects_other_shapes_and_groupings():
     got = bench.traffic_for("k_block_mixed<3>", n, mb, 8832)
     assert got is None or got == rec["bytes"]   # None once the kernel source changes
     assert got == bench.traffic_for("k_block_mixed<3>", n, mb, -1)
+
+
+def test_pack_2bit_layout():
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(3)
+    for n in (1, 4, 5, 11):
+        X = rng.integers(-1, 4, size=(n, 6)).astype(np.int8)
+        for call_of, miss in (((0, 1, 2), 3), ((3, 2, 0), 1)):
+            P = synth.pack_2bit(X, call_of=call_of, missing_call=miss)
+            assert P.shape == (-(-n // 4), 6) and P.flags.f_contiguous
+            for j in range(6):
+                for k in range(n):
+                    d = int(X[k, j])
+                    want = call_of[d] if d in (0, 1, 2) else miss
+                    assert (int(P[k // 4, j]) >> (2 * (k % 4))) & 3 == want
+                for k in range(n, 4 * P.shape[0]):      # padding calls are zero
+                    assert (int(P[k // 4, j]) >> (2 * (k % 4))) & 3 == 0

@@ -190,6 +190,49 @@ def test_S_formed_symmetric():
     assert np.all(np.linalg.eigvalsh(S) > 0)
 
 
+# ------------------------------------------------ multi-trait (Section 5) ---
+def test_multitrait_matches_exact_rational_per_trait():
+    """Two traits with M_1 = Phi + I (h = 1/2, sigma^2 = 2) and M_2 = Phi + 3 I
+    (h = 1/4, sigma^2 = 4), integer Phi: each b_ij against exact rational Eq. (1)."""
+    rng = np.random.default_rng(7)
+    n, q = 7, 2
+    A = rng.integers(-2, 3, size=(n, n))
+    phi = (A @ A.T).astype(float)
+    XL = np.ones((n, q))
+    XL[:, 1] = rng.integers(-3, 4, size=n)
+    X = rng.integers(0, 3, size=(n, 3)).astype(np.int8)
+    Y = rng.integers(-5, 6, size=(n, 2)).astype(float)
+    b, w, s = G.gls_multitrait(phi, [0.5, 0.25], [2.0, 4.0], XL, Y, X)
+    assert b.shape == (3, 2, q + 1) and s.shape == (3, 2)
+    for j, shift in enumerate((1, 3)):
+        Mj = (phi + shift * np.eye(n)).astype(int).tolist()
+        for i in range(3):
+            Xi = np.hstack([XL, X[:, i:i + 1]]).astype(int).tolist()
+            bx, wx = E.gls_exact(Mj, Xi, Y[:, j].astype(int).tolist())
+            assert s[i, j] == 0
+            assert rel_b(b[i, j], np.array([float(v) for v in bx])) <= 1e-11
+            assert abs(w[i, j] - float(wx)) <= 1e-10 * max(1.0, float(wx))
+
+
+def test_multitrait_with_one_M_is_the_multi_phenotype_solve():
+    """Equal (h, sigma^2) for every trait: one shared M, i.e. t phenotype columns."""
+    c, X = small_case(13, 90, 12, t=3)
+    b, w, s = G.gls_multitrait(c.phi, [c.h] * 3, [c.sigma2] * 3, c.XL, c.Y, X)
+    rb, rw, rs = G.gls(c.phi, c.h, c.sigma2, c.XL, c.Y, X, route="explicit")
+    assert rel_b(b, rb) <= 1e-11
+    assert np.all(s == rs[:, None])
+
+
+def test_multitrait_trait_order():
+    c, X = small_case(14, 80, 9, t=3)
+    hs, s2 = [0.1, 0.5, 0.8], [1.0, 0.6, 2.0]
+    b, w, s = G.gls_multitrait(c.phi, hs, s2, c.XL, c.Y, X)
+    perm = [2, 0, 1]
+    bp, wp, sp = G.gls_multitrait(c.phi, [hs[k] for k in perm], [s2[k] for k in perm],
+                                  c.XL, c.Y[:, perm], X)
+    assert np.array_equal(bp, b[:, perm]) and np.array_equal(wp, w[:, perm])
+
+
 # ------------------------------------------------------- degenerate SNPs -----
 def test_degenerate_and_bad_snps():
     c, X = small_case(12, 60, 6)

@@ -117,6 +117,41 @@ def test_mixed_ragged(gwas, variant, limbs, n, m, p, t, mblk):
           limbs)
 
 
+@pytest.mark.parametrize("limbs", [2, 3, 5])
+@pytest.mark.parametrize("n,t", [(1000, 2), (257, 1)])
+def test_constant_snps_are_singular_with_an_intercept(gwas, limbs, n, t):
+    """A SNP with every dosage equal is exactly collinear with the intercept column: the
+    oracle's pivot test flags it; the limb arithmetic decides it exactly (integer test
+    of the dosages, FP64 test of the all-ones column at factor time)."""
+    c = synth.make_cohort(300 + n, n, t=t, n_markers=400)
+    X = c.snps(40).copy(order="F")
+    X[:, 3] = 1
+    X[:, 7] = 2
+    X[:, 9] = 0
+    out = run(gwas, c, X, limbs=limbs, m_blk=64)
+    ref = oracle(c, X)
+    assert list(ref[2][[3, 7, 9]]) == [1, 1, 1]
+    check(out, ref, limbs)
+
+
+@pytest.mark.parametrize("limbs", [3, 5])
+def test_constant_snp_without_intercept_is_solved(gwas, limbs):
+    """Without an intercept in X_L a constant SNP is an ordinary regressor."""
+    c = synth.make_cohort(41, 600, n_markers=400)
+    XL = np.asfortranarray(c.XL[:, 1:])
+    X = c.snps(30).copy(order="F")
+    X[:, 2] = 1
+    X[:, 5] = 2
+    X[:, 8] = 0
+    with gwas.GLS(c.n, XL.shape[1] + 1, 1, precision=gwas.GWAS_PREC_MIXED, n_limbs=limbs,
+                  m_blk=64) as e:
+        e.factor(c.phi, c.h, c.sigma2, XL, c.Y)
+        out = e.solve(X)
+    ref = G.gls(c.phi, c.h, c.sigma2, XL, c.Y, X)
+    assert list(ref[2][[2, 5, 8]]) == [0, 0, 1]
+    check(out, ref, limbs)
+
+
 def test_mixed_degenerate_and_bad(gwas):
     c = synth.make_cohort(12, 300, n_markers=400)
     X = c.snps(70).copy(order="F")
