@@ -169,14 +169,16 @@ def bf16_flops_per_snp(n: int, q: int, t: int, limbs: int) -> float:
 # DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the bench's own launch shape), valid only
 # while the kernel source is the one captured (first 16 hex digits of its sha256) and, for
-# the limb kernel, while the L2 group size and the CTA-pair / fused-row choice are the
-# captured ones (the traffic depends on those, not on the pipeline depth).
+# the limb kernel, per L2 group size (captured with CTA pairs and fused rows; the traffic
+# depends on those, not on the pipeline depth).
 TRAFFIC = {
     "k_block_fp64": {"file": "block_fp64.cu", "sha": "17f101cf32e7945d", "n": 10000,
                      "m_blk": 16384, "bytes": 8830753024 + 101610496},
-    "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "a7fb685ba00e422f", "n": 10000,
-                         "m_blk": 16384, "group_mb": 40, "single_cta": False, "no_fuse": False,
-                         "bytes": 4063346176 + 81304064},
+    "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "1af7a5f567e776ec", "n": 10000,
+                         "m_blk": 16384, "single_cta": False, "no_fuse": False,
+                         "bytes_by_group_mb": {40: 4048532736 + 81214976,
+                                               80: 4555761920 + 79603968,
+                                               160: 8115475456 + 76000768}},
 }
 
 
@@ -202,17 +204,19 @@ def traffic_for(kernel: str, n: int, m_blk: int, tile_cfg=None):
     rec = TRAFFIC.get(kernel)
     if not rec or rec["n"] != n or rec["m_blk"] != m_blk:
         return None
-    if "group_mb" in rec:
+    nbytes = rec.get("bytes")
+    if "bytes_by_group_mb" in rec:
         f = tile_cfg_fields(tile_cfg)
-        if any(f[k] != rec[k] for k in ("group_mb", "single_cta", "no_fuse")):
+        if any(f[k] != rec[k] for k in ("single_cta", "no_fuse")):
             return None
+        nbytes = rec["bytes_by_group_mb"].get(f["group_mb"])
     path = os.path.join(ROOT, "paper_1304_2272_gb300", "csrc", rec["file"])
     try:
         with open(path, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()[:16]
     except OSError:
         return None
-    return rec["bytes"] if sha == rec["sha"] else None
+    return nbytes if sha == rec["sha"] else None
 
 
 def pack_2bit_torch(Xd):

@@ -983,10 +983,10 @@ gwas_status batch_enqueue(gwas_batch* b) {
         CKB(launch_geno_bf16_batch(b->d_jobs, nc, b->total_snps, b->s));
         CKB(launch_block_mixed_batch(b->d_tab, b->d_maps, nc, b->units_mx, b->ctx[0]->mx,
                                      b->stages, b->d_err, b->ctx[0]->num_sms, b->s));
-        CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, b->q + 1 + b->t, true, b->s));
+        CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, b->p, b->q + 1 + b->t, true, b->s));
     } else {
         CKB(launch_block_fp64_batch(b->d_jobs, nc, b->units_fp64, b->s));
-        CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, b->q + 1 + b->t, false, b->s));
+        CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, b->p, b->q + 1 + b->t, false, b->s));
     }
     return GWAS_OK;
 }

@@ -197,9 +197,9 @@ cudaError_t launch_block_fp64_batch(const BatchJob* jobs, int n_jobs, int64_t n_
                                     cudaStream_t s);
 cudaError_t launch_geno_bf16_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps,
                                    cudaStream_t s);
-// max_nred: the largest q + 1 + t over the jobs.
-cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, int max_nred,
-                                   bool mixed, cudaStream_t s);
+// p: the jobs' common q + 1; max_nred: the largest q + 1 + t over the jobs.
+cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, int p,
+                                   int max_nred, bool mixed, cudaStream_t s);
 
 // ---- REML and db/dh (reml.cu) -----------------------------------------------------------
 

@@ -28,38 +28,71 @@ __device__ __forceinline__ uint32_t bad_bytes(uint32_t w) {
     return (w & 0xFCFCFCFCu) | (w & (w >> 1) & 0x01010101u);
 }
 
+// 16 dosages -> flags and 32 bytes of BF16 at dst (32-byte aligned).
+__device__ __forceinline__ void geno_chunk16(const uint32_t (&in)[4], uint32_t first4,
+                                             uint32_t& flag, uint32_t& differ, uint4* d) {
+    uint32_t o[8];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        flag |= bad_bytes(in[e]);
+        differ |= in[e] ^ first4;
+        o[2 * e] = bf16_pair(__byte_perm(in[e], 0u, 0x4140));
+        o[2 * e + 1] = bf16_pair(__byte_perm(in[e], 0u, 0x4342));
+    }
+    d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
 __device__ __forceinline__ int geno_row_warp(const int8_t* __restrict__ src, int64_t n,
                                              uint16_t* __restrict__ dst) {
     const int lane = threadIdx.x % 32;
     const uint32_t first = (uint32_t)(uint8_t)src[0];
     const uint32_t first4 = first * 0x01010101u;
     uint32_t flag = 0, differ = 0;
-    int64_t k0 = 0;
+    uint4* d4 = reinterpret_cast<uint4*>(dst);  // BF16 rows start on 128-byte boundaries
+    // dosages [head, body) go through 16-dosage chunks, the rest one per lane
+    int64_t head = 0, body = 0;
     if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-        const int64_t nv = n / 16;
         const uint4* s4 = reinterpret_cast<const uint4*>(src);
-        uint4* d4 = reinterpret_cast<uint4*>(dst);  // BF16 rows start on 128-byte boundaries
-        for (int64_t v = lane; v < nv; v += 32) {
+        body = (n / 16) * 16;
+        for (int64_t v = lane; v < n / 16; v += 32) {
             const uint4 w = __ldg(s4 + v);
             const uint32_t in[4] = {w.x, w.y, w.z, w.w};
-            uint32_t o[8];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                flag |= bad_bytes(in[e]);
-                differ |= in[e] ^ first4;
-                o[2 * e] = bf16_pair(__byte_perm(in[e], 0u, 0x4140));
-                o[2 * e + 1] = bf16_pair(__byte_perm(in[e], 0u, 0x4342));
-            }
-            d4[2 * v] = make_uint4(o[0], o[1], o[2], o[3]);
-            d4[2 * v + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+            geno_chunk16(in, first4, flag, differ, d4 + 2 * v);
         }
-        k0 = nv * 16;
+    } else {
+        // A row off a 16-byte boundary (n not a multiple of 16): chunk v >= 1 is assembled
+        // from the five aligned 32-bit words around it with byte perms. Those words hold
+        // row bytes 16v - 3 .. 16v + 19 at most, so chunk v is taken while 16v + 19 < n
+        // (chunk 0 and the tail go one dosage per lane).
+        const int mis = (int)(reinterpret_cast<uintptr_t>(src) & 3);
+        const uint32_t* wb = reinterpret_cast<const uint32_t*>(src - mis);
+        const uint32_t sel = (uint32_t)mis | ((uint32_t)(mis + 1) << 4) |
+                             ((uint32_t)(mis + 2) << 8) | ((uint32_t)(mis + 3) << 12);
+        const int64_t vmax = n >= 20 ? (n - 20) / 16 + 1 : 1;
+        head = n < 16 ? n : 16;
+        body = 16 * vmax;
+        for (int64_t v = 1 + lane; v < vmax; v += 32) {
+            uint32_t a[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) a[k] = __ldg(wb + 4 * v + k);
+            uint32_t in[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) in[k] = __byte_perm(a[k], a[k + 1], sel);
+            geno_chunk16(in, first4, flag, differ, d4 + 2 * v);
+        }
     }
-    for (int64_t k = k0 + lane; k < n; k += 32) {
+    auto one = [&](int64_t k) {
         const uint32_t v = (uint32_t)(uint8_t)src[k];
         flag |= v > 2u ? 1u : 0u;
         differ |= v ^ first;
         dst[k] = (uint16_t)bf16_pair(v);
+    };
+    if (head > 0) {
+        for (int64_t k = lane; k < head; k += 32) one(k);
+        for (int64_t k = (body > head ? body : head) + lane; k < n; k += 32) one(k);
+    } else {
+        for (int64_t k = body + lane; k < n; k += 32) one(k);
     }
     const bool bad = __any_sync(0xffffffffu, flag != 0);
     const bool varies = __any_sync(0xffffffffu, differ != 0);

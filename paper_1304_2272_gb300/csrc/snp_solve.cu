@@ -65,29 +65,41 @@ struct RedMixed {
     }
 };
 
-template <class Red>
+// P > 0: p known at compile time (every loop unrolls, the p x p factor lives in
+// registers); P = 0: any p <= MAX_P (arrays in local memory).
+template <int P, class Red>
 __device__ __forceinline__ void solve_snp(const CohortDev& c, const Red& red,
                                           const uint8_t* __restrict__ bad, int64_t i,
                                           double* __restrict__ b, double* __restrict__ wald,
                                           uint8_t* __restrict__ status) {
-    const int q = c.q, t = c.t, p = q + 1;
+    constexpr int PM = P > 0 ? P : MAX_P;
+    const int p = P > 0 ? P : c.q + 1;
+    const int q = p - 1, t = c.t;
 
-    double sbl[MAX_P];  // S_BLi (q values) then S_BRi
+    double sbl[PM];  // S_BLi (q values) then S_BRi
+#pragma unroll
     for (int v = 0; v < p; ++v) sbl[v] = red(v, i);
     // C C^T = S_i (C lower triangular, column by column).
-    double C[MAX_P][MAX_P];
+    double C[PM][PM];
+    double rc[PM];   // 1 / C_jj: one FP64 division per pivot (division is costly here)
     double smax = sbl[q];
+#pragma unroll
     for (int a = 0; a < q; ++a) smax = fmax(smax, c.S_TL[a + a * q]);
     bool ok = true;
+#pragma unroll
     for (int j = 0; j < p; ++j) {
         double d = (j < q) ? c.S_TL[j + j * q] : sbl[q];
+#pragma unroll
         for (int k = 0; k < j; ++k) d -= C[j][k] * C[j][k];
         if (!(d > SINGULAR_RTOL * smax)) { ok = false; d = 1.0; }
         C[j][j] = sqrt(d);
+        rc[j] = 1.0 / C[j][j];
+#pragma unroll
         for (int r = j + 1; r < p; ++r) {
             double s = (r < q) ? c.S_TL[r + j * q] : sbl[j];
+#pragma unroll
             for (int k = 0; k < j; ++k) s -= C[r][k] * C[j][k];
-            C[r][j] = s / C[j][j];
+            C[r][j] = s * rc[j];
         }
     }
     const uint8_t fl = bad[i];
@@ -96,18 +108,23 @@ __device__ __forceinline__ void solve_snp(const CohortDev& c, const Red& red,
     const double nanv = nan("");
     const double cpp2 = C[p - 1][p - 1] * C[p - 1][p - 1];  // 1 / (S_i^{-1})_pp
     for (int j = 0; j < t; ++j) {
-        double z[MAX_P];
+        double z[PM];
+#pragma unroll
         for (int r = 0; r < p; ++r) {
             double s = (r < q) ? c.bbar_T[r + (int64_t)j * q] : red(q + 1 + j, i);
+#pragma unroll
             for (int k = 0; k < r; ++k) s -= C[r][k] * z[k];
-            z[r] = s / C[r][r];
+            z[r] = s * rc[r];
         }
+#pragma unroll
         for (int r = p - 1; r >= 0; --r) {
             double s = z[r];
+#pragma unroll
             for (int k = r + 1; k < p; ++k) s -= C[k][r] * z[k];
-            z[r] = s / C[r][r];
+            z[r] = s * rc[r];
         }
         double* bo = b + (i * t + j) * p;
+#pragma unroll
         for (int r = 0; r < p; ++r) bo[r] = st ? nanv : z[r];
         if (wald) wald[i * t + j] = st ? nanv : z[p - 1] * z[p - 1] * cpp2;
     }
@@ -175,17 +192,31 @@ k_reduce_partials_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n
     reduce_set(ps, i, valid, sh);
 }
 
-template <class Red>
+template <int P, class Red>
 __global__ void __launch_bounds__(128)
 k_snp_solve(CohortDev c, Red red, const uint8_t* __restrict__ bad, int64_t mb,
             double* __restrict__ b, double* __restrict__ wald, uint8_t* __restrict__ status) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= mb) return;
-    solve_snp(c, red, bad, i, b, wald, status);
+    solve_snp<P>(c, red, bad, i, b, wald, status);
+}
+
+// One thread per SNP; p = 2, 3, 4 get their own unrolled kernels.
+template <class Red>
+cudaError_t launch_solve(const CohortDev& c, const Red& red, const uint8_t* bad, int64_t mb,
+                         double* b, double* wald, uint8_t* status, cudaStream_t s) {
+    const unsigned grid = (unsigned)ceil_div(mb, 128);
+    switch (c.q + 1) {
+        case 2: k_snp_solve<2><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status); break;
+        case 3: k_snp_solve<3><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status); break;
+        case 4: k_snp_solve<4><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status); break;
+        default: k_snp_solve<0><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status); break;
+    }
+    return cudaGetLastError();
 }
 
 // Batched cohorts: one thread per SNP of every cohort (partials already reduced).
-template <bool MIXED>
+template <int P, bool MIXED>
 __global__ void __launch_bounds__(128)
 k_snp_solve_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -195,10 +226,10 @@ k_snp_solve_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps)
     if (i >= j.mb) return;
     if (MIXED) {
         RedMixed red{j.sq_part, j.lin, j.ldp, 1, j.c.q, 1, j.c.q + j.c.t};
-        solve_snp(j.c, red, j.bad, i, j.b, j.wald, j.status);
+        solve_snp<P>(j.c, red, j.bad, i, j.b, j.wald, j.status);
     } else {
         RedFp64 red{j.part, j.ldp, 1, n_red(j.c)};
-        solve_snp(j.c, red, j.bad, i, j.b, j.wald, j.status);
+        solve_snp<P>(j.c, red, j.bad, i, j.b, j.wald, j.status);
     }
 }
 
@@ -221,13 +252,11 @@ cudaError_t launch_snp_solve(const CohortDev& c, double* part, int64_t ldp, int 
     if (mb <= 0) return cudaSuccess;
     cudaError_t e = launch_reduce_fp64(c, part, ldp, n_tiles, mb, s);
     if (e != cudaSuccess) return e;
-    RedFp64 red{part, ldp, 1, n_red(c)};
-    k_snp_solve<<<(unsigned)ceil_div(mb, 128), 128, 0, s>>>(c, red, bad, mb, b, wald, status);
-    return cudaGetLastError();
+    return launch_solve(c, RedFp64{part, ldp, 1, n_red(c)}, bad, mb, b, wald, status, s);
 }
 
-cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, int max_nred,
-                                   bool mixed, cudaStream_t s) {
+cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, int p,
+                                   int max_nred, bool mixed, cudaStream_t s) {
     if (n_snps <= 0) return cudaSuccess;
     const dim3 gr((unsigned)ceil_div(n_snps, 32), (unsigned)max_nred);
     if (mixed) k_reduce_partials_batch<true><<<gr, RED_WARPS * 32, 0, s>>>(jobs, n_jobs, n_snps);
@@ -235,8 +264,17 @@ cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_s
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)ceil_div(n_snps, 128);
-    if (mixed) k_snp_solve_batch<true><<<grid, 128, 0, s>>>(jobs, n_jobs, n_snps);
-    else k_snp_solve_batch<false><<<grid, 128, 0, s>>>(jobs, n_jobs, n_snps);
+    // every cohort of a batch has the same p
+#define GWAS_BATCH_SOLVE(PP)                                                          \
+    if (mixed) k_snp_solve_batch<PP, true><<<grid, 128, 0, s>>>(jobs, n_jobs, n_snps); \
+    else k_snp_solve_batch<PP, false><<<grid, 128, 0, s>>>(jobs, n_jobs, n_snps);
+    switch (p) {
+        case 2: GWAS_BATCH_SOLVE(2) break;
+        case 3: GWAS_BATCH_SOLVE(3) break;
+        case 4: GWAS_BATCH_SOLVE(4) break;
+        default: GWAS_BATCH_SOLVE(0) break;
+    }
+#undef GWAS_BATCH_SOLVE
     return cudaGetLastError();
 }
 
@@ -248,9 +286,8 @@ cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const 
     cudaError_t e = reduce_partials(RedMixed{m.sq_part, m.lin, m.ldp, m.n_rt, q, m.lin_tiles(), m.R_e},
                                     n_red(c), mb, s);
     if (e != cudaSuccess) return e;
-    RedMixed red{m.sq_part, m.lin, m.ldp, 1, q, 1, m.R_e};
-    k_snp_solve<<<(unsigned)ceil_div(mb, 128), 128, 0, s>>>(c, red, bad, mb, b, wald, status);
-    return cudaGetLastError();
+    return launch_solve(c, RedMixed{m.sq_part, m.lin, m.ldp, 1, q, 1, m.R_e}, bad, mb, b, wald,
+                        status, s);
 }
 
 }  // namespace gwas

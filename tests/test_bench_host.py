@@ -24,12 +24,15 @@ def test_traffic_guard_rejects_other_shapes_and_groupings():
     n, mb = rec["n"], rec["m_blk"]
     assert bench.traffic_for("k_block_mixed<3>", n + 1, mb) is None
     assert bench.traffic_for("k_block_mixed<3>", n, mb // 2) is None
-    assert bench.traffic_for("k_block_mixed<3>", n, mb, 160 << 4) is None
+    assert bench.traffic_for("k_block_mixed<3>", n, mb, 120 << 4) is None   # not captured
     assert bench.traffic_for("k_block_mixed<3>", n, mb, 1 << 12) is None
     assert bench.traffic_for("k_block_mixed<9>", n, mb) is None
-    got = bench.traffic_for("k_block_mixed<3>", n, mb, 8832)
-    assert got is None or got == rec["bytes"]   # None once the kernel source changes
-    assert got == bench.traffic_for("k_block_mixed<3>", n, mb, -1)
+    for g in (40, 80, 160):
+        got = bench.traffic_for("k_block_mixed<3>", n, mb, (1 << 13) | (g << 4))
+        # None once the kernel source changes
+        assert got is None or got == rec["bytes_by_group_mb"][g]
+    assert bench.traffic_for("k_block_mixed<3>", n, mb, 8832) == \
+        bench.traffic_for("k_block_mixed<3>", n, mb, -1)
 
 
 def test_pack_2bit_layout():
