@@ -1,0 +1,60 @@
+"""The largest cohort of the metric, n = 30,000 (the mixed-precision workload's n), in the
+benchmark's launch shapes: sampled SNPs against the oracle, FP64 (1e-10) and 3-limb mixed
+(1e-6) and 5-limb mixed (1e-10). Exercises the 64-bit index arithmetic of the limb
+buffers (rows x n_pad > 2^31) and the 2^24 exactness bound near its n limit."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gls as G
+
+pytestmark = pytest.mark.gpu
+
+N = 30000
+
+
+def rel_b(b, ref):
+    scale = np.maximum(np.nanmax(np.abs(ref), axis=-1, keepdims=True), 1e-300)
+    return float(np.nanmax(np.abs(b - ref) / scale))
+
+
+@pytest.fixture(scope="module")
+def gw(gpu):
+    from paper_1304_2272_gb300 import gwas as g
+    g.load()
+    return g
+
+
+@pytest.fixture(scope="module")
+def big():
+    c = synth.make_cohort(30, N, device="cuda")
+    return c, G.factor(c.phi, c.h, c.sigma2)
+
+
+@pytest.mark.parametrize("precision,limbs,mb,tol", [
+    ("fp64", 3, 1024, 1e-10), ("mixed", 3, 4096, 1e-6), ("mixed", 5, 4096, 1e-10)])
+def test_n30k_sampled(gw, big, precision, limbs, mb, tol):
+    import torch
+    c, L = big
+    prec = gw.GWAS_PREC_FP64 if precision == "fp64" else gw.GWAS_PREC_MIXED
+    Xd = synth.genotypes_torch(31, N, mb, "cuda")
+    Xd[17] = 1                      # constant: singular with the intercept
+    with gw.GLS(N, 4, 1, m_blk=mb, precision=prec, n_limbs=limbs) as e:
+        e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
+        bd = torch.empty((mb, 1, 4), dtype=torch.float64, device="cuda")
+        wd = torch.empty((mb, 1), dtype=torch.float64, device="cuda")
+        sd = torch.empty(mb, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        gw.gwas_solve_block_device(e.ctx, Xd, mb, bd, wd, sd)
+        gw.gwas_sync(e.ctx)
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([[0, 17, 127, 128, mb - 1], rng.choice(mb, 60, replace=False)]))
+    Xs = np.asfortranarray(Xd[idx].cpu().numpy().T)
+    rb, rw, rs = G.gls_hoisted(L, c.XL, c.Y, Xs)
+    b, s = bd.cpu().numpy()[idx], sd.cpu().numpy()[idx]
+    np.testing.assert_array_equal(s, rs)
+    assert s[list(idx).index(17)] == 1
+    ok = rs == 0
+    err = rel_b(b[ok], rb[ok])
+    print(f"n=30000 {precision} x{limbs}: max rel b err {err:.2e}")
+    assert err <= tol
