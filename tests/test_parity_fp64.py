@@ -63,6 +63,7 @@ def test_small_workload_full_parity(gwas):
 @pytest.mark.parametrize("n,m,p,t,mblk", [
     (2, 5, 2, 1, 4), (17, 9, 3, 2, 4), (64, 65, 4, 1, 64), (65, 130, 4, 3, 100),
     (257, 300, 5, 1, 128), (1003, 333, 4, 1, 128), (130, 70, 20, 1, 64), (200, 50, 4, 16, 32),
+    (150, 40, 4, 64, 64), (140, 33, 20, 64, 32),   # the largest t (64) and p (20)
 ])
 def test_ragged_shapes(gwas, n, m, p, t, mblk):
     c = synth.make_cohort(100 + n, n, q=p - 1, t=t, n_markers=300)

@@ -152,6 +152,22 @@ def test_constant_snp_without_intercept_is_solved(gwas, limbs):
     check(out, ref, limbs)
 
 
+@pytest.mark.parametrize("p,t", [(20, 1), (4, 64), (20, 64)])
+def test_mixed_largest_p_and_t(gwas, p, t):
+    """p = 20 (the generic p x p solve) and t = 64 phenotypes: the linear rows fill a whole
+    N = 256 linear tile (3 x 83 = 249 rows)."""
+    c = synth.make_cohort(400 + p + t, 300, q=p - 1, t=t, n_markers=300)
+    X = c.snps(150)
+    check(run(gwas, c, X, m_blk=128), oracle(c, X), 3)
+
+
+def test_mixed_linear_rows_beyond_one_tile_are_unsupported(gwas):
+    """4 limbs x (19 + 64) linear rows exceed one UMMA (N <= 256): refused at init."""
+    with pytest.raises(gwas.GwasError) as ei:
+        gwas.GLS(300, 20, 64, precision=gwas.GWAS_PREC_MIXED, n_limbs=4, m_blk=128)
+    assert ei.value.status == gwas.GWAS_ERR_UNSUPPORTED
+
+
 def test_mixed_degenerate_and_bad(gwas):
     c = synth.make_cohort(12, 300, n_markers=400)
     X = c.snps(70).copy(order="F")

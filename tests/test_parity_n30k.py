@@ -31,6 +31,36 @@ def big():
     return c, G.factor(c.phi, c.h, c.sigma2)
 
 
+def test_mixed_at_the_exactness_limit(gw):
+    """n = 32,767, the largest n for which the FP32 sums of integer limb products
+    (|A_l| <= 256, dosages <= 2) stay exact (512 n < 2^24); sampled SNPs of one block."""
+    import torch
+    n, mb = 32767, 2048
+    c = synth.make_cohort(32, n, device="cuda")
+    Xd = synth.genotypes_torch(33, n, mb, "cuda")
+    Xd[:, :100] = 2          # large dosages in the first rows of L^-1's columns
+    with gw.GLS(n, 4, 1, m_blk=mb, precision=gw.GWAS_PREC_MIXED, n_limbs=3) as e:
+        e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
+        bd = torch.empty((mb, 1, 4), dtype=torch.float64, device="cuda")
+        wd = torch.empty((mb, 1), dtype=torch.float64, device="cuda")
+        sd = torch.empty(mb, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        gw.gwas_solve_block_device(e.ctx, Xd, mb, bd, wd, sd)
+        gw.gwas_sync(e.ctx)
+    with pytest.raises(gw.GwasError):
+        gw.GLS(32768, 4, 1, m_blk=64, precision=gw.GWAS_PREC_MIXED)
+    idx = np.unique(np.concatenate([[0, mb - 1], np.random.default_rng(6).choice(mb, 40, replace=False)]))
+    Xs = np.asfortranarray(Xd[idx].cpu().numpy().T)
+    L = G.factor(c.phi, c.h, c.sigma2)
+    rb, rw, rs = G.gls_hoisted(L, c.XL, c.Y, Xs)
+    b, s = bd.cpu().numpy()[idx], sd.cpu().numpy()[idx]
+    np.testing.assert_array_equal(s, rs)
+    ok = rs == 0
+    err = rel_b(b[ok], rb[ok])
+    print(f"n=32767 mixed x3: max rel b err {err:.2e}")
+    assert err <= 1e-6
+
+
 @pytest.mark.parametrize("precision,limbs,mb,tol", [
     ("fp64", 3, 1024, 1e-10), ("mixed", 3, 4096, 1e-6), ("mixed", 5, 4096, 1e-10)])
 def test_n30k_sampled(gw, big, precision, limbs, mb, tol):
