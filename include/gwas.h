@@ -64,14 +64,18 @@ typedef struct {
     int precision; /* gwas_precision                                                  */
     int m_blk;     /* largest block of SNPs one solve call may pass (device slot size) */
     int n_limbs;   /* GWAS_PREC_MIXED: BF16 limbs L^{-1} is split into (2..5); each adds
-                      9 bits: 3 keep b within ~1e-8 of FP64, 5 within ~1e-13           */
+                      9 bits (8 for n >= 32768, 7 for n >= 65536): with 9-bit limbs 3
+                      keep b within ~1e-8 of FP64, 5 within ~1e-13. n < 131072.        */
     int tile_cfg;  /* -1 = library default; for GWAS_PREC_MIXED, bits 0-3 = pipeline
                       stages (2..8, 0 = as many as fit), bits 4-11 = MB of BF16 dosages
                       per L2 group of SNP tiles (0 = 40), bit 12 = force one CTA per
                       128-SNP tile, bit 13 = force CTA pairs (cta_group::2), bit 14 = keep
                       the linear rows in a separate tile instead of fusing them into
                       the spare N of every limb tile; by default the linear rows are
-                      fused where they fit and the taller UMMA N wins                    */
+                      fused where they fit and the taller UMMA N wins; bits 15-16 = r
+                      caps the bits per limb at 9 - r (the default takes 9 bits for
+                      n < 32768, 8 for n < 65536, 7 for n < 131072, the most for which
+                      the FP32 sums of limb products stay exact)                        */
     int device;    /* CUDA device ordinal                                             */
     int timing;    /* 1 = record CUDA events around each dominant-kernel launch       */
     int use_graph; /* batches: 1 = capture the batched solve in a CUDA graph and

@@ -1,15 +1,16 @@
 // Mixed-precision hot path of one SNP block on the BF16 tensor cores (tcgen05).
 //
 // Xbar_blk := L^{-1} X_blk (Algorithm 2, Section 3) is the dominant dense contraction.
-// Dosages {0,1,2} are exact in BF16, so only W = L^{-1} needs splitting: per 64-row
-// tile with exponent E (max |W| <= 2^E),
-//     W = 2^(E-8) * sum_{l<S} A_l * 2^(-9 l) + O(2^(E-9S)),   A_l integers in [-256, 256],
-// and every A_l is exact in BF16. A_l x_i then has integer products <= 512 whose sums
-// stay below 2^24 for n < 32768, so the FP32 tensor-core accumulation of each limb is
-// exact. The epilogue recombines the limbs in 64-bit integers,
-//     T = sum_l C_l * 2^(9 (S-1-l)),   xbar = 2^(E-8-9(S-1)) * T,
+// Dosages {0,1,2} are exact in BF16, so only W = L^{-1} needs splitting: per tile of R
+// rows with exponent E (max |W| <= 2^E) and B bits per limb,
+//     W = 2^(E-(B-1)) * sum_{l<S} A_l * 2^(-B l) + O(2^(E-BS)),   |A_l| <= 2^(B-1) integers,
+// and every A_l is exact in BF16. A_l x_i then has integer products <= 2^B whose sums
+// stay below 2^24 while n < 2^(24-B), so the FP32 tensor-core accumulation of each limb
+// is exact: B = 9 for n < 32768, 8 for n < 65536, 7 for n < 131072. The epilogue
+// recombines the limbs in 64-bit integers,
+//     T = sum_l C_l * 2^(B (S-1-l)),   xbar = 2^(E-(B-1)-B(S-1)) * T,
 // and accumulates T^2 exactly in 128-bit integers for S_BRi = Xbar_Ri^T Xbar_Ri. The
-// only rounding left is the limb truncation of W (relative 2^(-9S) of the tile maximum)
+// only rounding left is the limb truncation of W (relative 2^(-BS) of the tile maximum)
 // and one conversion to FP64 per (row tile, SNP).
 //
 // The linear reductions of Algorithm 1, S_BLi = Xbar_Ri^T Xbar_L and bbar_Bi =
@@ -126,7 +127,10 @@ template <int S, int R, int NT>
 __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32_t tb, int rt,
                                               int64_t snp) {
     using namespace tc;
-    const int shift0 = 8 + 9 * (S - 1);
+    // x = 2^(E - shift0) T with T = sum_l C_l 2^(B (S-1-l)), B = a.radix bits per limb
+    const int B = a.radix;
+    const long long base = 1ll << B;
+    const int shift0 = (B - 1) + B * (S - 1);
     if (rt != (int)mx::EXTRA) {
         unsigned __int128 acc = 0;
 #pragma unroll 1
@@ -140,7 +144,7 @@ __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32
                 long long T = 0;
 #pragma unroll
                 for (int l = 0; l < S; ++l)
-                    T = T * 512 + (long long)__float2int_rn(__uint_as_float(v[l][i]));
+                    T = T * base + (long long)__float2int_rn(__uint_as_float(v[l][i]));
                 const unsigned long long uT = (unsigned long long)(T < 0 ? -T : T);
                 acc += (unsigned __int128)uT * uT;
             }
@@ -159,7 +163,7 @@ __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32
                     uint32_t x;
                     tmem_ld1(tb + (uint32_t)(R * S + l * R_e + j), x);
                     tmem_wait_ld();
-                    T = T * 512 + (long long)__float2int_rn(__uint_as_float(x));
+                    T = T * base + (long long)__float2int_rn(__uint_as_float(x));
                 }
                 const int64_t e = (int64_t)rt * R_e + j;
                 if (snp < a.mb) a.lin[e * a.ldp + snp] = ldexp((double)T, a.E_e[e] - shift0);
@@ -174,7 +178,7 @@ __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32
                 uint32_t x;
                 tmem_ld1(tb + (uint32_t)(l * R_e + j), x);
                 tmem_wait_ld();
-                T = T * 512 + (long long)__float2int_rn(__uint_as_float(x));
+                T = T * base + (long long)__float2int_rn(__uint_as_float(x));
             }
             if (snp < a.mb) a.lin[(int64_t)j * a.ldp + snp] = ldexp((double)T, a.E_e[j] - shift0);
         }
@@ -593,11 +597,19 @@ size_t smem_bytes(int N, int N_e, bool pair, int stages) {
 
 // UMMA N of the linear tile: a multiple of 32 (so each CTA of a pair holds whole
 // 8-row swizzle groups of it) and at least 32.
+int mixed_radix(int64_t n) {
+    for (int B = 9; B >= 7; --B)
+        if (n < (int64_t(1) << (24 - B))) return B;
+    return 0;
+}
+
 int mixed_linear_n(int S, int R_e) { return (int)std::max<int64_t>(32, round_up((int64_t)S * R_e, 32)); }
 
 cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk) {
     m.S = S;
     m.n = n;
+    m.radix = mixed_radix(n);
+    if (m.cfg_radix > 0 && 9 - m.cfg_radix < m.radix) m.radix = std::max(7, 9 - m.cfg_radix);
     // Tile height and kernel variant. When the limb rows of the single-CTA tile leave
     // room for the S x R_e linear rows, they ride in the same UMMA (N = 256, which also
     // suits CTA pairs); otherwise the taller UMMA N wins, CTA pairs on a tie.
@@ -654,6 +666,7 @@ static CohortMx make_cohort(const MixedDev& m, int64_t mb, bool pair) {
     c.ldp = m.ldp;
     c.unit_base = 0;
     c.extra = m.fused ? 0 : 1;
+    c.radix = m.radix;
     c.E_w = m.E;
     c.E_e = m.E + m.n_rt;
     c.sq_part = m.sq_part;

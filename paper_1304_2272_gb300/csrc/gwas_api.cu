@@ -181,6 +181,7 @@ void apply_tile_cfg(MixedDev& m, int tile_cfg) {
     m.cfg_single_cta = false;
     m.cfg_pair = false;
     m.cfg_no_fuse = false;
+    m.cfg_radix = 0;
     if (tile_cfg >= 0) {
         m.cfg_stages = tile_cfg & 0xF;
         const int g = (tile_cfg >> 4) & 0xFF;
@@ -188,6 +189,7 @@ void apply_tile_cfg(MixedDev& m, int tile_cfg) {
         m.cfg_single_cta = ((tile_cfg >> 12) & 1) != 0;
         m.cfg_pair = ((tile_cfg >> 13) & 1) != 0;
         m.cfg_no_fuse = ((tile_cfg >> 14) & 1) != 0;
+        m.cfg_radix = (tile_cfg >> 15) & 3;
     }
 }
 
@@ -249,10 +251,11 @@ gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx**
     if (o.precision != GWAS_PREC_FP64 && o.precision != GWAS_PREC_MIXED) return GWAS_ERR_ARG;
     if (n > (int64_t)1 << 31) return GWAS_ERR_ARG;
     if (o.precision == GWAS_PREC_MIXED) {
-        // exact FP32 accumulation of integer limb products needs 512 n < 2^24; the
-        // linear tile must fit one UMMA (N <= 256); with 5 limbs the recombined value
-        // stays below 2^61 and a tile's sum of R <= 48 squares below 2^126 (int64, int128)
-        if (o.n_limbs < 2 || o.n_limbs > 5 || n >= 32768 ||
+        // exact FP32 accumulation of integer limb products needs n 2^B < 2^24 with B >= 7
+        // bits per limb (n < 2^17); the linear tile must fit one UMMA (N <= 256); with 5
+        // limbs of 9 bits the recombined value stays below 2^61 and a tile's sum of R <= 48
+        // squares below 2^126 (int64, int128)
+        if (o.n_limbs < 2 || o.n_limbs > 5 || mixed_radix(n) == 0 ||
             o.n_limbs * ((p - 1) + t) > 256)
             return GWAS_ERR_UNSUPPORTED;
     }
@@ -782,7 +785,7 @@ gwas_status gwas_set_tile_cfg(gwas_ctx* c, int tile_cfg) {
     DeviceGuard g(c->device);
     CK(cudaStreamSynchronize(c->s_comp));
     MixedDev& m = c->mx;
-    const int old_R = m.R, old_NT = m.NT;
+    const int old_R = m.R, old_NT = m.NT, old_radix = m.radix;
     const bool old_pair = m.pair, old_fused = m.fused;
     apply_tile_cfg(m, tile_cfg);
     mixed_layout(m, c->n, m.S, m.R_e, c->opts.m_blk);
@@ -796,7 +799,7 @@ gwas_status gwas_set_tile_cfg(gwas_ctx* c, int tile_cfg) {
     if (relayout) {
         CK(mixed_alloc_layout(m));
     }
-    if (c->factored && (relayout || m.pair != old_pair)) {
+    if (c->factored && (relayout || m.pair != old_pair || m.radix != old_radix)) {
         int64_t nl = 0;
         CK(mixed_prepare(m, c->W, c->ld, c->Z, c->s_comp, &nl));
         CK(cudaStreamSynchronize(c->s_comp));
@@ -827,9 +830,11 @@ gwas_status gwas_autotune(gwas_ctx* c, const int8_t* X, int64_t mb_max, int reps
 
     std::vector<int> cfgs;
     if (c->mixed) {
+        // a radix cap set by the caller (tile_cfg bits 15-16) is kept
+        const int keep = c->opts.tile_cfg >= 0 ? (c->opts.tile_cfg & (3 << 15)) : 0;
         for (int variant : {1 << 12, 1 << 13, (1 << 14) | (1 << 12), (1 << 14) | (1 << 13)})
             for (int group : {40, 80, 160})
-                for (int stages : {0, 4}) cfgs.push_back(variant | (group << 4) | stages);
+                for (int stages : {0, 4}) cfgs.push_back(keep | variant | (group << 4) | stages);
     } else {
         cfgs.push_back(-1);
     }

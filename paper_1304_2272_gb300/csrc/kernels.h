@@ -99,6 +99,7 @@ struct CohortMx {
     int64_t ldp;        // leading dimension of sq_part / lin
     int64_t unit_base;  // first unit of this cohort in a batched launch
     int extra;          // 1: a separate linear tile per SNP tile; 0: linear rows fused
+    int radix;          // bits per limb B: limbs in [-2^(B-1), 2^(B-1)]
     const int* E_w;     // exponent per row tile
     const int* E_e;     // exponent per linear row (fused: per (row tile, linear row))
     double* sq_part;    // [n_rt][ldp]
@@ -108,6 +109,7 @@ struct CohortMx {
 // Device buffers and tensor maps of the BF16-limb path for one cohort.
 struct MixedDev {
     int S = 3;                  // BF16 limbs per element of L^{-1} and Z
+    int radix = 9;              // bits per limb: 9 for n < 2^15, 8 for n < 2^16, 7 for n < 2^17
     int64_t n = 0;
     int R = 64;                 // rows of L^{-1} per tile
     int NT = 256;               // UMMA N (limb rows, plus fused linear rows) of a row tile
@@ -132,6 +134,7 @@ struct MixedDev {
     bool cfg_single_cta = false;  // force one CTA per 128-SNP tile
     bool cfg_pair = false;        // force CTA pairs
     bool cfg_no_fuse = false;     // keep the linear rows in a separate tile
+    int cfg_radix = 0;            // bits per limb at most 9 - cfg_radix (tile_cfg bits 15-16)
     int lin_tiles() const { return fused ? n_rt : 1; }
     int n_exp() const { return n_rt + (fused ? n_rt * R_e : R_e); }
     CUtensorMap tmX, tmW, tmE;  // TMA maps of Xb, WL (row tiles), WL (linear tile)
@@ -139,6 +142,9 @@ struct MixedDev {
 };
 
 int mixed_linear_n(int S, int R_e);
+// Bits per limb B for n: the FP32 sums of n products |A_l x| <= 2^B stay below 2^24
+// (exact) while n < 2^(24-B); 0 when n is too large for any supported B (>= 7).
+int mixed_radix(int64_t n);
 // true when a kernel for m's (S, R, NT, pair) layout is compiled in
 bool mixed_shape_built(const MixedDev& m);
 cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk);

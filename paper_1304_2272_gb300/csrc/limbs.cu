@@ -183,13 +183,16 @@ __global__ void k_exponents(const unsigned long long* bits, int count, int* E) {
     E[i] = e;
 }
 
+// w = 2^(E-(B-1)) sum_l A_l 2^(-B l) + O(2^(E-BS)), A_l integers in [-2^(B-1), 2^(B-1)]
+// (|w| <= 2^E; B = 7..9 bits per limb).
 template <int S>
-__device__ __forceinline__ void split_limbs(double w, int E, uint16_t (&out)[S]) {
-    double r = ldexp(w, 8 - E);  // |r| <= 256
+__device__ __forceinline__ void split_limbs(double w, int E, int B, uint16_t (&out)[S]) {
+    double r = ldexp(w, (B - 1) - E);  // |r| <= 2^(B-1)
+    const double base = ldexp(1.0, B);
 #pragma unroll
     for (int l = 0; l < S; ++l) {
         const double a = rint(r);
-        r = (r - a) * 512.0;  // exact: |r - a| <= 1/2
+        r = (r - a) * base;  // exact: |r - a| <= 1/2
         // |a| <= 256 has at most 9 significant bits: the top half of its FP32 pattern
         // is its exact BF16 pattern
         out[l] = (uint16_t)(__float_as_uint((float)a) >> 16);
@@ -200,7 +203,7 @@ __device__ __forceinline__ void split_limbs(double w, int E, uint16_t (&out)[S])
 // R rows of L^{-1} per tile, row tiles NT rows apart.
 template <int S>
 __global__ void __launch_bounds__(256)
-k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int NT,
+k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int NT, int B,
           const int* __restrict__ E_w, uint16_t* __restrict__ WL, int64_t n_pad) {
     __shared__ double tile[32][33];
     const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
@@ -217,7 +220,7 @@ k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int NT,
         if (r >= n || k >= n || k > r) continue;
         const int64_t rt = r / R, i = r % R;
         uint16_t limbs[S];
-        split_limbs<S>(tile[tx][j], E_w[rt], limbs);
+        split_limbs<S>(tile[tx][j], E_w[rt], B, limbs);
 #pragma unroll
         for (int l = 0; l < S; ++l) WL[(rt * N + (int64_t)l * R + i) * n_pad + k] = limbs[l];
     }
@@ -226,13 +229,13 @@ k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int NT,
 // Z (n x R_e, column-major) -> limb rows base + l*R_e + j of WL.
 template <int S>
 __global__ void __launch_bounds__(256)
-k_split_z(const double* __restrict__ Z, int64_t n, int R_e, const int* __restrict__ E_e,
+k_split_z(const double* __restrict__ Z, int64_t n, int R_e, int B, const int* __restrict__ E_e,
           uint16_t* __restrict__ WL, int64_t n_pad, int64_t base_row) {
     const int j = blockIdx.y;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         uint16_t limbs[S];
-        split_limbs<S>(Z[k + (int64_t)j * n], E_e[j], limbs);
+        split_limbs<S>(Z[k + (int64_t)j * n], E_e[j], B, limbs);
 #pragma unroll
         for (int l = 0; l < S; ++l) WL[(base_row + (int64_t)l * R_e + j) * n_pad + k] = limbs[l];
     }
@@ -260,14 +263,14 @@ k_absmax_zf(const double* __restrict__ Z, int64_t n, int R, unsigned long long* 
 // each tile carries Z only on its own k-range, so the tiles' partial sums add up to Z^T x.
 template <int S>
 __global__ void __launch_bounds__(256)
-k_split_zf(const double* __restrict__ Z, int64_t n, int R, int NT, int R_e,
+k_split_zf(const double* __restrict__ Z, int64_t n, int R, int NT, int R_e, int B,
            const int* __restrict__ E_e, uint16_t* __restrict__ WL, int64_t n_pad) {
     const int j = blockIdx.y;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t rt = k / R;
         uint16_t limbs[S];
-        split_limbs<S>(Z[k + (int64_t)j * n], E_e[rt * R_e + j], limbs);
+        split_limbs<S>(Z[k + (int64_t)j * n], E_e[rt * R_e + j], B, limbs);
 #pragma unroll
         for (int l = 0; l < S; ++l)
             WL[(rt * NT + (int64_t)R * S + (int64_t)l * R_e + j) * n_pad + k] = limbs[l];
@@ -294,11 +297,12 @@ cudaError_t launch_limb_split(MixedDev& m, const double* W, int64_t ldw, const d
     const dim3 gz(64, (unsigned)m.R_e);
     const int64_t zbase = (int64_t)m.n_rt * m.NT;
 #define GWAS_SPLIT(SS)                                                                       \
-    k_split_w<SS><<<gw, 256, 0, s>>>(W, ldw, n, m.R, m.NT, m.E, m.WL, m.n_pad);              \
+    k_split_w<SS><<<gw, 256, 0, s>>>(W, ldw, n, m.R, m.NT, m.radix, m.E, m.WL, m.n_pad);     \
     if (m.fused)                                                                             \
-        k_split_zf<SS><<<gz, 256, 0, s>>>(Z, n, m.R, m.NT, m.R_e, m.E + m.n_rt, m.WL, m.n_pad); \
+        k_split_zf<SS><<<gz, 256, 0, s>>>(Z, n, m.R, m.NT, m.R_e, m.radix, m.E + m.n_rt, m.WL,  \
+                                          m.n_pad);                                          \
     else                                                                                     \
-        k_split_z<SS><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.E + m.n_rt, m.WL, m.n_pad, zbase);
+        k_split_z<SS><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.radix, m.E + m.n_rt, m.WL, m.n_pad, zbase);
     switch (m.S) {
         case 2: GWAS_SPLIT(2) break;
         case 3: GWAS_SPLIT(3) break;

@@ -81,6 +81,30 @@ def test_mixed_small_workload_full(gwas, variant):
     print(f"n=1000 mixed x3 ({variant}): max rel b err {eb:.2e}, Wald err {ew:.2e}")
 
 
+def tol_bits(bits_per_limb, limbs):
+    """b tolerance for limbs of B bits: 2^6 times the truncation 2^-BS of the tile maximum
+    (the 9-bit limbs measure 1.3x-2.3x of 2^-BS at n = 1000)."""
+    return max(2.0 ** (6 - bits_per_limb * limbs), 1e-13)
+
+
+@pytest.mark.parametrize("cap,bits", [(1, 8), (2, 7)])
+@pytest.mark.parametrize("limbs", [3, 4, 5])
+def test_smaller_limb_radix(gwas, cap, bits, limbs):
+    """8- and 7-bit limbs (the radix taken for n >= 32768 and n >= 65536), forced at
+    n = 1000 through tile_cfg bits 15-16; the fused and separate linear layouts."""
+    c = synth.make_cohort(0, 1000)
+    X = c.snps(3000)
+    ref = oracle(c, X)
+    for extra in (0, 1 << 14):
+        out = run(gwas, c, X, limbs=limbs, m_blk=1024, tile_cfg=(cap << 15) | extra)
+        b, w, s = out
+        np.testing.assert_array_equal(s, ref[2])
+        ok = ref[2] == 0
+        eb = rel_b(b[ok], ref[0][ok])
+        print(f"n=1000 mixed x{limbs} of {bits} bits (sep={bool(extra)}): max rel b err {eb:.2e}")
+        assert eb <= tol_bits(bits, limbs)
+
+
 @pytest.mark.parametrize("limbs", [4, 5])
 @pytest.mark.parametrize("variant", ["default", "pair"])
 def test_mixed_more_limbs_full(gwas, limbs, variant):

@@ -1,7 +1,8 @@
-"""The largest cohort of the metric, n = 30,000 (the mixed-precision workload's n), in the
-benchmark's launch shapes: sampled SNPs against the oracle, FP64 (1e-10) and 3-limb mixed
-(1e-6) and 5-limb mixed (1e-10). Exercises the 64-bit index arithmetic of the limb
-buffers (rows x n_pad > 2^31) and the 2^24 exactness bound near its n limit."""
+"""Large cohorts: n = 30,000 (the mixed-precision workload's n) in the benchmark's launch
+shapes, FP64 (1e-10), 3-limb mixed (1e-6) and 5-limb mixed (1e-10); n = 32,767, the last
+n with 9-bit limbs; n = 40,000 with 8-bit limbs. Sampled SNPs against the oracle. Exercises
+the 64-bit index arithmetic of the limb buffers (rows x n_pad > 2^31) and the 2^24
+exactness bound at its n limits."""
 import numpy as np
 import pytest
 
@@ -31,8 +32,45 @@ def big():
     return c, G.factor(c.phi, c.h, c.sigma2)
 
 
+@pytest.mark.parametrize("limbs", [3, 5])
+def test_n40k_takes_8_bit_limbs(gw, limbs):
+    """n = 40,000 (the paper's largest single-node cohort size): beyond 32767 the limbs
+    carry 8 bits so that the FP32 sums stay exact; sampled SNPs of one block."""
+    import torch
+    n, mb = 40000, 2048
+    c, L = big40k()
+    Xd = synth.genotypes_torch(41, n, mb, "cuda")
+    with gw.GLS(n, 4, 1, m_blk=mb, precision=gw.GWAS_PREC_MIXED, n_limbs=limbs) as e:
+        e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
+        bd = torch.empty((mb, 1, 4), dtype=torch.float64, device="cuda")
+        wd = torch.empty((mb, 1), dtype=torch.float64, device="cuda")
+        sd = torch.empty(mb, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        gw.gwas_solve_block_device(e.ctx, Xd, mb, bd, wd, sd)
+        gw.gwas_sync(e.ctx)
+    idx = np.unique(np.concatenate([[0, mb - 1], np.random.default_rng(7).choice(mb, 40, replace=False)]))
+    Xs = np.asfortranarray(Xd[idx].cpu().numpy().T)
+    rb, rw, rs = G.gls_hoisted(L, c.XL, c.Y, Xs)
+    b, s = bd.cpu().numpy()[idx], sd.cpu().numpy()[idx]
+    np.testing.assert_array_equal(s, rs)
+    ok = rs == 0
+    err = rel_b(b[ok], rb[ok])
+    print(f"n=40000 mixed x{limbs} (8-bit limbs): max rel b err {err:.2e}")
+    assert err <= (1e-6 if limbs == 3 else 1e-10)
+
+
+_cache40 = {}
+
+
+def big40k():
+    if not _cache40:
+        c = synth.make_cohort(40, 40000, device="cuda")
+        _cache40["v"] = (c, G.factor(c.phi, c.h, c.sigma2))
+    return _cache40["v"]
+
+
 def test_mixed_at_the_exactness_limit(gw):
-    """n = 32,767, the largest n for which the FP32 sums of integer limb products
+    """n = 32,767, the largest n for which the FP32 sums of 9-bit limb products
     (|A_l| <= 256, dosages <= 2) stay exact (512 n < 2^24); sampled SNPs of one block."""
     import torch
     n, mb = 32767, 2048
@@ -47,8 +85,6 @@ def test_mixed_at_the_exactness_limit(gw):
         torch.cuda.synchronize()
         gw.gwas_solve_block_device(e.ctx, Xd, mb, bd, wd, sd)
         gw.gwas_sync(e.ctx)
-    with pytest.raises(gw.GwasError):
-        gw.GLS(32768, 4, 1, m_blk=64, precision=gw.GWAS_PREC_MIXED)
     idx = np.unique(np.concatenate([[0, mb - 1], np.random.default_rng(6).choice(mb, 40, replace=False)]))
     Xs = np.asfortranarray(Xd[idx].cpu().numpy().T)
     L = G.factor(c.phi, c.h, c.sigma2)
@@ -88,3 +124,9 @@ def test_n30k_sampled(gw, big, precision, limbs, mb, tol):
     err = rel_b(b[ok], rb[ok])
     print(f"n=30000 {precision} x{limbs}: max rel b err {err:.2e}")
     assert err <= tol
+
+
+def test_mixed_refuses_n_beyond_7_bit_limbs(gw):
+    with pytest.raises(gw.GwasError) as ei:
+        gw.GLS(131072, 4, 1, m_blk=64, precision=gw.GWAS_PREC_MIXED)
+    assert ei.value.status == gw.GWAS_ERR_UNSUPPORTED
