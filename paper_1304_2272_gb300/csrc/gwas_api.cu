@@ -132,6 +132,22 @@ cudaEvent_t pooled_event(gwas_ctx* c) {
     return e;
 }
 
+// Adds the event times of completed timed launches to stats.trsm_ms and recycles their
+// events; with wait = false it stops at the first launch still in flight, so a long
+// timed run keeps a bounded number of pending events.
+void fold_timings(gwas_ctx* c, bool wait) {
+    size_t k = 0;
+    for (; k < c->timed.size(); ++k) {
+        auto& pr = c->timed[k];
+        if (!wait && cudaEventQuery(pr.second) != cudaSuccess) break;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) c->stats.trsm_ms += ms;
+        c->ev_pool.push_back(pr.first);
+        c->ev_pool.push_back(pr.second);
+    }
+    c->timed.erase(c->timed.begin(), c->timed.begin() + (std::ptrdiff_t)k);
+}
+
 // The block compute on the compute stream: trsm + fused reductions, then the
 // per-SNP solve. X, b, wald, status are device pointers.
 gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, double* wald,
@@ -139,6 +155,7 @@ gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, doubl
     CohortDev cv = cohort_view(c);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->opts.timing) {
+        if (c->timed.size() >= 64) fold_timings(c, false);
         e0 = pooled_event(c);
         e1 = pooled_event(c);
         CK(cudaEventRecord(e0, c->s_comp));
@@ -614,13 +631,7 @@ gwas_status gwas_get_stats(gwas_ctx* c, gwas_stats* out) {
     DeviceGuard g(c->device);
     gwas_status st = gwas_sync(c, -1);
     if (st != GWAS_OK) return st;
-    for (auto& pr : c->timed) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) c->stats.trsm_ms += ms;
-        c->ev_pool.push_back(pr.first);
-        c->ev_pool.push_back(pr.second);
-    }
-    c->timed.clear();
+    fold_timings(c, true);
     *out = c->stats;
     return GWAS_OK;
 }
@@ -981,6 +992,20 @@ void batch_free(gwas_batch* b) {
     for (auto* c : b->ctx) gwas_finalize(c);
 }
 
+// As fold_timings, for a batch (its events are created per solve and destroyed here).
+void batch_fold_timings(gwas_batch* b, bool wait) {
+    size_t k = 0;
+    for (; k < b->timed.size(); ++k) {
+        auto& pr = b->timed[k];
+        if (!wait && cudaEventQuery(pr.second) != cudaSuccess) break;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) b->stats.trsm_ms += ms;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    b->timed.erase(b->timed.begin(), b->timed.begin() + (std::ptrdiff_t)k);
+}
+
 // Enqueue the batched solve on the batch stream (device tables already current).
 gwas_status batch_enqueue(gwas_batch* b) {
     const int nc = b->n_cohorts;
@@ -1150,6 +1175,7 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (b->opts.timing) {
+        if (b->timed.size() >= 64) batch_fold_timings(b, false);
         CKB(cudaEventCreate(&e0));
         CKB(cudaEventCreate(&e1));
         CKB(cudaEventRecord(e0, b->s));
@@ -1212,13 +1238,7 @@ gwas_status gwas_batch_get_stats(gwas_batch* b, gwas_stats* out) {
     if (!b || !out) return GWAS_ERR_ARG;
     const gwas_status st = gwas_batch_sync(b, -1);
     if (st != GWAS_OK) return st;
-    for (auto& pr : b->timed) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) b->stats.trsm_ms += ms;
-        cudaEventDestroy(pr.first);
-        cudaEventDestroy(pr.second);
-    }
-    b->timed.clear();
+    batch_fold_timings(b, true);
     gwas_stats agg = b->stats;
     agg.factor_ms = 0;
     agg.factor_launches = 0;

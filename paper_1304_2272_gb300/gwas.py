@@ -172,6 +172,30 @@ def _require(x, dtype, name: str, order: str = "F"):
     return x
 
 
+_TORCH_DTYPES = {np.int8: "torch.int8", np.uint8: "torch.uint8", np.float64: "torch.float64"}
+
+
+def _require_dev(x, dtype, name: str):
+    """A device buffer passed as a tensor must have the C ABI's element type and be
+    contiguous (raw addresses and None pass through unchecked)."""
+    if x is None or isinstance(x, int):
+        return x
+    if hasattr(x, "is_contiguous") and hasattr(x, "dtype"):
+        if str(x.dtype) != _TORCH_DTYPES[dtype]:
+            raise TypeError(f"{name} must be {_TORCH_DTYPES[dtype]}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if getattr(x, "is_cuda", True) is False:
+            raise ValueError(f"{name} must be in device memory")
+    return x
+
+
+def _outs_dev(b, wald, status):
+    _require_dev(b, np.float64, "b")
+    _require_dev(wald, np.float64, "wald")
+    _require_dev(status, np.uint8, "status")
+
+
 # ---- entry points (same names as the C ABI) -----------------------------------
 def gwas_default_opts() -> gwas_opts:
     o = gwas_opts()
@@ -206,6 +230,8 @@ def gwas_solve_block(ctx, X, mb: int, b, wald, status) -> None:
 
 
 def gwas_solve_block_device(ctx, X, mb: int, b, wald, status) -> None:
+    _require_dev(X, np.int8, "X")
+    _outs_dev(b, wald, status)
     _check(ctx, load().gwas_solve_block_device(ctx, _addr(X), int(mb), _addr(b), _addr(wald),
                                                _addr(status)))
 
@@ -231,6 +257,8 @@ def gwas_solve_block_packed(ctx, Xp, mb: int, code, b, wald, status) -> None:
 
 
 def gwas_solve_block_packed_device(ctx, Xp, mb: int, code, b, wald, status) -> None:
+    _require_dev(Xp, np.uint8, "Xp")
+    _outs_dev(b, wald, status)
     _check(ctx, load().gwas_solve_block_packed_device(ctx, _addr(Xp), int(mb), _code(code),
                                                       _addr(b), _addr(wald), _addr(status)))
 
@@ -302,6 +330,9 @@ def gwas_reml(ctx, Phi, h: float, sigma2: float, XL, Y, pheno: int = 0,
 
 
 def gwas_solve_block_grad_device(ctx, X, mb: int, b, wald, status, dbdh) -> None:
+    _require_dev(X, np.int8, "X")
+    _outs_dev(b, wald, status)
+    _require_dev(dbdh, np.float64, "dbdh")
     _check(ctx, load().gwas_solve_block_grad_device(ctx, _addr(X), int(mb), _addr(b), _addr(wald),
                                                     _addr(status), _addr(dbdh)))
 
@@ -361,6 +392,9 @@ def _ptr_array(items):
 def gwas_batch_solve_device(batch, X, mb, b, wald, status) -> None:
     """X, b, wald, status: sequences of device arrays (one per cohort); mb: SNP counts."""
     n = len(X)
+    for k in range(n):
+        _require_dev(X[k], np.int8, f"X[{k}]")
+        _outs_dev(b[k], wald[k] if wald is not None else None, status[k])
     mbs = (_i64 * n)(*[int(v) for v in mb])
     w = _ptr_array(wald) if wald is not None else None
     _bcheck(batch, load().gwas_batch_solve_device(batch, _ptr_array(X), mbs, _ptr_array(b), w,

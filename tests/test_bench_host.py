@@ -51,3 +51,22 @@ def test_pack_2bit_layout():
                     assert (int(P[k // 4, j]) >> (2 * (k % 4))) & 3 == want
                 for k in range(n, 4 * P.shape[0]):      # padding calls are zero
                     assert (int(P[k // 4, j]) >> (2 * (k % 4))) & 3 == 0
+
+
+def test_device_arguments_are_checked_before_the_call():
+    """Tensors with the wrong element type or layout are refused by the binding without
+    reaching the library (CPU tensors stand in for device ones)."""
+    import pytest
+    import torch
+    from paper_1304_2272_gb300 import gwas
+    X = torch.zeros((4, 8), dtype=torch.int8)
+    b = torch.zeros((4, 1, 4), dtype=torch.float64)
+    with pytest.raises(TypeError):
+        gwas._require_dev(torch.zeros(3, dtype=torch.float32), gwas.np.float64, "b")
+    with pytest.raises(ValueError):
+        gwas._require_dev(torch.zeros((4, 8), dtype=torch.int8).t(), gwas.np.int8, "X")
+    with pytest.raises(ValueError):
+        gwas._require_dev(X, gwas.np.int8, "X")        # host tensor
+    assert gwas._require_dev(None, gwas.np.int8, "X") is None
+    assert gwas._require_dev(1234, gwas.np.int8, "X") == 1234
+    del b

@@ -205,3 +205,16 @@ def test_full_size_sampled(gwas):
     out = (bd.cpu().numpy()[idx], wd.cpu().numpy()[idx], sd.cpu().numpy()[idx])
     assert_parity(out, ref)
     e.close()
+
+
+def test_timing_over_many_blocks(gwas):
+    """With timing on, the event times of a long run are folded as launches complete:
+    every launch is counted once."""
+    c = synth.make_cohort(60, 128, n_markers=200)
+    X = c.snps(64 * 150)
+    with gwas.GLS(c.n, 4, 1, m_blk=64, timing=1) as e:
+        e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
+        out = e.solve(X)
+        st = e.stats()
+    assert st["trsm_launches"] == 150 and st["blocks"] == 150 and st["trsm_ms"] > 0
+    assert_parity(out, oracle(c, X))
