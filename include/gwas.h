@@ -233,7 +233,9 @@ void* gwas_stream(const gwas_ctx* ctx);
  * adjoint: the derivative of l with respect to M is -1/2 (P - P y y^T P), P =
  * M^-1 - M^-1 X_L (X_L^T M^-1 X_L)^-1 X_L^T M^-1, contracted with dM/dh = sigma2 (Phi - I)
  * and dM/dsigma2 = M / sigma2. Runs gwas_factor(ctx, Phi, 1, h, sigma2, XL, Y) first, then
- * forms M^-1 = L^-T L^-1 and the small Gram matrices of Z = M^-1 [X_L | Y] on the GPU.
+ * the small Gram matrices of Z = M^-1 [X_L | Y] on the GPU. For h >= 1e-2 the traces
+ * use Phi = (M / sigma2 - (1 - h) I) / h and tr M^-1 = |L^-1|_F^2 (no n x n product
+ * beyond the factor); below it M^-1 = L^-T L^-1 is formed and Phi read directly.
  * Phi: the FULL n x n symmetric matrix (both triangles are read), host or device. With
  * profile != 0 every value is reported at sigma2 = sigma2_hat(h) (so dl/dh is the
  * derivative of the profiled likelihood). Afterwards the context is ready for

@@ -51,7 +51,9 @@ struct gwas_ctx {
     double* Z = nullptr;          // n x (q + t): L^{-T} [Xbar_L | Ybar] = M^{-1} [X_L | Y]
     // REML and db/dh (allocated on first use)
     double* Phi = nullptr;        // full Phi, ld
-    double* Minv = nullptr;       // M^{-1} = L^{-T} L^{-1}, ld
+    double* Minv = nullptr;       // M^{-1} = L^{-T} L^{-1}, ld (formed when db/dh needs it)
+    bool minv_ready = false;      // Minv holds M^{-1} of the current factor
+    double* XLY = nullptr;        // [X_L | Y] (n x (q+t)) as given to the last gwas_factor
     double* part2 = nullptr;      // adjoint partials, FP64 partial layout
     double* small = nullptr;      // G1, G2, PhiZ and scalars
     bool grad_ready = false;
@@ -227,6 +229,7 @@ void free_all(gwas_ctx* c) {
     cudaFree(c->S_TL); cudaFree(c->bbar_T); cudaFree(c->d_info); cudaFree(c->part);
     cudaFree(c->bad); cudaFree(c->Xunpack);
     cudaFree(c->Phi); cudaFree(c->Minv); cudaFree(c->part2); cudaFree(c->small);
+    cudaFree(c->XLY);
     cudaFree(c->Z); cudaFree(c->mx.WL); cudaFree(c->mx.bits); cudaFree(c->mx.E);
     cudaFree(c->mx.Xb); cudaFree(c->mx.sq_part); cudaFree(c->mx.lin); cudaFree(c->mx.err);
     for (int s = 0; s < 2; ++s) {
@@ -350,6 +353,7 @@ gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double 
     DeviceGuard g(c->device);
     c->factored = false;
     c->grad_ready = false;
+    c->minv_ready = false;
     c->err_index = -1;
     const int64_t n = c->n, ld = c->ld;
     cudaStream_t s = c->s_comp;
@@ -369,13 +373,13 @@ gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double 
     // W := L^{-1}
     CK(cudaMemsetAsync(c->W, 0, (size_t)ld * ld * sizeof(double), s));
     const int64_t half = round_up(ceil_div(n, 2), T64);
-    TmpDev tmp_buf, in_buf;
+    TmpDev tmp_buf;
     CK(cudaMalloc(&tmp_buf.p, (size_t)half * half * sizeof(double)));
     double* tmp = (double*)tmp_buf.p;
     CK(trtri_lower(c->L, ld, n, c->Dinv, c->W, ld, tmp, s, &nl));
-    // Xbar_L := W X_L, Ybar := W Y
-    CK(cudaMalloc(&in_buf.p, (size_t)n * (c->q + c->t) * sizeof(double)));
-    double* XLin = (double*)in_buf.p;
+    // Xbar_L := W X_L, Ybar := W Y ([X_L | Y] is kept for the REML identities)
+    if (!c->XLY) CK(dmalloc(&c->XLY, (size_t)n * (c->q + c->t)));
+    double* XLin = c->XLY;
     double* Yin = XLin + (size_t)n * c->q;
     CK(cudaMemcpyAsync(XLin, XL, (size_t)n * c->q * sizeof(double), cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(Yin, Y, (size_t)n * c->t * sizeof(double), cudaMemcpyDefault, s));
@@ -657,6 +661,19 @@ void* gwas_stream(const gwas_ctx* c) { return c ? (void*)c->s_comp : nullptr; }
 // ============================================================================
 namespace {
 
+// M^-1 = W^T W (W = L^-1 lower triangular) into c->Minv.
+cudaError_t form_minv(gwas_ctx* c, cudaStream_t s) {
+    const int64_t n = c->n, ld = c->ld;
+    cudaError_t e;
+    if (!c->Minv && (e = dmalloc(&c->Minv, (size_t)ld * ld)) != cudaSuccess) return e;
+    GemmF64 mi;
+    mi.M = n; mi.N = n; mi.K = n; mi.A = c->W; mi.lda = ld; mi.transA = true; mi.a_upper = true;
+    mi.B = c->W; mi.ldb = ld; mi.b_lower = true; mi.C = c->Minv; mi.ldc = ld;
+    if ((e = gemm_f64(mi, s)) != cudaSuccess) return e;
+    c->minv_ready = true;
+    return cudaSuccess;
+}
+
 // Layout of c->small: G1 and G2 ((q+t)^2 each), PhiZ (n x (q+t)), then scalars.
 struct SmallLayout {
     int64_t nz, g1, g2, phiz, yy, logdet, frob, fpart, out, total;
@@ -688,19 +705,22 @@ extern "C" gwas_status gwas_reml(gwas_ctx* c, const double* Phi, double h, doubl
     const int64_t n = c->n, ld = c->ld, nz = c->q + c->t;
     cudaStream_t s = c->s_comp;
     const SmallLayout sl(c);
-    if (!c->Phi) CK(dmalloc(&c->Phi, (size_t)ld * ld));
-    if (!c->Minv) CK(dmalloc(&c->Minv, (size_t)ld * ld));
+    // For h >= 1e-2 Phi enters only through M: Phi Z and <M^-1, Phi> follow from M, Z and
+    // tr M^-1 = |L^-1|_F^2, so neither Phi nor M^-1 (n^3/3 flops) is formed; below it the
+    // identities would divide a cancellation by h, and Phi and M^-1 are used directly.
+    const bool identity = h >= 1e-2;
     if (!c->Z) CK(dmalloc(&c->Z, (size_t)n * nz));
     if (!c->small) CK(dmalloc(&c->small, (size_t)sl.total));
     double* sm = c->small;
-    // the full Phi (the Frobenius product reads both triangles)
-    CK(cudaMemcpy2DAsync(c->Phi, ld * sizeof(double), Phi, n * sizeof(double), n * sizeof(double), n,
-                         cudaMemcpyDefault, s));
-    // M^-1 = W^T W (W = L^-1 lower triangular)
-    GemmF64 mi;
-    mi.M = n; mi.N = n; mi.K = n; mi.A = c->W; mi.lda = ld; mi.transA = true; mi.a_upper = true;
-    mi.B = c->W; mi.ldb = ld; mi.b_lower = true; mi.C = c->Minv; mi.ldc = ld;
-    CK(gemm_f64(mi, s));
+    if (!identity) {
+        if (!c->Phi) CK(dmalloc(&c->Phi, (size_t)ld * ld));
+        if (!c->Minv) CK(dmalloc(&c->Minv, (size_t)ld * ld));
+        // the full Phi (the Frobenius product reads both triangles)
+        CK(cudaMemcpy2DAsync(c->Phi, ld * sizeof(double), Phi, n * sizeof(double),
+                             n * sizeof(double), n, cudaMemcpyDefault, s));
+        // M^-1 = W^T W (W = L^-1 lower triangular)
+        CK(form_minv(c, s));
+    }
     if (!c->mixed) {  // the mixed factor already formed Z
         GemmF64 z;
         z.M = n; z.N = c->q; z.K = n; z.A = c->W; z.lda = ld; z.transA = true; z.a_upper = true;
@@ -710,29 +730,38 @@ extern "C" gwas_status gwas_reml(gwas_ctx* c, const double* Phi, double h, doubl
         zy.N = c->t; zy.B = c->Ybar; zy.C = c->Z + (size_t)n * c->q;
         CK(gemm_f64(zy, s));
     }
-    // Phi Z, G1 = Z^T Z, G2 = Z^T Phi Z, |ybar_j|^2
-    GemmF64 pz;
-    pz.M = n; pz.N = nz; pz.K = n; pz.A = c->Phi; pz.lda = ld; pz.B = c->Z; pz.ldb = n;
-    pz.C = sm + sl.phiz; pz.ldc = n;
-    CK(gemm_f64(pz, s));
+    // G1 = Z^T Z; G2 = Z^T Phi Z (identity: Z^T [X_L | Y]); |ybar_j|^2
     GemmF64 g1;
     g1.M = nz; g1.N = nz; g1.K = n; g1.A = c->Z; g1.lda = n; g1.transA = true; g1.B = c->Z;
     g1.ldb = n; g1.C = sm + sl.g1; g1.ldc = nz;
     CK(gemm_f64(g1, s));
     GemmF64 g2 = g1;
-    g2.B = sm + sl.phiz; g2.C = sm + sl.g2;
+    g2.C = sm + sl.g2;
+    if (identity) {
+        g2.B = c->XLY;
+    } else {
+        GemmF64 pz;
+        pz.M = n; pz.N = nz; pz.K = n; pz.A = c->Phi; pz.lda = ld; pz.B = c->Z; pz.ldb = n;
+        pz.C = sm + sl.phiz; pz.ldc = n;
+        CK(gemm_f64(pz, s));
+        g2.B = sm + sl.phiz;
+    }
     CK(gemm_f64(g2, s));
     GemmF64 yy;
     yy.M = 1; yy.N = 1; yy.K = n; yy.A = c->Ybar + (size_t)n * pheno; yy.lda = n; yy.transA = true;
     yy.B = c->Ybar + (size_t)n * pheno; yy.ldb = n; yy.C = sm + sl.yy; yy.ldc = 1;
     CK(gemm_f64(yy, s));
     CK(launch_logdiag(c->L, ld, n, sm + sl.logdet, s));
-    CK(launch_frob_trace(c->Minv, c->Phi, ld, n, sm + sl.fpart, sm + sl.frob, s));
+    if (identity)
+        CK(launch_frob_trace(c->W, c->W, ld, n, sm + sl.fpart, sm + sl.frob, s));
+    else
+        CK(launch_frob_trace(c->Minv, c->Phi, ld, n, sm + sl.fpart, sm + sl.frob, s));
     RemlDev r;
     r.n = n; r.q = c->q; r.t = c->t; r.j = pheno; r.h = h; r.sigma2 = sigma2;
     r.profile = profile ? 1 : 0;
     r.S_TL = c->S_TL; r.bbar_T = c->bbar_T; r.G1 = sm + sl.g1; r.G2 = sm + sl.g2;
     r.yy = sm + sl.yy; r.logdet_M = sm + sl.logdet; r.frob = sm + sl.frob; r.out = sm + sl.out;
+    r.identity = identity ? 1 : 0;
     CK(launch_reml_assemble(r, s));
     double host[8];
     CK(cudaMemcpyAsync(host, sm + sl.out, sizeof host, cudaMemcpyDeviceToHost, s));
@@ -765,6 +794,10 @@ extern "C" gwas_status gwas_solve_block_grad_device(gwas_ctx* c, const int8_t* X
     const int64_t n = c->n;
     const int n_tiles = (int)ceil_div(n, T64);
     if (!c->part2) CK(dmalloc(&c->part2, (size_t)n_tiles * (c->q + 1 + c->t) * c->ldp));
+    if (!c->minv_ready) {  // gwas_reml did not need M^-1 (h >= 1e-2): form it once
+        CK(form_minv(c, c->s_comp));
+        c->stats.kernel_launches += 1;
+    }
     // forward: b_i, Wald, status, and the partials of S_i and bbar_i
     if ((st = run_block(c, X, mb, b, wald, status)) != GWAS_OK) return st;
     // adjoint: the same kernel with M^-1 (dense) and Z = M^-1 [X_L | Y]

@@ -225,10 +225,14 @@ struct RemlDev {
     const double* S_TL = nullptr;  // q x q
     const double* bbar_T = nullptr;// q x t
     const double* G1 = nullptr;    // Zc^T Zc,      (q+t) x (q+t), Zc = M^-1 [X_L | Y]
-    const double* G2 = nullptr;    // Zc^T Phi Zc,  (q+t) x (q+t)
+    const double* G2 = nullptr;    // Zc^T Phi Zc (identity = 1: Zc^T [X_L | Y]), (q+t) x (q+t)
     const double* yy = nullptr;    // ybar_j^T ybar_j
     const double* logdet_M = nullptr;
-    const double* frob = nullptr;  // [<M^-1, Phi>, tr M^-1]
+    const double* frob = nullptr;  // [<M^-1, Phi>, tr M^-1] (identity = 1: [|L^-1|_F^2, *])
+    // 1: Phi enters only through M = sigma2 (h Phi + (1-h) I), h > 0: Phi Zc =
+    // ([X_L | Y] / sigma2 - (1-h) Zc) / h and <M^-1, Phi> = (n / sigma2 - (1-h) tr M^-1) / h
+    // with tr M^-1 = |L^-1|_F^2, so neither Phi nor M^-1 is formed
+    int identity = 0;
     double* out = nullptr;         // 8 doubles, see gwas_reml_result
 };
 cudaError_t launch_reml_assemble(const RemlDev& r, cudaStream_t s);

@@ -131,6 +131,11 @@ __global__ void k_reml_assemble(RemlDev r) {
     const int q = r.q, t = r.t, nz = q + t, jy = q + r.j;
     double C[MAX_P][MAX_P];
     double* out = r.out;
+    // Zc^T Phi Zc, entry (a, b)
+    auto g2 = [&](int a, int b) {
+        const double v = r.G2[a + b * nz];
+        return r.identity ? (v / r.sigma2 - (1.0 - r.h) * r.G1[a + b * nz]) / r.h : v;
+    };
     if (!small_chol(r.S_TL, q, C)) {
         for (int k = 0; k < 8; ++k) out[k] = nan("");
         return;
@@ -149,7 +154,7 @@ __global__ void k_reml_assemble(RemlDev r) {
         for (int a = 0; a < q; ++a) col[a] = (a == b) ? 1.0 : 0.0;
         small_solve(C, q, col);  // column b of A^-1
         for (int a = 0; a < q; ++a)
-            trAD += col[a] * (r.G2[b + a * nz] - r.G1[b + a * nz]);
+            trAD += col[a] * (g2(b, a) - r.G1[b + a * nz]);
     }
     // Py = Zc v with v = [-beta; e_j]: quadratic forms in G1 and G2
     double pp = 0.0, pPhip = 0.0;
@@ -160,13 +165,15 @@ __global__ void k_reml_assemble(RemlDev r) {
             const double vb = b < q ? -beta[b] : (b == jy ? 1.0 : 0.0);
             if (vb == 0.0) continue;
             pp += va * vb * r.G1[a + b * nz];
-            pPhip += va * vb * r.G2[a + b * nz];
+            pPhip += va * vb * g2(a, b);
         }
     }
     const double n = (double)r.n;
     double s2 = r.sigma2;
     double logdet_M = 2.0 * (*r.logdet_M);
-    double tr_dMh = s2 * ((r.frob[0] - r.frob[1]) - trAD);   // tr(P dM/dh)
+    const double tr_minv = r.identity ? r.frob[0] : r.frob[1];
+    const double minv_phi = r.identity ? (n / s2 - (1.0 - r.h) * tr_minv) / r.h : r.frob[0];
+    double tr_dMh = s2 * ((minv_phi - tr_minv) - trAD);       // tr(P dM/dh)
     double q_dMh = s2 * (pPhip - pp);                        // (Py)^T dM/dh (Py)
     const double s2_hat = s2 * yPy / (n - q);
     if (r.profile) {

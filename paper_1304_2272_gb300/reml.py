@@ -1,7 +1,7 @@
 """REML fitting of h through the library's hand-written adjoint (marshalling only).
 
 ``REMLFunction`` is a ``torch.autograd.Function`` whose forward calls ``gwas_reml`` (FP64
-Cholesky, L^-1 and M^-1 on the GPU) and whose backward returns the adjoint gradient the
+Cholesky and L^-1 on the GPU) and whose backward returns the adjoint gradient the
 library computed with it, so the REML log-likelihood can be used like any other torch
 objective. ``fit_h`` maximises the profiled likelihood (sigma^2 profiled out) by a
 safeguarded secant iteration on its derivative dl/dh, starting from h0.
@@ -25,10 +25,17 @@ class REMLEngine:
         self.pheno = pheno
         self.ctx = gwas.gwas_init(n, self.q + 1, self.t, **opts)
         self.evals = 0
+        # Phi is read by every evaluation: keep one copy in device memory (Phi is
+        # symmetric, so its storage order does not matter)
+        import torch
+        dev = f"cuda:{int(opts.get('device', 0))}"
+        self.Phi_dev = torch.from_numpy(np.ascontiguousarray(self.Phi)).to(dev)
+        torch.cuda.synchronize(dev)
 
     def eval(self, h: float, sigma2: float, profile: bool = False) -> dict:
         self.evals += 1
-        return gwas.gwas_reml(self.ctx, self.Phi, h, sigma2, self.XL, self.Y, self.pheno, profile)
+        return gwas.gwas_reml(self.ctx, self.Phi_dev, h, sigma2, self.XL, self.Y, self.pheno,
+                              profile)
 
     def close(self):
         if self.ctx:

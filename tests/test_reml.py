@@ -32,7 +32,10 @@ def engine(gw, c):
     return REMLEngine(c.phi, c.XL, c.Y)
 
 
-@pytest.mark.parametrize("h,s2", [(0.1, 1.0), (0.25, 1.3), (0.7, 0.6)])
+# h >= 1e-2 takes the trace identities (no Phi product, no M^-1); 0 <= h < 1e-2 the
+# direct route with Phi and M^-1
+@pytest.mark.parametrize("h,s2", [(0.1, 1.0), (0.25, 1.3), (0.7, 0.6), (0.01, 0.9),
+                                  (0.005, 1.1), (0.0, 0.8)])
 def test_reml_matches_oracle(gw, cohort, h, s2):
     c = cohort
     e = engine(gw, c)
