@@ -183,39 +183,60 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int6
     if (tid == 0 && fail >= 0) atomicMin(info, (int)(base + fail));
 }
 
+// Two-level right-looking blocked Cholesky: panels of NB = 256 columns, each factored in
+// 64-column blocks (diagonal block in shared memory, the rows below by D_k^T, then the
+// rank-64 update of the panel's remaining columns only); the columns right of the panel
+// get one rank-NB update per panel, so the large trailing GEMMs run with K = 256.
 cudaError_t cholesky_blocked(double* A, int64_t lda, int64_t n, double* Dinv, int* d_info,
                              cudaStream_t s, int64_t* launches) {
-    const int64_t nt = ceil_div(n, T64);
+    constexpr int64_t NB = 4 * T64;
     int64_t nl = 0;
     const int smem = 2 * T64 * (T64 + 1) * (int)sizeof(double);
-    cudaError_t ea = cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (ea != cudaSuccess) return ea;
-    for (int64_t k = 0; k < nt; ++k) {
-        const int64_t k0 = k * T64;
-        const int kb = (int)std::min<int64_t>(T64, n - k0);
-        double* Akk = A + k0 + k0 * lda;
-        double* Dk = Dinv + k * T64 * T64;
-        k_potrf_diag<<<1, 256, smem, s>>>(Akk, lda, kb, k0, Dk, d_info);
-        ++nl;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        const int64_t below = n - k0 - kb;
-        if (below <= 0) break;
-        double* P = A + (k0 + kb) + k0 * lda;  // panel rows below the block
-        // L_ik := A_ik L_kk^{-T} = A_ik D_k^T (one column tile: in place is safe)
-        GemmF64 g;
-        g.M = below; g.N = kb; g.K = kb;
-        g.A = P; g.lda = lda; g.B = Dk; g.ldb = T64; g.transB = true;
-        g.C = P; g.ldc = lda;
-        if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
-        // A22 -= L_panel L_panel^T (lower tiles only)
-        GemmF64 u;
-        u.M = below; u.N = below; u.K = kb;
-        u.A = P; u.lda = lda; u.B = P; u.ldb = lda; u.transB = true;
-        u.C = A + (k0 + kb) + (k0 + kb) * lda; u.ldc = lda;
-        u.alpha = -1.0; u.beta = 1.0; u.c_lower = true;
-        if ((e = gemm_f64(u, s)) != cudaSuccess) return e;
-        nl += 2;
+    cudaError_t e = cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    for (int64_t p0 = 0; p0 < n; p0 += NB) {
+        const int64_t pend = std::min<int64_t>(n, p0 + NB);  // panel columns [p0, pend)
+        for (int64_t k0 = p0; k0 < pend; k0 += T64) {
+            const int kb = (int)std::min<int64_t>(T64, n - k0);
+            double* Akk = A + k0 + k0 * lda;
+            double* Dk = Dinv + (k0 / T64) * T64 * T64;
+            k_potrf_diag<<<1, 256, smem, s>>>(Akk, lda, kb, k0, Dk, d_info);
+            ++nl;
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            const int64_t below = n - k0 - kb;
+            if (below <= 0) break;
+            double* P = A + (k0 + kb) + k0 * lda;  // rows below the block
+            // L_ik := A_ik L_kk^{-T} = A_ik D_k^T (one column tile: in place is safe)
+            GemmF64 g;
+            g.M = below; g.N = kb; g.K = kb;
+            g.A = P; g.lda = lda; g.B = Dk; g.ldb = T64; g.transB = true;
+            g.C = P; g.ldc = lda;
+            if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+            ++nl;
+            // the panel's remaining columns [k0 + kb, pend) -= L_below L_(those rows)^T
+            const int64_t w = pend - (k0 + kb);
+            if (w > 0) {
+                GemmF64 u;
+                u.M = below; u.N = w; u.K = kb;
+                u.A = P; u.lda = lda; u.B = P; u.ldb = lda; u.transB = true;
+                u.C = A + (k0 + kb) + (k0 + kb) * lda; u.ldc = lda;
+                u.alpha = -1.0; u.beta = 1.0; u.c_lower = true;
+                if ((e = gemm_f64(u, s)) != cudaSuccess) return e;
+                ++nl;
+            }
+        }
+        // A22 -= L_(rows >= pend, panel) L_(rows >= pend, panel)^T (lower tiles only)
+        const int64_t rest = n - pend;
+        if (rest > 0) {
+            double* Q = A + pend + p0 * lda;
+            GemmF64 u;
+            u.M = rest; u.N = rest; u.K = pend - p0;
+            u.A = Q; u.lda = lda; u.B = Q; u.ldb = lda; u.transB = true;
+            u.C = A + pend + pend * lda; u.ldc = lda;
+            u.alpha = -1.0; u.beta = 1.0; u.c_lower = true;
+            if ((e = gemm_f64(u, s)) != cudaSuccess) return e;
+            ++nl;
+        }
     }
     if (launches) *launches += nl;
     return cudaSuccess;
