@@ -174,11 +174,11 @@ def bf16_flops_per_snp(n: int, q: int, t: int, limbs: int) -> float:
 TRAFFIC = {
     "k_block_fp64": {"file": "block_fp64.cu", "sha": "17f101cf32e7945d", "n": 10000,
                      "m_blk": 16384, "bytes": 8830753024 + 101610496},
-    "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "1af7a5f567e776ec", "n": 10000,
+    "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "886cdd079efba4ca", "n": 10000,
                          "m_blk": 16384, "single_cta": False, "no_fuse": False,
-                         "bytes_by_group_mb": {40: 4048532736 + 81214976,
-                                               80: 4555761920 + 79603968,
-                                               160: 8115475456 + 76000768}},
+                         "bytes_by_group_mb": {40: 4036415744 + 81025792,
+                                               80: 4554571520 + 79876352,
+                                               160: 8137596416 + 76032256}},
 }
 
 
