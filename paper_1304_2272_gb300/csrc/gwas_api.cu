@@ -15,11 +15,21 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gwas.h"
 #include "common.cuh"
 #include "kernels.h"
 
 using namespace gwas;
+
+namespace {
+// NVTX range over one API call (named in profiler timelines; free without a tool).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+}  // namespace
 
 struct gwas_ctx {
     gwas_opts opts{};
@@ -154,6 +164,7 @@ void fold_timings(gwas_ctx* c, bool wait) {
 // per-SNP solve. X, b, wald, status are device pointers.
 gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, double* wald,
                       uint8_t* status) {
+    Range range_("gwas block");
     CohortDev cv = cohort_view(c);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->opts.timing) {
@@ -346,6 +357,7 @@ gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx**
 
 gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double h,
                         double sigma2, const double* XL, const double* Y) {
+    Range range_("gwas_factor");
     if (!c) return GWAS_ERR_ARG;
     if (!M_or_Phi || !XL || !Y) return fail(c, GWAS_ERR_ARG, "gwas_factor: NULL input");
     if (is_phi && !(h >= 0.0 && h <= 1.0 && sigma2 > 0.0))
@@ -696,6 +708,7 @@ struct SmallLayout {
 extern "C" gwas_status gwas_reml(gwas_ctx* c, const double* Phi, double h, double sigma2,
                                  const double* XL, const double* Y, int pheno, int profile,
                                  gwas_reml_result* out) {
+    Range range_("gwas_reml");
     if (!c || !out) return GWAS_ERR_ARG;
     if (!Phi || !XL || !Y) return fail(c, GWAS_ERR_ARG, "gwas_reml: NULL input");
     if (pheno < 0 || pheno >= c->t) return fail(c, GWAS_ERR_ARG, "gwas_reml: phenotype out of range");
@@ -852,6 +865,7 @@ gwas_status gwas_set_tile_cfg(gwas_ctx* c, int tile_cfg) {
 }
 
 gwas_status gwas_autotune(gwas_ctx* c, const int8_t* X, int64_t mb_max, int reps, gwas_tune* out) {
+    Range range_("gwas_autotune");
     if (!c || !out) return GWAS_ERR_ARG;
     if (!c->factored) return fail(c, GWAS_ERR_STATE, "gwas_autotune before gwas_factor");
     if (mb_max < 1 || mb_max > c->opts.m_blk) mb_max = c->opts.m_blk;
@@ -1122,6 +1136,7 @@ gwas_status gwas_batch_factor(gwas_batch* b, int cohort, const double* M_or_Phi,
 gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const int64_t* mb,
                                     double* const* bo, double* const* wald,
                                     uint8_t* const* status) {
+    Range range_("gwas batch solve");
     if (!b) return GWAS_ERR_ARG;
     if (!X || !mb || !bo || !status) return bfail(b, GWAS_ERR_ARG, "batch solve: NULL array");
     const int nc = b->n_cohorts;
