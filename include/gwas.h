@@ -203,6 +203,22 @@ gwas_status gwas_solve_all(gwas_ctx* ctx, const int8_t* X, int64_t m, double* b,
                            double* wald, uint8_t* status);
 
 /*
+ * Wait until host-path block number `block` (0-based count of the gwas_solve_block and
+ * gwas_solve_block_packed calls made on this context) has completed: its input buffer may
+ * be reused and its b / wald / status read. A streaming caller can recycle its pinned host
+ * buffers this way while later blocks are in flight (Algorithm 2's double buffering).
+ * timeout_ms < 0 waits without limit. Errors: GWAS_ERR_ARG (no such block yet),
+ * GWAS_ERR_TIMEOUT, GWAS_ERR_CUDA.
+ */
+gwas_status gwas_wait_block(gwas_ctx* ctx, int64_t block, int timeout_ms);
+
+/* Page-locked host memory for streaming buffers (cudaHostAlloc, portable); *out = NULL
+ * for bytes = 0. gwas_host_free(NULL) is allowed. Errors: GWAS_ERR_ARG, GWAS_ERR_OOM
+ * (alloc), GWAS_ERR_CUDA (free). */
+gwas_status gwas_host_alloc(size_t bytes, void** out);
+gwas_status gwas_host_free(void* p);
+
+/*
  * Wait for all queued work of the context. timeout_ms < 0 waits without limit;
  * otherwise polls and returns GWAS_ERR_TIMEOUT after about timeout_ms (the work
  * stays queued and a later gwas_sync may still succeed). Never hangs the host

@@ -1,8 +1,10 @@
 """In-tree build of the engine's C-ABI shared library for sm_103a (GB300).
 
 Every ``csrc/*.cu`` file is compiled in parallel with nvcc into ``_build/`` and
-linked into ``libgwas_gb300.so`` next to this file (CUDA runtime linked statically).
-A source newer than the library triggers a rebuild; ``force=True`` always rebuilds.
+linked into ``libgwas_gb300.so`` next to this file (CUDA runtime linked statically);
+``cli/gwas_stream.cpp`` is then built against it into ``gwas_stream`` (a native
+out-of-core driver of the C ABI). A source newer than its product triggers a rebuild;
+``force=True`` always rebuilds.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ CSRC = PKG / "csrc"
 INCLUDE = PKG.parent / "include"
 BUILD = PKG / "_build"
 LIB = PKG / "libgwas_gb300.so"
+CLI_SRC = PKG / "cli" / "gwas_stream.cpp"
+CLI = PKG / "gwas_stream"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", str(INCLUDE)]
@@ -46,9 +50,26 @@ def up_to_date() -> bool:
     return all(p.stat().st_mtime <= t for p in _deps())
 
 
+def build_cli(force: bool = False) -> Path:
+    """Compile the streaming command-line driver against the library."""
+    if not force and CLI.exists() and CLI.stat().st_mtime >= max(
+            LIB.stat().st_mtime, CLI_SRC.stat().st_mtime, (INCLUDE / "gwas.h").stat().st_mtime):
+        return CLI
+    cxx = os.environ.get("CXX") or shutil.which("g++") or "g++"
+    tmp = CLI.with_suffix(".tmp")
+    cmd = [cxx, "-O2", "-std=c++17", "-I", str(INCLUDE), "-o", str(tmp), str(CLI_SRC),
+           "-L", str(PKG), "-lgwas_gb300", "-Wl,-rpath,$ORIGIN", "-pthread"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"building gwas_stream failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, CLI)
+    return CLI
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> Path:
-    """Compile the library if needed and return its path."""
+    """Compile the library (and the streaming driver) if needed; return the library path."""
     if not force and up_to_date():
+        build_cli()
         return LIB
     BUILD.mkdir(exist_ok=True)
     cc = nvcc()
@@ -72,6 +93,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    build_cli(force=True)
     return LIB
 
 

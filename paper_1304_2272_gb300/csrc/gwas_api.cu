@@ -79,6 +79,10 @@ struct gwas_ctx {
     gwas_stats stats{};
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed;  // pending trsm timings
     std::vector<cudaEvent_t> ev_pool;
+    // host-path blocks: number submitted, and the completion events (D2H done) of those
+    // from index done_base on that are not yet known to be complete
+    int64_t host_blocks = 0, done_base = 0;
+    std::vector<cudaEvent_t> done_ev;
 };
 
 namespace {
@@ -251,6 +255,7 @@ void free_all(gwas_ctx* c) {
         if (c->ev_d2h[s]) cudaEventDestroy(c->ev_d2h[s]);
     }
     for (auto& pr : c->timed) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    for (auto e : c->done_ev) cudaEventDestroy(e);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->s_comp) cudaStreamDestroy(c->s_comp);
     if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
@@ -535,6 +540,16 @@ static gwas_status host_block(gwas_ctx* c, const void* X, bool packed, const int
                            cudaMemcpyDeviceToHost, c->s_d2h));
     CK(cudaMemcpyAsync(status, c->sslot[s], (size_t)mb, cudaMemcpyDeviceToHost, c->s_d2h));
     CK(cudaEventRecord(c->ev_d2h[s], c->s_d2h));
+    // completion of this block for gwas_wait_block (drop the leading ones already done)
+    while (!c->done_ev.empty() && cudaEventQuery(c->done_ev.front()) == cudaSuccess) {
+        c->ev_pool.push_back(c->done_ev.front());
+        c->done_ev.erase(c->done_ev.begin());
+        ++c->done_base;
+    }
+    cudaEvent_t done = pooled_event(c);
+    CK(cudaEventRecord(done, c->s_d2h));
+    c->done_ev.push_back(done);
+    ++c->host_blocks;
     c->stats.h2d_bytes += (int64_t)in_bytes;
     c->stats.d2h_bytes += mb * t * p * 8 + (wald ? mb * t * 8 : 0) + mb;
     return GWAS_OK;
@@ -623,6 +638,39 @@ gwas_status gwas_sync(gwas_ctx* c, int timeout_ms) {
         if (el >= timeout_ms) return fail(c, GWAS_ERR_TIMEOUT, "gwas_sync: timed out");
         std::this_thread::sleep_for(std::chrono::microseconds(200));
     }
+}
+
+gwas_status gwas_wait_block(gwas_ctx* c, int64_t block, int timeout_ms) {
+    if (!c) return GWAS_ERR_ARG;
+    if (block < 0 || block >= c->host_blocks)
+        return fail(c, GWAS_ERR_ARG, "gwas_wait_block: no such host-path block");
+    if (block < c->done_base) return GWAS_OK;
+    DeviceGuard g(c->device);
+    cudaEvent_t e = c->done_ev[(size_t)(block - c->done_base)];
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t q = cudaEventQuery(e);
+        if (q == cudaSuccess) return GWAS_OK;
+        if (q != cudaErrorNotReady) return cuda_fail(c, q, "gwas_wait_block");
+        if (timeout_ms >= 0) {
+            const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(
+                                std::chrono::steady_clock::now() - t0).count();
+            if (el >= timeout_ms) return fail(c, GWAS_ERR_TIMEOUT, "gwas_wait_block: timed out");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+gwas_status gwas_host_alloc(size_t bytes, void** out) {
+    if (!out) return GWAS_ERR_ARG;
+    *out = nullptr;
+    if (bytes == 0) return GWAS_OK;
+    return cudaHostAlloc(out, bytes, cudaHostAllocPortable) == cudaSuccess ? GWAS_OK : GWAS_ERR_OOM;
+}
+
+gwas_status gwas_host_free(void* p) {
+    if (!p) return GWAS_OK;
+    return cudaFreeHost(p) == cudaSuccess ? GWAS_OK : GWAS_ERR_CUDA;
 }
 
 gwas_status gwas_finalize(gwas_ctx* c) {

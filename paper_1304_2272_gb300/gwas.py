@@ -91,6 +91,9 @@ SIGNATURES = {
     "gwas_solve_block_packed_device": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp, _vp]),
     "gwas_solve_all": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp]),
     "gwas_sync": (_int, [_ctx_p, _int]),
+    "gwas_wait_block": (_int, [_ctx_p, _i64, _int]),
+    "gwas_host_alloc": (_int, [ctypes.c_size_t, ctypes.POINTER(_vp)]),
+    "gwas_host_free": (_int, [_vp]),
     "gwas_finalize": (_int, [_ctx_p]),
     "gwas_last_error": (ctypes.c_char_p, [_ctx_p]),
     "gwas_error_index": (_i64, [_ctx_p]),
@@ -271,6 +274,23 @@ def gwas_solve_all(ctx, X, m: int, b, wald, status) -> None:
 
 def gwas_sync(ctx, timeout_ms: int = -1) -> None:
     _check(ctx, load().gwas_sync(ctx, int(timeout_ms)))
+
+
+def gwas_wait_block(ctx, block: int, timeout_ms: int = -1) -> None:
+    _check(ctx, load().gwas_wait_block(ctx, int(block), int(timeout_ms)))
+
+
+def gwas_host_alloc(nbytes: int) -> int:
+    """Address of nbytes of page-locked host memory (free with gwas_host_free)."""
+    p = _vp()
+    st = load().gwas_host_alloc(int(nbytes), ctypes.byref(p))
+    if st != GWAS_OK:
+        raise GwasError(st, "gwas_host_alloc failed")
+    return int(p.value or 0)
+
+
+def gwas_host_free(addr: int) -> None:
+    load().gwas_host_free(addr)
 
 
 def gwas_finalize(ctx) -> None:
