@@ -35,7 +35,7 @@ namespace {
 
 struct Args {
     int64_t n = 0, m = 0, m_blk = 16384;
-    int q = 0, t = 1, limbs = 3, device = 0;
+    int q = 0, t = 1, limbs = 3, device = 0, readers = 2;
     double h = 0.4, sigma2 = 1.0;
     bool mixed = false, m_given = false;
     std::string phi, covar, pheno, bed, dosages, out;
@@ -49,7 +49,7 @@ struct Args {
 void usage() {
     die(1, "usage: gwas_stream --n N --q Q [--t T] --phi F --covar F --pheno F "
            "(--bed F | --dosages F) --m M [--m-blk B] [--h H] [--sigma2 S] [--m-given] "
-           "[--precision fp64|mixed] [--limbs L] [--device D] --out PREFIX");
+           "[--precision fp64|mixed] [--limbs L] [--device D] [--readers R] --out PREFIX");
 }
 
 Args parse(int argc, char** argv) {
@@ -70,6 +70,7 @@ Args parse(int argc, char** argv) {
         else if (k == "--m-given") a.m_given = true;
         else if (k == "--limbs") a.limbs = std::stoi(val());
         else if (k == "--device") a.device = std::stoi(val());
+        else if (k == "--readers") a.readers = std::stoi(val());
         else if (k == "--precision") {
             const std::string v = val();
             if (v == "mixed") a.mixed = true;
@@ -82,7 +83,8 @@ Args parse(int argc, char** argv) {
         else if (k == "--out") a.out = val();
         else usage();
     }
-    if (a.n < 1 || a.q < 1 || a.t < 1 || a.m < 1 || a.m_blk < 1 || a.phi.empty() ||
+    if (a.n < 1 || a.q < 1 || a.t < 1 || a.m < 1 || a.m_blk < 1 || a.readers < 1 ||
+        a.readers > 8 || a.phi.empty() ||
         a.covar.empty() || a.pheno.empty() || a.out.empty() || a.bed.empty() == a.dosages.empty())
         usage();
     return a;
@@ -152,8 +154,9 @@ int main(int argc, char** argv) {
     const double setup_s =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_setup).count();
 
-    // streaming: NB page-locked input buffers and output slots
-    const int NB = 3;
+    // streaming: NB page-locked input buffers and output slots; `readers` threads read
+    // the blocks in turn (block blk by thread blk % readers) so that file reads overlap
+    const int R = a.readers, NB = R + 2;
     const int64_t mblk = o.m_blk, nblk = (a.m + mblk - 1) / mblk;
     std::vector<void*> in(NB, nullptr), ob(NB, nullptr), ow(NB, nullptr), os(NB, nullptr);
     for (int k = 0; k < NB; ++k) {
@@ -167,16 +170,19 @@ int main(int argc, char** argv) {
 
     Ring ring;
     ring.filled.assign(NB, -1);
-    std::vector<char> free_(NB, 1);
-    double read_s = 0.0;
-    std::thread reader([&] {
-        for (int64_t blk = 0; blk < nblk; ++blk) {
+    // owner[k]: the last block collected from buffer k (initially k - NB, so that blocks
+    // 0 .. NB-1 find their buffers free)
+    std::vector<int64_t> owner(NB);
+    for (int k = 0; k < NB; ++k) owner[k] = k - NB;
+    std::vector<double> read_s(R, 0.0);
+    auto read_loop = [&](int r) {
+        for (int64_t blk = r; blk < nblk; blk += R) {
             const int k = (int)(blk % NB);
             {
+                // buffer k is handed to block blk once block blk - NB has been collected
                 std::unique_lock<std::mutex> lk(ring.mu);
-                ring.cv.wait(lk, [&] { return free_[k] || ring.failed; });
+                ring.cv.wait(lk, [&] { return owner[k] == blk - NB || ring.failed; });
                 if (ring.failed) return;
-                free_[k] = 0;
             }
             const int64_t mb = std::min(mblk, a.m - blk * mblk);
             const size_t bytes = (size_t)(per_snp * mb);
@@ -184,18 +190,23 @@ int main(int argc, char** argv) {
             const auto t0 = std::chrono::steady_clock::now();
             size_t done = 0;
             while (done < bytes) {
-                const ssize_t r = ::pread(fd, (char*)in[k] + done, bytes - done, off + (off_t)done);
-                if (r <= 0) break;
-                done += (size_t)r;
+                const ssize_t got = ::pread(fd, (char*)in[k] + done, bytes - done, off + (off_t)done);
+                if (got <= 0) break;
+                done += (size_t)got;
             }
-            read_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            read_s[r] += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
             std::lock_guard<std::mutex> lk(ring.mu);
             if (done != bytes) ring.failed = true;
             else ring.filled[k] = blk;
             ring.cv.notify_all();
             if (ring.failed) return;
         }
-    });
+    };
+    std::vector<std::thread> reader;
+    for (int r = 0; r < R; ++r) reader.emplace_back(read_loop, r);
+    auto join_readers = [&] {
+        for (auto& th : reader) th.join();
+    };
 
     static const int8_t PLINK[4] = {2, -1, 1, 0};  // 00 hom first, 01 missing, 10 het, 11 hom second
     const auto t0 = std::chrono::steady_clock::now();
@@ -208,7 +219,7 @@ int main(int argc, char** argv) {
         std::memcpy(&W[(size_t)(blk * mblk * a.t)], ow[k], (size_t)(mb * a.t * 8));
         std::memcpy(&St[(size_t)(blk * mblk)], os[k], (size_t)mb);
         std::lock_guard<std::mutex> lk(ring.mu);
-        free_[k] = 1;
+        owner[k] = blk;
         ring.filled[k] = -1;
         ring.cv.notify_all();
     };
@@ -220,7 +231,7 @@ int main(int argc, char** argv) {
             ring.cv.wait(lk, [&] { return ring.filled[k] == blk || ring.failed; });
             if (ring.failed) {
                 lk.unlock();
-                reader.join();
+                join_readers();
                 die(4, "short read of the genotype file");
             }
             wait_read_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - tw).count();
@@ -237,7 +248,7 @@ int main(int argc, char** argv) {
         if (blk >= NB - 1) collect(blk - (NB - 1));
     }
     for (int64_t blk = std::max<int64_t>(0, nblk - (NB - 1)); blk < nblk; ++blk) collect(blk);
-    reader.join();
+    join_readers();
     check(ctx, gwas_sync(ctx, -1), "gwas_sync");
     const double stream_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     ::close(fd);
@@ -248,10 +259,11 @@ int main(int argc, char** argv) {
     int64_t ok = 0;
     for (uint8_t s : St) ok += (s == 0);
     std::printf("{\"n\": %lld, \"m\": %lld, \"m_blk\": %lld, \"precision\": \"%s\", \"input\": \"%s\", "
-                "\"setup_s\": %.3f, \"stream_s\": %.3f, \"snps_per_s\": %.1f, \"read_s\": %.3f, "
+                "\"setup_s\": %.3f, \"stream_s\": %.3f, \"snps_per_s\": %.1f, \"read_thread_s\": %.3f, "
                 "\"solver_waited_for_reads_s\": %.3f, \"genotype_bytes\": %lld, \"status_ok\": %lld}\n",
                 (long long)a.n, (long long)a.m, (long long)mblk, a.mixed ? "mixed" : "fp64",
-                packed ? "bed" : "int8", setup_s, stream_s, (double)a.m / stream_s, read_s,
+                packed ? "bed" : "int8", setup_s, stream_s, (double)a.m / stream_s,
+                [&] { double t = 0; for (double v : read_s) t += v; return t; }(),
                 wait_read_s, (long long)(per_snp * a.m), (long long)ok);
     for (int k = 0; k < NB; ++k) {
         gwas_host_free(in[k]);
