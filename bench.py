@@ -172,8 +172,8 @@ def bf16_flops_per_snp(n: int, q: int, t: int, limbs: int) -> float:
 # the limb kernel, per L2 group size (captured with CTA pairs and fused rows; the traffic
 # depends on those, not on the pipeline depth).
 TRAFFIC = {
-    "k_block_fp64": {"file": "block_fp64.cu", "sha": "17f101cf32e7945d", "n": 10000,
-                     "m_blk": 16384, "bytes": 8830753024 + 101610496},
+    "k_block_fp64": {"file": "block_fp64.cu", "sha": "47c01bde2896f773", "n": 10000,
+                     "m_blk": 16384, "bytes": 2061468160 + 110667520},
     "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "886cdd079efba4ca", "n": 10000,
                          "m_blk": 16384, "single_cta": False, "no_fuse": False,
                          "bytes_by_group_mb": {40: 4036415744 + 81025792,

@@ -110,11 +110,21 @@ __device__ __forceinline__ void block_fp64_unit(const CohortDev& c, const int8_t
     }
 }
 
+// Units are taken group by group of `group` SNP tiles (a group's dosages stay in L2 while
+// every row tile of L^{-1} passes over them, so each dosage byte comes from DRAM about once
+// and each row tile of L^{-1} once per group), and within a group row tile by row tile,
+// the heaviest (longest k-range) first.
 __global__ void __launch_bounds__(256)
 k_block_fp64(CohortDev c, const int8_t* __restrict__ X, int64_t ldx, int64_t mb, int n_rt,
-             int n_ct, double* __restrict__ part, int64_t ldp, uint8_t* __restrict__ bad) {
-    const int unit = blockIdx.x;
-    block_fp64_unit(c, X, ldx, mb, n_rt, n_rt - 1 - unit / n_ct, unit % n_ct, part, ldp, bad);
+             int n_ct, int group, double* __restrict__ part, int64_t ldp,
+             uint8_t* __restrict__ bad) {
+    const int64_t u = blockIdx.x;
+    const int64_t per_group = (int64_t)n_rt * group;
+    const int g = (int)(u / per_group);
+    const int gsz = min(group, n_ct - g * group);
+    const int local = (int)(u - g * per_group);
+    block_fp64_unit(c, X, ldx, mb, n_rt, n_rt - 1 - local / gsz, g * group + local % gsz, part,
+                    ldp, bad);
 }
 
 // Batched cohorts: one grid over every cohort's units (cohort found by binary search).
@@ -148,7 +158,9 @@ cudaError_t launch_block_fp64(const CohortDev& c, const int8_t* X, int64_t ldx, 
     const int64_t units = (int64_t)n_rt * n_ct;
     if (units <= 0) return cudaSuccess;
     if (units > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_block_fp64<<<(unsigned)units, 256, 0, s>>>(c, X, ldx, mb, n_rt, n_ct, part, ldp, bad);
+    // SNP tiles per group: 40 MB of int8 dosages
+    const int group = (int)std::max<int64_t>(1, std::min<int64_t>(n_ct, (40ll << 20) / (T64 * ldx)));
+    k_block_fp64<<<(unsigned)units, 256, 0, s>>>(c, X, ldx, mb, n_rt, n_ct, group, part, ldp, bad);
     return cudaGetLastError();
 }
 
