@@ -41,25 +41,14 @@ cudaError_t launch_build_M(const double* src, int64_t lds, double* M, int64_t ld
 // Thread (tx, ty) owns rows tx + 16 a and columns ty + 16 b of the tile, so a warp
 // stores 16 consecutive rows of a column-major C.
 // ----------------------------------------------------------------------------
+// acc[a][b] += sum_{k in [kbeg, kend)} op(A)(i0 + tx + 16a, k) op(B)(k, j0 + ty + 16b)
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
+__device__ __forceinline__ void gemm_tile(const GemmF64& g, int64_t i0, int64_t j0, int64_t kbeg,
+                                          int64_t kend, double (&acc)[4][4]) {
     __shared__ double As[KC64][T64 + 1];  // As[k][i] = op(A)(i0 + i, k0 + k)
     __shared__ double Bs[KC64][T64 + 1];  // Bs[k][j] = op(B)(k0 + k, j0 + j)
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
-    const int64_t i0 = (int64_t)blockIdx.x * T64, j0 = (int64_t)blockIdx.y * T64;
-    if (g.c_lower && j0 > i0) return;
-    int64_t kbeg = 0, kend = g.K;
-    if (g.a_lower) kend = min64(kend, i0 + T64);
-    if (g.a_upper) kbeg = i0;
-    if (g.b_lower && j0 > kbeg) kbeg = j0;
-
-    double acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-
     for (int64_t k0 = kbeg; k0 < kend; k0 += KC64) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -96,6 +85,25 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
         }
         __syncthreads();
     }
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t i0 = (int64_t)blockIdx.x * T64, j0 = (int64_t)blockIdx.y * T64;
+    if (g.c_lower && j0 > i0) return;
+    int64_t kbeg = 0, kend = g.K;
+    if (g.a_lower) kend = min64(kend, i0 + T64);
+    if (g.a_upper) kbeg = i0;
+    if (g.b_lower && j0 > kbeg) kbeg = j0;
+
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    gemm_tile<TA, TB>(g, i0, j0, kbeg, kend, acc);
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int64_t gi = i0 + tx + 16 * a;
@@ -111,8 +119,55 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
     }
 }
 
+// Skinny products (one 64 x 64 output tile, long K: the Gram matrices A^T B of n x q
+// panels): CTA s accumulates k in [s chunk, (s+1) chunk) into ws[s]; k_splitk_reduce adds
+// the slices in ascending s (fixed order) and applies alpha and beta.
+__global__ void __launch_bounds__(256) k_gemm_tn_splitk(GemmF64 g, int64_t chunk, double* ws) {
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t kbeg = (int64_t)blockIdx.x * chunk, kend = min64(g.K, kbeg + chunk);
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    gemm_tile<true, false>(g, 0, 0, kbeg, kend, acc);
+    double* w = ws + (int64_t)blockIdx.x * T64 * T64;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) w[(tx + 16 * a) + (ty + 16 * b) * T64] = acc[a][b];
+}
+
+__global__ void k_splitk_reduce(GemmF64 g, int splits, const double* __restrict__ ws) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = e % T64, j = e / T64;
+    if (j >= T64 || i >= g.M || j >= g.N) return;
+    double sum = 0.0;
+    for (int s2 = 0; s2 < splits; ++s2) sum += ws[(int64_t)s2 * T64 * T64 + i + j * T64];
+    double* c = g.C + i + (int64_t)j * g.ldc;
+    const double v = g.alpha * sum;
+    *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
+}
+
 cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    const bool skinny = g.transA && !g.transB && g.M <= T64 && g.N <= T64 && g.K >= 8192 &&
+                        !g.a_lower && !g.a_upper && !g.b_lower && !g.c_lower;
+    if (skinny) {
+        const int64_t splits = std::min<int64_t>(304, ceil_div(g.K, 256));
+        const int64_t chunk = round_up(ceil_div(g.K, splits), KC64);
+        const int nsplit = (int)ceil_div(g.K, chunk);
+        double* ws = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws),
+                                        (size_t)nsplit * T64 * T64 * sizeof(double), s);
+        if (e != cudaSuccess) return e;
+        k_gemm_tn_splitk<<<(unsigned)nsplit, 256, 0, s>>>(g, chunk, ws);
+        k_splitk_reduce<<<T64 * T64 / 256, 256, 0, s>>>(g, nsplit, ws);
+        e = cudaGetLastError();
+        const cudaError_t f = cudaFreeAsync(ws, s);
+        return e != cudaSuccess ? e : f;
+    }
     dim3 grid((unsigned)ceil_div(g.M, T64), (unsigned)ceil_div(g.N, T64));
     if (!g.transA && !g.transB) k_gemm_f64<false, false><<<grid, 256, 0, s>>>(g);
     else if (!g.transA && g.transB) k_gemm_f64<false, true><<<grid, 256, 0, s>>>(g);
