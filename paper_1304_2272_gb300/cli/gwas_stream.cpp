@@ -13,8 +13,13 @@
 //                  dosage is the count of the first allele, missing calls give status 2)
 //   --dosages FILE n bytes per SNP, int8 dosages {0,1,2}
 // Outputs: PREFIX.b (m x t x p float64, SNP-major), PREFIX.wald (m x t float64),
-// PREFIX.status (m uint8: 0 ok, 1 singular, 2 bad or missing genotype), and one JSON line
-// on stdout with the timings.
+// PREFIX.status (m uint8: 0 ok, 1 singular, 2 bad or missing genotype), written block by
+// block, and one JSON line on stdout with the timings.
+// Checkpoint / resume: with --checkpoint every completed block is flushed to disk and then
+// recorded in PREFIX.progress (written to a temporary file and renamed, so it never claims
+// more than is on disk); --resume continues a job from the blocks PREFIX.progress records
+// (the job's sizes and formats must match); --max-blocks K stops cleanly after K new
+// blocks (a time-sliced run; resume it later).
 #include <fcntl.h>
 #include <unistd.h>
 
@@ -37,7 +42,8 @@ struct Args {
     int64_t n = 0, m = 0, m_blk = 16384;
     int q = 0, t = 1, limbs = 3, device = 0, readers = 2;
     double h = 0.4, sigma2 = 1.0;
-    bool mixed = false, m_given = false;
+    bool mixed = false, m_given = false, checkpoint = false, resume = false;
+    int64_t max_blocks = -1;
     std::string phi, covar, pheno, bed, dosages, out;
 };
 
@@ -49,7 +55,8 @@ struct Args {
 void usage() {
     die(1, "usage: gwas_stream --n N --q Q [--t T] --phi F --covar F --pheno F "
            "(--bed F | --dosages F) --m M [--m-blk B] [--h H] [--sigma2 S] [--m-given] "
-           "[--precision fp64|mixed] [--limbs L] [--device D] [--readers R] --out PREFIX");
+           "[--precision fp64|mixed] [--limbs L] [--device D] [--readers R] "
+           "[--checkpoint] [--resume] [--max-blocks K] --out PREFIX");
 }
 
 Args parse(int argc, char** argv) {
@@ -71,6 +78,9 @@ Args parse(int argc, char** argv) {
         else if (k == "--limbs") a.limbs = std::stoi(val());
         else if (k == "--device") a.device = std::stoi(val());
         else if (k == "--readers") a.readers = std::stoi(val());
+        else if (k == "--checkpoint") a.checkpoint = true;
+        else if (k == "--resume") a.resume = a.checkpoint = true;
+        else if (k == "--max-blocks") a.max_blocks = std::stoll(val()), a.checkpoint = true;
         else if (k == "--precision") {
             const std::string v = val();
             if (v == "mixed") a.mixed = true;
@@ -100,10 +110,45 @@ std::vector<double> read_f64(const std::string& path, size_t count) {
     return v;
 }
 
-void write_all(const std::string& path, const void* p, size_t bytes) {
-    FILE* f = std::fopen(path.c_str(), "wb");
-    if (!f || std::fwrite(p, 1, bytes, f) != bytes) die(5, "cannot write " + path);
+void pwrite_all(int fd, const void* p, size_t bytes, off_t off, const std::string& what) {
+    size_t done = 0;
+    while (done < bytes) {
+        const ssize_t w = ::pwrite(fd, (const char*)p + done, bytes - done, off + (off_t)done);
+        if (w <= 0) die(5, "cannot write " + what);
+        done += (size_t)w;
+    }
+}
+
+// The job identity recorded with the progress: a resume must describe the same job.
+std::string job_key(const Args& a, int64_t mblk) {
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "n=%lld m=%lld m_blk=%lld q=%d t=%d input=%s precision=%s limbs=%d",
+                  (long long)a.n, (long long)a.m, (long long)mblk, a.q, a.t,
+                  a.bed.empty() ? "int8" : "bed", a.mixed ? "mixed" : "fp64", a.limbs);
+    return buf;
+}
+
+int64_t read_progress(const std::string& path, const std::string& key) {
+    FILE* f = std::fopen(path.c_str(), "r");
+    if (!f) return 0;  // nothing done yet
+    char line[512] = {0};
+    const bool got = std::fgets(line, sizeof line, f) != nullptr;
     std::fclose(f);
+    const std::string s = got ? std::string(line) : std::string();
+    const std::string head = "gwas_stream-progress " + key + " blocks=";
+    if (s.compare(0, head.size(), head) != 0) die(6, path + " belongs to another job");
+    return std::stoll(s.substr(head.size()));
+}
+
+void write_progress(const std::string& path, const std::string& key, int64_t blocks) {
+    const std::string tmp = path + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) die(5, "cannot write " + tmp);
+    std::fprintf(f, "gwas_stream-progress %s blocks=%lld\n", key.c_str(), (long long)blocks);
+    std::fflush(f);
+    ::fsync(::fileno(f));
+    std::fclose(f);
+    if (std::rename(tmp.c_str(), path.c_str()) != 0) die(5, "cannot update " + path);
 }
 
 void check(gwas_ctx* ctx, gwas_status st, const char* what) {
@@ -165,8 +210,18 @@ int main(int argc, char** argv) {
         check(ctx, gwas_host_alloc((size_t)(mblk * a.t * 8), &ow[k]), "gwas_host_alloc");
         check(ctx, gwas_host_alloc((size_t)mblk, &os[k]), "gwas_host_alloc");
     }
-    std::vector<double> B((size_t)(a.m * a.t * p)), W((size_t)(a.m * a.t));
-    std::vector<uint8_t> St((size_t)a.m);
+    // outputs, written block by block; blocks [b0, nblk) are this run's
+    const std::string key = job_key(a, mblk), progress = a.out + ".progress";
+    const int64_t b0 = a.resume ? read_progress(progress, key) : 0;
+    if (b0 > nblk) die(6, progress + " records more blocks than the job has");
+    const int64_t b_end = a.max_blocks >= 0 ? std::min(nblk, b0 + a.max_blocks) : nblk;
+    const int oflags = O_RDWR | O_CREAT | (a.resume ? 0 : O_TRUNC);
+    const int fb = ::open((a.out + ".b").c_str(), oflags, 0644);
+    const int fw = ::open((a.out + ".wald").c_str(), oflags, 0644);
+    const int fs = ::open((a.out + ".status").c_str(), oflags, 0644);
+    if (fb < 0 || fw < 0 || fs < 0) die(5, "cannot open the output files " + a.out + ".*");
+    if (a.checkpoint && !a.resume) write_progress(progress, key, 0);
+    int64_t ok = 0;
 
     Ring ring;
     ring.filled.assign(NB, -1);
@@ -175,13 +230,15 @@ int main(int argc, char** argv) {
     std::vector<int64_t> owner(NB);
     for (int k = 0; k < NB; ++k) owner[k] = k - NB;
     std::vector<double> read_s(R, 0.0);
+    // li = blk - b0 is the block's index in this run (buffers, owners, gwas_wait_block)
     auto read_loop = [&](int r) {
-        for (int64_t blk = r; blk < nblk; blk += R) {
-            const int k = (int)(blk % NB);
+        for (int64_t li = r; b0 + li < b_end; li += R) {
+            const int64_t blk = b0 + li;
+            const int k = (int)(li % NB);
             {
-                // buffer k is handed to block blk once block blk - NB has been collected
+                // buffer k is handed to block li once block li - NB has been collected
                 std::unique_lock<std::mutex> lk(ring.mu);
-                ring.cv.wait(lk, [&] { return owner[k] == blk - NB || ring.failed; });
+                ring.cv.wait(lk, [&] { return owner[k] == li - NB || ring.failed; });
                 if (ring.failed) return;
             }
             const int64_t mb = std::min(mblk, a.m - blk * mblk);
@@ -197,7 +254,7 @@ int main(int argc, char** argv) {
             read_s[r] += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
             std::lock_guard<std::mutex> lk(ring.mu);
             if (done != bytes) ring.failed = true;
-            else ring.filled[k] = blk;
+            else ring.filled[k] = li;
             ring.cv.notify_all();
             if (ring.failed) return;
         }
@@ -211,24 +268,33 @@ int main(int argc, char** argv) {
     static const int8_t PLINK[4] = {2, -1, 1, 0};  // 00 hom first, 01 missing, 10 het, 11 hom second
     const auto t0 = std::chrono::steady_clock::now();
     double wait_read_s = 0.0;
-    auto collect = [&](int64_t blk) {  // outputs of a completed block into the result arrays
-        const int k = (int)(blk % NB);
-        check(ctx, gwas_wait_block(ctx, blk, -1), "gwas_wait_block");
+    auto collect = [&](int64_t li) {  // a completed block's outputs to the output files
+        const int64_t blk = b0 + li;
+        const int k = (int)(li % NB);
+        check(ctx, gwas_wait_block(ctx, li, -1), "gwas_wait_block");
         const int64_t mb = std::min(mblk, a.m - blk * mblk);
-        std::memcpy(&B[(size_t)(blk * mblk * a.t * p)], ob[k], (size_t)(mb * a.t * p * 8));
-        std::memcpy(&W[(size_t)(blk * mblk * a.t)], ow[k], (size_t)(mb * a.t * 8));
-        std::memcpy(&St[(size_t)(blk * mblk)], os[k], (size_t)mb);
+        pwrite_all(fb, ob[k], (size_t)(mb * a.t * p * 8), (off_t)(blk * mblk * a.t * p * 8), a.out + ".b");
+        pwrite_all(fw, ow[k], (size_t)(mb * a.t * 8), (off_t)(blk * mblk * a.t * 8), a.out + ".wald");
+        pwrite_all(fs, os[k], (size_t)mb, (off_t)(blk * mblk), a.out + ".status");
+        for (int64_t i = 0; i < mb; ++i) ok += (((const uint8_t*)os[k])[i] == 0);
+        if (a.checkpoint) {  // on disk first, then recorded
+            if (::fdatasync(fb) != 0 || ::fdatasync(fw) != 0 || ::fdatasync(fs) != 0)
+                die(5, "cannot flush the output files");
+            write_progress(progress, key, blk + 1);
+        }
         std::lock_guard<std::mutex> lk(ring.mu);
-        owner[k] = blk;
+        owner[k] = li;
         ring.filled[k] = -1;
         ring.cv.notify_all();
     };
-    for (int64_t blk = 0; blk < nblk; ++blk) {
-        const int k = (int)(blk % NB);
+    const int64_t nrun = b_end - b0;
+    for (int64_t li = 0; li < nrun; ++li) {
+        const int64_t blk = b0 + li;
+        const int k = (int)(li % NB);
         {
             const auto tw = std::chrono::steady_clock::now();
             std::unique_lock<std::mutex> lk(ring.mu);
-            ring.cv.wait(lk, [&] { return ring.filled[k] == blk || ring.failed; });
+            ring.cv.wait(lk, [&] { return ring.filled[k] == li || ring.failed; });
             if (ring.failed) {
                 lk.unlock();
                 join_readers();
@@ -245,26 +311,28 @@ int main(int argc, char** argv) {
             check(ctx, gwas_solve_block(ctx, (const int8_t*)in[k], mb, (double*)ob[k],
                                         (double*)ow[k], (uint8_t*)os[k]),
                   "gwas_solve_block");
-        if (blk >= NB - 1) collect(blk - (NB - 1));
+        if (li >= NB - 1) collect(li - (NB - 1));
     }
-    for (int64_t blk = std::max<int64_t>(0, nblk - (NB - 1)); blk < nblk; ++blk) collect(blk);
+    for (int64_t li = std::max<int64_t>(0, nrun - (NB - 1)); li < nrun; ++li) collect(li);
     join_readers();
     check(ctx, gwas_sync(ctx, -1), "gwas_sync");
     const double stream_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     ::close(fd);
 
-    write_all(a.out + ".b", B.data(), B.size() * sizeof(double));
-    write_all(a.out + ".wald", W.data(), W.size() * sizeof(double));
-    write_all(a.out + ".status", St.data(), St.size());
-    int64_t ok = 0;
-    for (uint8_t s : St) ok += (s == 0);
+    ::close(fb);
+    ::close(fw);
+    ::close(fs);
+    const int64_t snps_run = std::min(a.m, b_end * mblk) - std::min(a.m, b0 * mblk);
     std::printf("{\"n\": %lld, \"m\": %lld, \"m_blk\": %lld, \"precision\": \"%s\", \"input\": \"%s\", "
+                "\"first_block\": %lld, \"blocks_done\": %lld, \"blocks\": %lld, \"complete\": %s, "
                 "\"setup_s\": %.3f, \"stream_s\": %.3f, \"snps_per_s\": %.1f, \"read_thread_s\": %.3f, "
                 "\"solver_waited_for_reads_s\": %.3f, \"genotype_bytes\": %lld, \"status_ok\": %lld}\n",
                 (long long)a.n, (long long)a.m, (long long)mblk, a.mixed ? "mixed" : "fp64",
-                packed ? "bed" : "int8", setup_s, stream_s, (double)a.m / stream_s,
+                packed ? "bed" : "int8", (long long)b0, (long long)b_end, (long long)nblk,
+                b_end == nblk ? "true" : "false", setup_s, stream_s,
+                stream_s > 0 ? (double)snps_run / stream_s : 0.0,
                 [&] { double t = 0; for (double v : read_s) t += v; return t; }(),
-                wait_read_s, (long long)(per_snp * a.m), (long long)ok);
+                wait_read_s, (long long)(per_snp * snps_run), (long long)ok);
     for (int k = 0; k < NB; ++k) {
         gwas_host_free(in[k]);
         gwas_host_free(ob[k]);

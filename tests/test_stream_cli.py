@@ -80,3 +80,32 @@ def test_short_genotype_file_is_an_error(gpu, tmp_path):
                  tmp_path / "covar.f64", "--pheno", tmp_path / "pheno.f64", "--dosages",
                  tmp_path / "dos.i8", "--m", 80, "--m-blk", 32, "--out", tmp_path / "o"])
     assert r.returncode == 4 and "short read" in r.stderr
+
+
+@pytest.mark.gpu
+def test_checkpoint_and_resume(gpu, tmp_path):
+    """A job stopped after 2 of its 5 blocks and resumed writes the same bytes as one
+    uninterrupted run; a resume with other job sizes is refused."""
+    n, m = 257, 300
+    c = synth.make_cohort(73, n, n_markers=300)
+    X = c.snps(m)
+    write_inputs(tmp_path, c, X)
+    base = ["--n", n, "--q", 3, "--phi", tmp_path / "phi.f64", "--covar", tmp_path / "covar.f64",
+            "--pheno", tmp_path / "pheno.f64", "--bed", tmp_path / "g.bed", "--m", m,
+            "--m-blk", 64, "--h", c.h, "--sigma2", c.sigma2]
+    full = run_cli([*base, "--out", tmp_path / "full"])
+    assert full.returncode == 0, full.stderr
+    first = run_cli([*base, "--checkpoint", "--max-blocks", 2, "--out", tmp_path / "part"])
+    assert first.returncode == 0, first.stderr
+    info = json.loads(first.stdout.strip().splitlines()[-1])
+    assert info["blocks_done"] == 2 and info["blocks"] == 5 and info["complete"] is False
+    assert (tmp_path / "part.progress").read_text().strip().endswith("blocks=2")
+    rest = run_cli([*base, "--resume", "--out", tmp_path / "part"])
+    assert rest.returncode == 0, rest.stderr
+    info = json.loads(rest.stdout.strip().splitlines()[-1])
+    assert info["first_block"] == 2 and info["complete"] is True
+    for ext in (".b", ".wald", ".status"):
+        assert (tmp_path / ("part" + ext)).read_bytes() == (tmp_path / ("full" + ext)).read_bytes()
+    other = [*base[:-6], "--m-blk", 32, "--h", c.h, "--sigma2", c.sigma2]
+    bad = run_cli([*other, "--resume", "--out", tmp_path / "part"])
+    assert bad.returncode == 6 and "another job" in bad.stderr
