@@ -219,6 +219,25 @@ def traffic_for(kernel: str, n: int, m_blk: int, tile_cfg=None):
     return nbytes if sha == rec["sha"] else None
 
 
+def h2d_peak_gbs(pinned, dev) -> float:
+    """Host -> device copy rate of one pinned block on its own (cudaMemcpyAsync through
+    torch, CUDA events), the denominator of the streaming roofline."""
+    import torch
+    d = torch.empty(pinned.shape, dtype=pinned.dtype, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        d.copy_(pinned, non_blocking=True)          # warm-up
+        e0.record(s)
+        for _ in range(3):
+            d.copy_(pinned, non_blocking=True)
+        e1.record(s)
+    e1.synchronize()
+    nbytes = pinned.numel() * pinned.element_size()
+    return 3 * nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
 def pack_2bit_torch(Xd):
     """(mb, n) device dosages in {0,1,2} -> (mb, ceil(n/4)) uint8 2-bit calls, four
     individuals per byte (individual k in bits 2(k%4), 2(k%4)+1 of byte k/4)."""
@@ -402,6 +421,8 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
         # device-resident rate survives streaming (1.0 = copies fully hidden)
         e2e["h2d_gbs"] = n * mb * steps * world / e2e_s / 1e9
         e2e["streamed_over_resident"] = e2e["value"] / value
+        e2e["h2d_peak_gbs"] = h2d_peak_gbs(hpool[0], dev)
+        e2e["h2d_frac"] = e2e["h2d_gbs"] / world / e2e["h2d_peak_gbs"]
         # the same stream as 2-bit calls (n/4 bytes per SNP), unpacked on the GPU
         ppool = [pack_2bit_torch(x).cpu().pin_memory() for x in pool[:2]]
         for s in range(warmup):
