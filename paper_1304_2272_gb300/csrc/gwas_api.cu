@@ -117,7 +117,9 @@ gwas_status cuda_fail(gwas_ctx* c, cudaError_t e, const char* where) {
 
 template <typename T>
 cudaError_t dmalloc(T** p, size_t count) {
-    return cudaMalloc((void**)p, count * sizeof(T) + 256);
+    const cudaError_t e = cudaMalloc((void**)p, count * sizeof(T) + 256);
+    if (e != cudaSuccess) *p = nullptr;  // a failed allocation leaves nothing to free or use
+    return e;
 }
 
 CohortDev cohort_view(const gwas_ctx* c) {
@@ -490,13 +492,12 @@ static gwas_status check_block_args(gwas_ctx* c, const int8_t* X, int64_t mb, do
 // The host-memory path's device slots are allocated on its first use, so contexts that
 // only ever take device pointers (gwas_solve_block_device, batches) never hold them.
 static gwas_status ensure_host_slots(gwas_ctx* c) {
-    if (c->Xslot[0]) return GWAS_OK;
     const int64_t mblk = c->opts.m_blk;
-    for (int s = 0; s < 2; ++s) {
-        CK(dmalloc(&c->Xslot[s], (size_t)c->n * mblk));
-        CK(dmalloc(&c->bslot[s], (size_t)mblk * c->t * c->p));
-        CK(dmalloc(&c->wslot[s], (size_t)mblk * c->t));
-        CK(dmalloc(&c->sslot[s], (size_t)mblk));
+    for (int s = 0; s < 2; ++s) {  // each buffer on its own, so a failed call can be retried
+        if (!c->Xslot[s]) CK(dmalloc(&c->Xslot[s], (size_t)c->n * mblk));
+        if (!c->bslot[s]) CK(dmalloc(&c->bslot[s], (size_t)mblk * c->t * c->p));
+        if (!c->wslot[s]) CK(dmalloc(&c->wslot[s], (size_t)mblk * c->t));
+        if (!c->sslot[s]) CK(dmalloc(&c->sslot[s], (size_t)mblk));
     }
     return GWAS_OK;
 }
@@ -510,8 +511,9 @@ static gwas_status host_block(gwas_ctx* c, const void* X, bool packed, const int
     gwas_status st;
     if ((st = ensure_host_slots(c)) != GWAS_OK) return st;
     const int64_t pbytes = ceil_div(c->n, 4);
-    if (packed && !c->Pslot[0])
-        for (int k = 0; k < 2; ++k) CK(dmalloc(&c->Pslot[k], (size_t)pbytes * c->opts.m_blk));
+    if (packed)
+        for (int k = 0; k < 2; ++k)
+            if (!c->Pslot[k]) CK(dmalloc(&c->Pslot[k], (size_t)pbytes * c->opts.m_blk));
     const int s = c->slot;
     c->slot ^= 1;
     const int64_t t = c->t, p = c->p;
