@@ -903,13 +903,18 @@ gwas_status gwas_set_tile_cfg(gwas_ctx* c, int tile_cfg) {
     }
     c->opts.tile_cfg = tile_cfg;
     const bool relayout = m.R != old_R || m.NT != old_NT || m.fused != old_fused;
-    if (relayout) {
-        CK(mixed_alloc_layout(m));
-    }
-    if (c->factored && (relayout || m.pair != old_pair || m.radix != old_radix)) {
-        int64_t nl = 0;
-        CK(mixed_prepare(m, c->W, c->ld, c->Z, c->s_comp, &nl));
-        CK(cudaStreamSynchronize(c->s_comp));
+    const bool was_factored = c->factored;
+    if (relayout || (was_factored && (m.pair != old_pair || m.radix != old_radix))) {
+        // the limbs are rebuilt: until that succeeds the context holds no usable factor
+        // (a failed re-allocation must not leave a solve launching on freed buffers)
+        c->factored = false;
+        if (relayout) CK(mixed_alloc_layout(m));
+        if (was_factored) {
+            int64_t nl = 0;
+            CK(mixed_prepare(m, c->W, c->ld, c->Z, c->s_comp, &nl));
+            CK(cudaStreamSynchronize(c->s_comp));
+            c->factored = true;
+        }
     }
     return GWAS_OK;
 }
