@@ -56,3 +56,42 @@ def test_host_side_errors_are_status_codes(gpu):
         X2[3, 5] = 7
         b, w, s = e.solve(X2)
         assert s[5] == 2 and np.all(np.isnan(b[5])) and np.all(s[np.arange(40) != 5] == 0)
+
+
+@pytest.mark.gpu
+def test_wait_block_and_pinned_host_buffers(gpu):
+    """Host-path blocks in page-locked buffers from gwas_host_alloc: gwas_wait_block(k)
+    returns once block k's outputs are in host memory; a block not yet submitted is an
+    argument error; the results equal those of gwas_solve_all."""
+    import ctypes
+    from paper_1304_2272_gb300 import gwas as gw
+    c = synth.make_cohort(81, 200, n_markers=200)
+    X = c.snps(3 * 64)
+    n, mb, p = c.n, 64, 4
+    with gw.GLS(n, p, 1, m_blk=mb) as e:
+        e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
+        ref = e.solve(X)
+        xs = gw.gwas_host_alloc(n * mb * 3)
+        bs = gw.gwas_host_alloc(mb * p * 8 * 3)
+        ss = gw.gwas_host_alloc(mb * 3)
+        try:
+            ctypes.memmove(xs, np.ascontiguousarray(X.T).ctypes.data, n * mb * 3)
+            first = gw.gwas_get_stats(e.ctx)["blocks"]
+            for k in range(3):
+                gw.gwas_solve_block(e.ctx, xs + k * n * mb, mb, bs + k * mb * p * 8, None,
+                                    ss + k * mb)
+            base = 3  # e.solve above ran 3 host-path blocks through gwas_solve_all
+            for k in range(3):
+                gw.gwas_wait_block(e.ctx, base + k, 5000)
+            with pytest.raises(gw.GwasError) as ei:
+                gw.gwas_wait_block(e.ctx, base + 3, 10)
+            assert ei.value.status == gw.GWAS_ERR_ARG
+            b = np.frombuffer((ctypes.c_double * (3 * mb * p)).from_address(bs), dtype=np.float64)
+            s = np.frombuffer((ctypes.c_uint8 * (3 * mb)).from_address(ss), dtype=np.uint8)
+            np.testing.assert_array_equal(b.reshape(3 * mb, 1, p), ref[0])
+            np.testing.assert_array_equal(s, ref[2])
+            assert gw.gwas_get_stats(e.ctx)["blocks"] == first + 3
+        finally:
+            gw.gwas_host_free(xs)
+            gw.gwas_host_free(bs)
+            gw.gwas_host_free(ss)
