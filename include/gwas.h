@@ -169,6 +169,17 @@ gwas_status gwas_solve_block_device(gwas_ctx* ctx, const int8_t* X, int64_t mb, 
                                     double* wald, uint8_t* status);
 
 /*
+ * As gwas_solve_block_device, and also S_i^{-1} = (X_i^T M^{-1} X_i)^{-1} of every SNP into
+ * cov (DEVICE, mb x p x p float64, SNP-major, each matrix column-major and written in
+ * full; NaN unless status is 0). S_i^{-1} is the covariance of b_i (sigma^2 is inside M):
+ * the p x p matrix generated beside b_i (Section 3); wald = b_ip^2 / (S_i^{-1})_pp. It is
+ * formed from the same p x p Cholesky factor as b_i. Errors as gwas_solve_block_device,
+ * GWAS_ERR_ARG for a NULL cov.
+ */
+gwas_status gwas_solve_block_cov_device(gwas_ctx* ctx, const int8_t* X, int64_t mb, double* b,
+                                        double* wald, uint8_t* status, double* cov);
+
+/*
  * 2-bit packed genotype calls (the paper streams FP64 genotypes; this packs four calls
  * per byte, so a block's host -> device copy is n/4 bytes per SNP instead of n). Xp
  * holds mb SNP columns of ceil(n/4) bytes each; individual k of a column sits in bits

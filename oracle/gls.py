@@ -376,3 +376,37 @@ def gls_multitrait(phi, hs, sigma2s, XL, Y, X, route: str = "hoisted"):
     wald = np.concatenate([o[1] for o in outs], axis=1)
     status = np.stack([o[2] for o in outs], axis=1)
     return b, wald, status
+
+
+def gls_cov(phi_or_M, h, sigma2, XL, X, is_phi: bool = True, route: str = "hoisted"):
+    """S_i^{-1} = (X_i^T M^{-1} X_i)^{-1} for every SNP (m x p x p, NaN unless status 0):
+    the covariance of b_i (sigma^2 is inside M), read as the p x p matrix the method
+    generates beside b_i (Section 3). ``hoisted``: S_i from Algorithm 1's Xbar_i, inverted
+    by its p x p Cholesky; ``explicit``: Eq. (1)'s X_i^T M^{-1} X_i with a Gauss-Jordan
+    M^{-1} and A_i^{-1} (small n only). Also returns the status (as ``gls``)."""
+    XL = np.asarray(XL, dtype=np.float64)
+    n = XL.shape[0]
+    Xg = np.asarray(X)
+    m, p = Xg.shape[1], XL.shape[1] + 1
+    out = np.full((m, p, p), np.nan)
+    if route == "explicit":
+        M = build_M(phi_or_M, h, sigma2) if is_phi else np.asarray(phi_or_M, dtype=np.float64)
+        Minv = gauss_jordan_inverse(M)
+        status = genotype_status(Xg)
+        for i in range(m):
+            if status[i] != STATUS_OK:
+                continue
+            Xi = np.hstack([XL, Xg[:, i:i + 1].astype(np.float64)])
+            try:
+                out[i] = gauss_jordan_inverse(Xi.T @ Minv @ Xi)
+            except np.linalg.LinAlgError:
+                status[i] = STATUS_SINGULAR
+        return out, status
+    L = factor(phi_or_M, h, sigma2, is_phi)
+    S, _, status = normal_equations_per_snp(L, XL, np.zeros((n, 1)), Xg)
+    eye = np.broadcast_to(np.eye(p), S.shape)
+    Sinv, _, ok = spd_solve(S, eye)
+    status = np.where(status != STATUS_OK, status, np.where(ok, STATUS_OK, STATUS_SINGULAR))
+    good = status == STATUS_OK
+    out[good] = Sinv[good]
+    return out, status.astype(np.uint8)

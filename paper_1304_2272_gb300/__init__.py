@@ -30,6 +30,7 @@ from .gwas import (  # noqa: F401
     gwas_reset_stats,
     gwas_solve_all,
     gwas_solve_block,
+    gwas_solve_block_cov_device,
     gwas_solve_block_device,
     gwas_solve_block_noalloc,
     gwas_solve_block_packed,

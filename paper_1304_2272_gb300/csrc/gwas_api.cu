@@ -169,7 +169,7 @@ void fold_timings(gwas_ctx* c, bool wait) {
 // The block compute on the compute stream: trsm + fused reductions, then the
 // per-SNP solve. X, b, wald, status are device pointers.
 gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, double* wald,
-                      uint8_t* status) {
+                      uint8_t* status, double* cov = nullptr) {
     Range range_("gwas block");
     CohortDev cv = cohort_view(c);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -197,11 +197,11 @@ gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, doubl
         c->timed.emplace_back(e0, e1);
     }
     if (c->mixed) {
-        CK(launch_snp_solve_mixed(cv, c->mx, c->bad, mb, b, wald, status, c->s_comp));
+        CK(launch_snp_solve_mixed(cv, c->mx, c->bad, mb, b, wald, status, c->s_comp, cov));
         c->stats.kernel_launches += 2;
     } else {
         CK(launch_snp_solve(cv, c->part, c->ldp, (int)ceil_div(c->n, T64), c->bad, mb, b, wald,
-                            status, c->s_comp));
+                            status, c->s_comp, cov));
         c->stats.kernel_launches += 1;
     }
     c->stats.kernel_launches += 2;
@@ -592,6 +592,15 @@ gwas_status gwas_solve_block_device(gwas_ctx* c, const int8_t* X, int64_t mb, do
     if (st != GWAS_OK) return st;
     DeviceGuard g(c->device);
     return run_block(c, X, mb, b, wald, status);
+}
+
+gwas_status gwas_solve_block_cov_device(gwas_ctx* c, const int8_t* X, int64_t mb, double* b,
+                                        double* wald, uint8_t* status, double* cov) {
+    gwas_status st = check_block_args(c, X, mb, b, status);
+    if (st != GWAS_OK) return st;
+    if (!cov) return fail(c, GWAS_ERR_ARG, "gwas_solve_block_cov_device: NULL cov");
+    DeviceGuard g(c->device);
+    return run_block(c, X, mb, b, wald, status, cov);
 }
 
 gwas_status gwas_solve_all(gwas_ctx* c, const int8_t* X, int64_t m, double* b, double* wald,

@@ -82,10 +82,10 @@ cudaError_t launch_reduce_fp64(const CohortDev& c, double* part, int64_t ldp, in
 
 // Reduces the row-tile partials (as launch_reduce_fp64: the totals replace row tile 0),
 // assembles S_i and bbar_i (Algorithm 1), solves by p x p Cholesky, writes b, wald (may
-// be null), status.
+// be null), status, and cov (may be null: mb x p x p, S_i^{-1} of every SNP).
 cudaError_t launch_snp_solve(const CohortDev& c, double* part, int64_t ldp, int n_tiles,
                              const uint8_t* bad, int64_t mb, double* b, double* wald,
-                             uint8_t* status, cudaStream_t s);
+                             uint8_t* status, cudaStream_t s, double* cov = nullptr);
 
 // ---- mixed-precision hot path (block_mixed.cu) ----------------------------------
 
@@ -163,7 +163,7 @@ cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaS
 // p x p solves from the mixed partial layout.
 cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const uint8_t* bad,
                                    int64_t mb, double* b, double* wald, uint8_t* status,
-                                   cudaStream_t s);
+                                   cudaStream_t s, double* cov = nullptr);
 
 // Batched cohorts (one CTA per 128-SNP tile, tile height rows_single(S)).
 int mixed_stage_count(const MixedDev& m);

@@ -71,7 +71,8 @@ template <int P, class Red>
 __device__ __forceinline__ void solve_snp(const CohortDev& c, const Red& red,
                                           const uint8_t* __restrict__ bad, int64_t i,
                                           double* __restrict__ b, double* __restrict__ wald,
-                                          uint8_t* __restrict__ status) {
+                                          uint8_t* __restrict__ status,
+                                          double* __restrict__ cov = nullptr) {
     constexpr int PM = P > 0 ? P : MAX_P;
     const int p = P > 0 ? P : c.q + 1;
     const int q = p - 1, t = c.t;
@@ -129,6 +130,34 @@ __device__ __forceinline__ void solve_snp(const CohortDev& c, const Red& red,
         if (wald) wald[i * t + j] = st ? nanv : z[p - 1] * z[p - 1] * cpp2;
     }
     status[i] = st;
+    if (cov) {
+        // S_i^{-1} = C^{-T} C^{-1} (the covariance of b_i; M carries sigma^2): G = C^{-1}
+        // column by column, then the symmetric product, written in full (column-major)
+        double G[PM][PM];
+#pragma unroll
+        for (int cc = 0; cc < p; ++cc) {
+#pragma unroll
+            for (int r = 0; r < p; ++r) G[r][cc] = 0.0;
+            G[cc][cc] = rc[cc];
+#pragma unroll
+            for (int r = cc + 1; r < p; ++r) {
+                double acc = 0.0;
+#pragma unroll
+                for (int k = cc; k < r; ++k) acc = fma(C[r][k], G[k][cc], acc);
+                G[r][cc] = -acc * rc[r];
+            }
+        }
+        double* co = cov + i * p * p;
+#pragma unroll
+        for (int a2 = 0; a2 < p; ++a2)
+#pragma unroll
+            for (int b2 = 0; b2 < p; ++b2) {
+                double acc = 0.0;
+#pragma unroll
+                for (int k = 0; k < p; ++k) acc = fma(G[k][a2], G[k][b2], acc);
+                co[a2 + b2 * p] = st ? nanv : acc;
+            }
+    }
 }
 
 // Adds the row-tile partials of every reduction value and writes the total over the first
@@ -195,22 +224,23 @@ k_reduce_partials_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n
 template <int P, class Red>
 __global__ void __launch_bounds__(128)
 k_snp_solve(CohortDev c, Red red, const uint8_t* __restrict__ bad, int64_t mb,
-            double* __restrict__ b, double* __restrict__ wald, uint8_t* __restrict__ status) {
+            double* __restrict__ b, double* __restrict__ wald, uint8_t* __restrict__ status,
+            double* __restrict__ cov) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= mb) return;
-    solve_snp<P>(c, red, bad, i, b, wald, status);
+    solve_snp<P>(c, red, bad, i, b, wald, status, cov);
 }
 
 // One thread per SNP; p = 2, 3, 4 get their own unrolled kernels.
 template <class Red>
 cudaError_t launch_solve(const CohortDev& c, const Red& red, const uint8_t* bad, int64_t mb,
-                         double* b, double* wald, uint8_t* status, cudaStream_t s) {
+                         double* b, double* wald, uint8_t* status, double* cov, cudaStream_t s) {
     const unsigned grid = (unsigned)ceil_div(mb, 128);
     switch (c.q + 1) {
-        case 2: k_snp_solve<2><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status); break;
-        case 3: k_snp_solve<3><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status); break;
-        case 4: k_snp_solve<4><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status); break;
-        default: k_snp_solve<0><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status); break;
+        case 2: k_snp_solve<2><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status, cov); break;
+        case 3: k_snp_solve<3><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status, cov); break;
+        case 4: k_snp_solve<4><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status, cov); break;
+        default: k_snp_solve<0><<<grid, 128, 0, s>>>(c, red, bad, mb, b, wald, status, cov); break;
     }
     return cudaGetLastError();
 }
@@ -248,11 +278,11 @@ cudaError_t launch_reduce_fp64(const CohortDev& c, double* part, int64_t ldp, in
 
 cudaError_t launch_snp_solve(const CohortDev& c, double* part, int64_t ldp, int n_tiles,
                              const uint8_t* bad, int64_t mb, double* b, double* wald,
-                             uint8_t* status, cudaStream_t s) {
+                             uint8_t* status, cudaStream_t s, double* cov) {
     if (mb <= 0) return cudaSuccess;
     cudaError_t e = launch_reduce_fp64(c, part, ldp, n_tiles, mb, s);
     if (e != cudaSuccess) return e;
-    return launch_solve(c, RedFp64{part, ldp, 1, n_red(c)}, bad, mb, b, wald, status, s);
+    return launch_solve(c, RedFp64{part, ldp, 1, n_red(c)}, bad, mb, b, wald, status, cov, s);
 }
 
 cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_snps, int p,
@@ -280,14 +310,14 @@ cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_s
 
 cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const uint8_t* bad,
                                    int64_t mb, double* b, double* wald, uint8_t* status,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, double* cov) {
     if (mb <= 0) return cudaSuccess;
     const int q = c.q;
     cudaError_t e = reduce_partials(RedMixed{m.sq_part, m.lin, m.ldp, m.n_rt, q, m.lin_tiles(), m.R_e},
                                     n_red(c), mb, s);
     if (e != cudaSuccess) return e;
     return launch_solve(c, RedMixed{m.sq_part, m.lin, m.ldp, 1, q, 1, m.R_e}, bad, mb, b, wald,
-                        status, s);
+                        status, cov, s);
 }
 
 }  // namespace gwas

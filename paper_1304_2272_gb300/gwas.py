@@ -87,6 +87,7 @@ SIGNATURES = {
     "gwas_factor": (_int, [_ctx_p, _vp, _int, _dbl, _dbl, _vp, _vp]),
     "gwas_solve_block": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp]),
     "gwas_solve_block_device": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp]),
+    "gwas_solve_block_cov_device": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp, _vp]),
     "gwas_solve_block_packed": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp, _vp]),
     "gwas_solve_block_packed_device": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp, _vp]),
     "gwas_solve_all": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp]),
@@ -264,6 +265,14 @@ def gwas_solve_block_packed_device(ctx, Xp, mb: int, code, b, wald, status) -> N
     _outs_dev(b, wald, status)
     _check(ctx, load().gwas_solve_block_packed_device(ctx, _addr(Xp), int(mb), _code(code),
                                                       _addr(b), _addr(wald), _addr(status)))
+
+
+def gwas_solve_block_cov_device(ctx, X, mb: int, b, wald, status, cov) -> None:
+    _require_dev(X, np.int8, "X")
+    _outs_dev(b, wald, status)
+    _require_dev(cov, np.float64, "cov")
+    _check(ctx, load().gwas_solve_block_cov_device(ctx, _addr(X), int(mb), _addr(b), _addr(wald),
+                                                   _addr(status), _addr(cov)))
 
 
 def gwas_solve_all(ctx, X, m: int, b, wald, status) -> None:

@@ -233,6 +233,45 @@ def test_multitrait_trait_order():
     assert np.array_equal(bp, b[:, perm]) and np.array_equal(wp, w[:, perm])
 
 
+# ------------------------------------- the p x p matrix S_i^-1 (Section 3) ---
+def test_cov_matches_exact_rational_inverse():
+    """S_i^-1 = (X_i^T M^-1 X_i)^-1 of both oracle routes against exact rationals."""
+    rng = np.random.default_rng(8)
+    n, q = 7, 2
+    A = rng.integers(-2, 3, size=(n, n))
+    M = (A @ A.T + 2 * np.eye(n, dtype=int)).astype(int)
+    XL = np.ones((n, q), dtype=int)
+    XL[:, 1] = rng.integers(-3, 4, size=n)
+    X = rng.integers(0, 3, size=(n, 4)).astype(np.int8)
+    Minv = E.inverse(M.tolist())
+    for route in ("hoisted", "explicit"):
+        cov, st = G.gls_cov(M.astype(float), None, None, XL.astype(float), X, is_phi=False,
+                            route=route)
+        assert np.all(st == 0)
+        for i in range(X.shape[1]):
+            Xi = np.hstack([XL, X[:, i:i + 1]]).astype(int).tolist()
+            XiT = [list(r) for r in zip(*Xi)]
+            Ai = E.matmul(E.matmul(XiT, Minv), Xi)
+            ref = np.array([[float(v) for v in row] for row in E.inverse(Ai)])
+            assert np.max(np.abs(cov[i] - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+def test_cov_is_consistent_with_wald_and_spd():
+    c, X = small_case(15, 120, 20, t=2)
+    X = X.copy(order="F")
+    X[:, 4] = 1
+    cov, st = G.gls_cov(c.phi, c.h, c.sigma2, c.XL, X)
+    b, w, s = G.gls(c.phi, c.h, c.sigma2, c.XL, c.Y, X)
+    np.testing.assert_array_equal(st, s)
+    ok = s == 0
+    assert st[4] == 1 and np.all(np.isnan(cov[4]))
+    # Wald = b_p^2 / (S^-1)_pp for every phenotype (the oracle's Wald comes from C_pp^2)
+    pp = cov[ok][:, -1, -1]
+    assert np.max(np.abs(b[ok][:, :, -1] ** 2 / pp[:, None] - w[ok]) / np.maximum(w[ok], 1)) <= 1e-10
+    assert np.max(np.abs(cov[ok] - np.transpose(cov[ok], (0, 2, 1)))) <= 1e-12 * np.max(np.abs(cov[ok]))
+    assert np.all(np.linalg.eigvalsh(cov[ok]) > 0)
+
+
 # ------------------------------------------------------- degenerate SNPs -----
 def test_degenerate_and_bad_snps():
     c, X = small_case(12, 60, 6)

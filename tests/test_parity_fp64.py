@@ -218,3 +218,39 @@ def test_timing_over_many_blocks(gwas):
         st = e.stats()
     assert st["trsm_launches"] == 150 and st["blocks"] == 150 and st["trsm_ms"] > 0
     assert_parity(out, oracle(c, X))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
+def test_cov_output_matches_oracle(gwas, precision, tol):
+    """S_i^-1 (the p x p matrix beside b_i) against the oracle, NaN where status != 0."""
+    import torch
+    c = synth.make_cohort(91, 400, t=2, n_markers=300)
+    X = c.snps(300).copy(order="F")
+    X[:, 5] = 2
+    X[0, 6] = 5
+    mb, p = X.shape[1], 4
+    prec = gwas.GWAS_PREC_FP64 if precision == "fp64" else gwas.GWAS_PREC_MIXED
+    with gwas.GLS(c.n, p, 2, m_blk=512, precision=prec) as e:
+        e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
+        Xd = torch.from_numpy(np.ascontiguousarray(X.T)).cuda()
+        bd = torch.empty((mb, 2, p), dtype=torch.float64, device="cuda")
+        wd = torch.empty((mb, 2), dtype=torch.float64, device="cuda")
+        sd = torch.empty(mb, dtype=torch.uint8, device="cuda")
+        cd = torch.empty((mb, p, p), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        gwas.gwas_solve_block_cov_device(e.ctx, Xd, mb, bd, wd, sd, cd)
+        gwas.gwas_sync(e.ctx)
+        with pytest.raises(gwas.GwasError):
+            gwas.gwas_solve_block_cov_device(e.ctx, Xd, mb, bd, wd, sd, None)
+    cov = cd.cpu().numpy().transpose(0, 2, 1)      # each matrix column-major
+    st = sd.cpu().numpy()
+    ref, rs = G.gls_cov(c.phi, c.h, c.sigma2, c.XL, X)
+    np.testing.assert_array_equal(st, rs)
+    assert st[5] == 1 and st[6] == 2 and np.all(np.isnan(cov[st != 0]))
+    ok = rs == 0
+    scale = np.max(np.abs(ref[ok]), axis=(1, 2), keepdims=True)
+    assert np.max(np.abs(cov[ok] - ref[ok]) / scale) <= tol
+    # the Wald statistic is b_p^2 / (S^-1)_pp
+    w = wd.cpu().numpy()[ok]
+    b = bd.cpu().numpy()[ok]
+    assert np.max(np.abs(b[:, :, -1] ** 2 / cov[ok][:, -1, -1][:, None] - w) / np.maximum(w, 1)) <= 1e-9
