@@ -70,3 +70,17 @@ def test_device_arguments_are_checked_before_the_call():
     assert gwas._require_dev(None, gwas.np.int8, "X") is None
     assert gwas._require_dev(1234, gwas.np.int8, "X") == 1234
     del b
+
+
+def test_autotune_cache_roundtrip_on_the_host(tmp_path, monkeypatch):
+    """The tuning cache: one entry per (device, shape, precision, limbs, m_blk) key, written
+    atomically and read back; a read-only or corrupt cache never raises."""
+    from paper_1304_2272_gb300 import autotune
+    monkeypatch.setenv("GWAS_AUTOTUNE_CACHE", str(tmp_path / "c" / "tune.json"))
+    k1 = autotune.key_for(10000, 4, 1, 1, 3, 16384)
+    k2 = autotune.key_for(10000, 4, 1, 1, 5, 16384)
+    assert k1 != k2 and "n=10000" in k1 and "limbs=3" in k1
+    autotune._store({k1: {"tile_cfg": 8832, "m_blk": 16384}})
+    assert autotune._load()[k1]["tile_cfg"] == 8832
+    (tmp_path / "c" / "tune.json").write_text("{not json")
+    assert autotune._load() == {}
