@@ -168,13 +168,13 @@ def bf16_flops_per_snp(n: int, q: int, t: int, limbs: int) -> float:
 
 # DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the bench's own launch shape), valid only
-# while the kernel source is the one captured (first 16 hex digits of its sha256) and, for
+# while the kernel source is the one captured (code_sha of its file) and, for
 # the limb kernel, per L2 group size (captured with CTA pairs and fused rows; the traffic
 # depends on those, not on the pipeline depth).
 TRAFFIC = {
-    "k_block_fp64": {"file": "block_fp64.cu", "sha": "47c01bde2896f773", "n": 10000,
+    "k_block_fp64": {"file": "block_fp64.cu", "sha": "f12d054bee8830fb", "n": 10000,
                      "m_blk": 16384, "bytes": 2061468160 + 110667520},
-    "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "886cdd079efba4ca", "n": 10000,
+    "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "176da42a48ba3994", "n": 10000,
                          "m_blk": 16384, "single_cta": False, "no_fuse": False,
                          "bytes_by_group_mb": {40: 4036415744 + 81025792,
                                                80: 4554571520 + 79876352,
@@ -200,7 +200,6 @@ MIXED_TOL = {2: 1e-4, 3: 1e-6, 4: 1e-9, 5: 1e-10}
 
 
 def traffic_for(kernel: str, n: int, m_blk: int, tile_cfg=None):
-    import hashlib
     rec = TRAFFIC.get(kernel)
     if not rec or rec["n"] != n or rec["m_blk"] != m_blk:
         return None
@@ -212,11 +211,22 @@ def traffic_for(kernel: str, n: int, m_blk: int, tile_cfg=None):
         nbytes = rec["bytes_by_group_mb"].get(f["group_mb"])
     path = os.path.join(ROOT, "paper_1304_2272_gb300", "csrc", rec["file"])
     try:
-        with open(path, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        with open(path, encoding="utf-8") as f:
+            sha = code_sha(f.read())
     except OSError:
         return None
     return nbytes if sha == rec["sha"] else None
+
+
+def code_sha(src: str) -> str:
+    """First 16 hex digits of the sha256 of a CUDA source with its comments and blank
+    space removed: edits to comments keep a traffic record, any code change drops it."""
+    import hashlib
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    src = re.sub(r"\s+", " ", src).strip()
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def h2d_peak_gbs(pinned, dev) -> float:

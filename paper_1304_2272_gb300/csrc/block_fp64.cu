@@ -6,7 +6,7 @@
 // lower-triangular matrix product W X_blk with no dependency between row tiles:
 // every (row tile, SNP tile) pair is an independent unit, Xbar never reaches global
 // memory, and the reductions are taken from the tile while it sits in registers.
-// Each unit writes its row-tile partial sums; k_snp_solve adds them in a fixed
+// Each unit writes its row-tile partial sums; k_reduce_partials adds them in a fixed
 // order (no float atomics, so results are reproducible run to run).
 #include <algorithm>
 
@@ -16,8 +16,9 @@
 namespace gwas {
 
 // One CTA = one 64-row x 64-SNP unit; 256 threads, 4 rows x 4 SNPs per thread.
-// Thread (tx, ty): rows tx + 16 a, SNPs ty + 16 b. Units are ordered heaviest row
-// tile first (a row tile r needs k < (r+1)*64) so the tail of the grid is short.
+// Thread (tx, ty): rows tx + 16 a, SNPs ty + 16 b. Within an L2 group of SNP tiles the
+// units are ordered heaviest row tile first (a row tile r needs k < (r+1)*64) so the
+// tail of the grid is short.
 __device__ __forceinline__ void block_fp64_unit(const CohortDev& c, const int8_t* __restrict__ X,
                                                 int64_t ldx, int64_t mb, int n_rt, int rt, int ct,
                                                 double* __restrict__ part, int64_t ldp,
