@@ -84,3 +84,11 @@ def test_autotune_cache_roundtrip_on_the_host(tmp_path, monkeypatch):
     assert autotune._load()[k1]["tile_cfg"] == 8832
     (tmp_path / "c" / "tune.json").write_text("{not json")
     assert autotune._load() == {}
+
+
+def test_code_sha_ignores_comments_only():
+    src = "// a kernel\n__global__ void k(int* x) {  /* body */\n    x[0] = 1;  // one\n}\n"
+    same = "// another comment\n__global__ void k(int* x) {\n  x[0] = 1;\n}\n"
+    other = "__global__ void k(int* x) { x[0] = 2; }"
+    assert bench.code_sha(src) == bench.code_sha(same)
+    assert bench.code_sha(src) != bench.code_sha(other)
