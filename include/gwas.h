@@ -28,6 +28,16 @@
  *   - Every call returns a gwas_status; nothing aborts or throws across the ABI.
  *     gwas_last_error() describes the most recent failure of a context.
  *   - A context is bound to one CUDA device and is not thread-safe.
+ *
+ * Typical use (host buffers; error checks omitted):
+ *
+ *     gwas_opts o;  gwas_default_opts(&o);      // o.precision = GWAS_PREC_MIXED, ...
+ *     gwas_ctx* ctx;  gwas_init(n, p, t, &o, &ctx);
+ *     gwas_factor(ctx, Phi, 1, h, sigma2, XL, Y);    // once per cohort
+ *     for (each block of mb <= o.m_blk SNPs)         // page-locked X for overlap
+ *         gwas_solve_block(ctx, X_blk, mb, b_blk, wald_blk, status_blk);
+ *     gwas_sync(ctx, -1);                            // all outputs are now in place
+ *     gwas_finalize(ctx);
  */
 #ifndef GWAS_GB300_H
 #define GWAS_GB300_H
