@@ -6,98 +6,9 @@
 // "compute block k" and "copy b of block k-1 out", which is the paper's
 // load_start/load_wait/store_start/store_wait pattern with the disk replaced by
 // pinned host memory and the second memory region by the second device slot.
-#include <algorithm>
-#include <chrono>
-#include <cmath>
-#include <cstdio>
-#include <cstring>
-#include <string>
-#include <thread>
-#include <vector>
+#include "api_internal.h"
 
-#include <nvtx3/nvToolsExt.h>
-
-#include "../../include/gwas.h"
-#include "common.cuh"
-#include "kernels.h"
-
-using namespace gwas;
-
-namespace {
-// NVTX range over one API call (named in profiler timelines; free without a tool).
-struct Range {
-    explicit Range(const char* name) { nvtxRangePushA(name); }
-    ~Range() { nvtxRangePop(); }
-};
-}  // namespace
-
-struct gwas_ctx {
-    gwas_opts opts{};
-    int device = 0;
-    int64_t n = 0;
-    int p = 0, q = 0, t = 0;
-    int64_t ld = 0;               // leading dimension of L and W
-    double* L = nullptr;          // n x n: M, then its Cholesky factor
-    double* W = nullptr;          // n x n: L^{-1}
-    double* Dinv = nullptr;       // diagonal 64 x 64 inverses
-    double* XLbar = nullptr;      // n x q
-    double* Ybar = nullptr;       // n x t
-    double* S_TL = nullptr;       // q x q
-    double* bbar_T = nullptr;     // q x t
-    int* d_info = nullptr;
-    // block pipeline
-    int8_t* Xslot[2] = {nullptr, nullptr};
-    double* bslot[2] = {nullptr, nullptr};
-    double* wslot[2] = {nullptr, nullptr};
-    uint8_t* sslot[2] = {nullptr, nullptr};
-    uint8_t* Pslot[2] = {nullptr, nullptr};  // 2-bit packed host blocks (first use)
-    int8_t* Xunpack = nullptr;    // unpacked dosages of gwas_solve_block_packed_device
-    double* part = nullptr;       // row-tile partial sums
-    int64_t ldp = 0;
-    uint8_t* bad = nullptr;
-    // mixed-precision path
-    bool mixed = false;
-    MixedDev mx;
-    double* Z = nullptr;          // n x (q + t): L^{-T} [Xbar_L | Ybar] = M^{-1} [X_L | Y]
-    // REML and db/dh (allocated on first use)
-    double* Phi = nullptr;        // full Phi, ld
-    double* Minv = nullptr;       // M^{-1} = L^{-T} L^{-1}, ld (formed when db/dh needs it)
-    bool minv_ready = false;      // Minv holds M^{-1} of the current factor
-    double* XLY = nullptr;        // [X_L | Y] (n x (q+t)) as given to the last gwas_factor
-    double* part2 = nullptr;      // adjoint partials, FP64 partial layout
-    double* small = nullptr;      // G1, G2, PhiZ and scalars
-    bool grad_ready = false;
-    double grad_h = 0.0, grad_s2 = 0.0;
-    bool ones_singular = false;   // the all-ones SNP is collinear with X_L (mixed path)
-    int num_sms = 0;
-    cudaStream_t s_comp = nullptr, s_h2d = nullptr, s_d2h = nullptr;
-    cudaEvent_t ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
-    int slot = 0;
-    bool factored = false;
-    std::string err;
-    int64_t err_index = -1;
-    gwas_stats stats{};
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed;  // pending trsm timings
-    std::vector<cudaEvent_t> ev_pool;
-    // host-path blocks: number submitted, and the completion events (D2H done) of those
-    // from index done_base on that are not yet known to be complete
-    int64_t host_blocks = 0, done_base = 0;
-    std::vector<cudaEvent_t> done_ev;
-};
-
-namespace {
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
+namespace gwas_api {
 gwas_status fail(gwas_ctx* c, gwas_status st, const std::string& msg) {
     if (c) c->err = msg;
     return st;
@@ -109,19 +20,6 @@ gwas_status cuda_fail(gwas_ctx* c, cudaError_t e, const char* where) {
     return fail(c, e == cudaErrorMemoryAllocation ? GWAS_ERR_OOM : GWAS_ERR_CUDA, m);
 }
 
-#define CK(call)                                              \
-    do {                                                      \
-        cudaError_t e_ = (call);                              \
-        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
-    } while (0)
-
-template <typename T>
-cudaError_t dmalloc(T** p, size_t count) {
-    const cudaError_t e = cudaMalloc((void**)p, count * sizeof(T) + 256);
-    if (e != cudaSuccess) *p = nullptr;  // a failed allocation leaves nothing to free or use
-    return e;
-}
-
 CohortDev cohort_view(const gwas_ctx* c) {
     CohortDev v;
     v.n = c->n; v.q = c->q; v.t = c->t;
@@ -130,14 +28,6 @@ CohortDev cohort_view(const gwas_ctx* c) {
     v.ones_singular = c->ones_singular;
     return v;
 }
-
-// Owns a temporary device allocation for the duration of one call.
-struct TmpDev {
-    void* p = nullptr;
-    ~TmpDev() {
-        if (p) cudaFree(p);
-    }
-};
 
 cudaEvent_t pooled_event(gwas_ctx* c) {
     if (!c->ev_pool.empty()) {
@@ -169,7 +59,7 @@ void fold_timings(gwas_ctx* c, bool wait) {
 // The block compute on the compute stream: trsm + fused reductions, then the
 // per-SNP solve. X, b, wald, status are device pointers.
 gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, double* wald,
-                      uint8_t* status, double* cov = nullptr) {
+                      uint8_t* status, double* cov) {
     Range range_("gwas block");
     CohortDev cv = cohort_view(c);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -264,8 +154,18 @@ void free_all(gwas_ctx* c) {
     if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
 }
 
-}  // namespace
+gwas_status check_block_args(gwas_ctx* c, const int8_t* X, int64_t mb, double* b,
+                                    uint8_t* status) {
+    if (!c) return GWAS_ERR_ARG;
+    if (!c->factored) return fail(c, GWAS_ERR_STATE, "solve before a successful gwas_factor");
+    if (!X || !b || !status) return fail(c, GWAS_ERR_ARG, "solve: NULL pointer");
+    if (mb < 1 || mb > c->opts.m_blk) return fail(c, GWAS_ERR_ARG, "solve: need 1 <= mb <= m_blk");
+    return GWAS_OK;
+}
 
+}  // namespace gwas_api
+
+using namespace gwas_api;
 extern "C" {
 
 void gwas_default_opts(gwas_opts* o) {
@@ -477,15 +377,6 @@ gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double 
         return fail(c, GWAS_ERR_NOT_SPD, buf);
     }
     c->factored = true;
-    return GWAS_OK;
-}
-
-static gwas_status check_block_args(gwas_ctx* c, const int8_t* X, int64_t mb, double* b,
-                                    uint8_t* status) {
-    if (!c) return GWAS_ERR_ARG;
-    if (!c->factored) return fail(c, GWAS_ERR_STATE, "solve before a successful gwas_factor");
-    if (!X || !b || !status) return fail(c, GWAS_ERR_ARG, "solve: NULL pointer");
-    if (mb < 1 || mb > c->opts.m_blk) return fail(c, GWAS_ERR_ARG, "solve: need 1 <= mb <= m_blk");
     return GWAS_OK;
 }
 
@@ -728,166 +619,6 @@ void* gwas_stream(const gwas_ctx* c) { return c ? (void*)c->s_comp : nullptr; }
 }  // extern "C"
 
 // ============================================================================
-// REML log-likelihood, its gradient, and db_i/dh.
-// ============================================================================
-namespace {
-
-// M^-1 = W^T W (W = L^-1 lower triangular) into c->Minv.
-cudaError_t form_minv(gwas_ctx* c, cudaStream_t s) {
-    const int64_t n = c->n, ld = c->ld;
-    cudaError_t e;
-    if (!c->Minv && (e = dmalloc(&c->Minv, (size_t)ld * ld)) != cudaSuccess) return e;
-    GemmF64 mi;
-    mi.M = n; mi.N = n; mi.K = n; mi.A = c->W; mi.lda = ld; mi.transA = true; mi.a_upper = true;
-    mi.B = c->W; mi.ldb = ld; mi.b_lower = true; mi.C = c->Minv; mi.ldc = ld;
-    if ((e = gemm_f64(mi, s)) != cudaSuccess) return e;
-    c->minv_ready = true;
-    return cudaSuccess;
-}
-
-// Layout of c->small: G1 and G2 ((q+t)^2 each), PhiZ (n x (q+t)), then scalars.
-struct SmallLayout {
-    int64_t nz, g1, g2, phiz, yy, logdet, frob, fpart, out, total;
-    explicit SmallLayout(const gwas_ctx* c) {
-        nz = c->q + c->t;
-        g1 = 0;
-        g2 = g1 + nz * nz;
-        phiz = g2 + nz * nz;
-        yy = phiz + c->n * nz;
-        logdet = yy + 1;
-        frob = logdet + 1;
-        fpart = frob + 2;
-        out = fpart + 2 * ceil_div(c->n, 256);
-        total = out + 8;
-    }
-};
-
-}  // namespace
-
-extern "C" gwas_status gwas_reml(gwas_ctx* c, const double* Phi, double h, double sigma2,
-                                 const double* XL, const double* Y, int pheno, int profile,
-                                 gwas_reml_result* out) {
-    Range range_("gwas_reml");
-    if (!c || !out) return GWAS_ERR_ARG;
-    if (!Phi || !XL || !Y) return fail(c, GWAS_ERR_ARG, "gwas_reml: NULL input");
-    if (pheno < 0 || pheno >= c->t) return fail(c, GWAS_ERR_ARG, "gwas_reml: phenotype out of range");
-    gwas_status st = gwas_factor(c, Phi, 1, h, sigma2, XL, Y);
-    if (st != GWAS_OK) return st;
-    DeviceGuard g(c->device);
-    const int64_t n = c->n, ld = c->ld, nz = c->q + c->t;
-    cudaStream_t s = c->s_comp;
-    const SmallLayout sl(c);
-    // For h >= 1e-2 Phi enters only through M: Phi Z and <M^-1, Phi> follow from M, Z and
-    // tr M^-1 = |L^-1|_F^2, so neither Phi nor M^-1 (n^3/3 flops) is formed; below it the
-    // identities would divide a cancellation by h, and Phi and M^-1 are used directly.
-    const bool identity = h >= 1e-2;
-    if (!c->Z) CK(dmalloc(&c->Z, (size_t)n * nz));
-    if (!c->small) CK(dmalloc(&c->small, (size_t)sl.total));
-    double* sm = c->small;
-    if (!identity) {
-        if (!c->Phi) CK(dmalloc(&c->Phi, (size_t)ld * ld));
-        if (!c->Minv) CK(dmalloc(&c->Minv, (size_t)ld * ld));
-        // the full Phi (the Frobenius product reads both triangles)
-        CK(cudaMemcpy2DAsync(c->Phi, ld * sizeof(double), Phi, n * sizeof(double),
-                             n * sizeof(double), n, cudaMemcpyDefault, s));
-        // M^-1 = W^T W (W = L^-1 lower triangular)
-        CK(form_minv(c, s));
-    }
-    if (!c->mixed) {  // the mixed factor already formed Z
-        GemmF64 z;
-        z.M = n; z.N = c->q; z.K = n; z.A = c->W; z.lda = ld; z.transA = true; z.a_upper = true;
-        z.B = c->XLbar; z.ldb = n; z.C = c->Z; z.ldc = n;
-        CK(gemm_f64(z, s));
-        GemmF64 zy = z;
-        zy.N = c->t; zy.B = c->Ybar; zy.C = c->Z + (size_t)n * c->q;
-        CK(gemm_f64(zy, s));
-    }
-    // G1 = Z^T Z; G2 = Z^T Phi Z (identity: Z^T [X_L | Y]); |ybar_j|^2
-    GemmF64 g1;
-    g1.M = nz; g1.N = nz; g1.K = n; g1.A = c->Z; g1.lda = n; g1.transA = true; g1.B = c->Z;
-    g1.ldb = n; g1.C = sm + sl.g1; g1.ldc = nz;
-    CK(gemm_f64(g1, s));
-    GemmF64 g2 = g1;
-    g2.C = sm + sl.g2;
-    if (identity) {
-        g2.B = c->XLY;
-    } else {
-        GemmF64 pz;
-        pz.M = n; pz.N = nz; pz.K = n; pz.A = c->Phi; pz.lda = ld; pz.B = c->Z; pz.ldb = n;
-        pz.C = sm + sl.phiz; pz.ldc = n;
-        CK(gemm_f64(pz, s));
-        g2.B = sm + sl.phiz;
-    }
-    CK(gemm_f64(g2, s));
-    GemmF64 yy;
-    yy.M = 1; yy.N = 1; yy.K = n; yy.A = c->Ybar + (size_t)n * pheno; yy.lda = n; yy.transA = true;
-    yy.B = c->Ybar + (size_t)n * pheno; yy.ldb = n; yy.C = sm + sl.yy; yy.ldc = 1;
-    CK(gemm_f64(yy, s));
-    CK(launch_logdiag(c->L, ld, n, sm + sl.logdet, s));
-    if (identity)
-        CK(launch_frob_trace(c->W, c->W, ld, n, sm + sl.fpart, sm + sl.frob, s));
-    else
-        CK(launch_frob_trace(c->Minv, c->Phi, ld, n, sm + sl.fpart, sm + sl.frob, s));
-    RemlDev r;
-    r.n = n; r.q = c->q; r.t = c->t; r.j = pheno; r.h = h; r.sigma2 = sigma2;
-    r.profile = profile ? 1 : 0;
-    r.S_TL = c->S_TL; r.bbar_T = c->bbar_T; r.G1 = sm + sl.g1; r.G2 = sm + sl.g2;
-    r.yy = sm + sl.yy; r.logdet_M = sm + sl.logdet; r.frob = sm + sl.frob; r.out = sm + sl.out;
-    r.identity = identity ? 1 : 0;
-    CK(launch_reml_assemble(r, s));
-    double host[8];
-    CK(cudaMemcpyAsync(host, sm + sl.out, sizeof host, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    out->loglik = host[0];
-    out->dl_dh = host[1];
-    out->dl_dsigma2 = host[2];
-    out->sigma2_hat = host[3];
-    out->yPy = host[4];
-    out->logdet_M = host[5];
-    out->logdet_A = host[6];
-    out->sigma2 = host[7];
-    c->grad_ready = true;
-    c->grad_h = h;
-    c->grad_s2 = sigma2;
-    if (!std::isfinite(host[0])) return fail(c, GWAS_ERR_NOT_SPD, "gwas_reml: X_L^T M^-1 X_L is not SPD");
-    return GWAS_OK;
-}
-
-extern "C" gwas_status gwas_solve_block_grad_device(gwas_ctx* c, const int8_t* X, int64_t mb,
-                                                    double* b, double* wald, uint8_t* status,
-                                                    double* dbdh) {
-    gwas_status st = check_block_args(c, X, mb, b, status);
-    if (st != GWAS_OK) return st;
-    if (!dbdh) return fail(c, GWAS_ERR_ARG, "gwas_solve_block_grad_device: NULL dbdh");
-    if (c->mixed) return fail(c, GWAS_ERR_UNSUPPORTED, "db/dh is built for GWAS_PREC_FP64 contexts");
-    if (!c->grad_ready) return fail(c, GWAS_ERR_STATE, "db/dh needs a gwas_reml at the current h");
-    if (!(c->grad_h > 0.0)) return fail(c, GWAS_ERR_ARG, "db/dh needs h > 0");
-    DeviceGuard g(c->device);
-    const int64_t n = c->n;
-    const int n_tiles = (int)ceil_div(n, T64);
-    if (!c->part2) CK(dmalloc(&c->part2, (size_t)n_tiles * (c->q + 1 + c->t) * c->ldp));
-    if (!c->minv_ready) {  // gwas_reml did not need M^-1 (h >= 1e-2): form it once
-        CK(form_minv(c, c->s_comp));
-        c->stats.kernel_launches += 1;
-    }
-    // forward: b_i, Wald, status, and the partials of S_i and bbar_i
-    if ((st = run_block(c, X, mb, b, wald, status)) != GWAS_OK) return st;
-    // adjoint: the same kernel with M^-1 (dense) and Z = M^-1 [X_L | Y]
-    CohortDev adj = cohort_view(c);
-    adj.W = c->Minv;
-    adj.ldw = c->ld;
-    adj.dense = true;
-    adj.XLbar = c->Z;
-    adj.Ybar = c->Z + (size_t)n * c->q;
-    CK(launch_block_fp64(adj, X, n, mb, c->part2, c->ldp, c->bad, c->s_comp));
-    const SmallLayout sl(c);
-    CK(launch_dbdh(cohort_view(c), c->part, c->part2, c->ldp, n_tiles, c->small + sl.g1,
-                   c->grad_s2 / c->grad_h, c->bad, mb, dbdh, c->s_comp));
-    c->stats.kernel_launches += 3;
-    return GWAS_OK;
-}
-
-// ============================================================================
 // Tile configuration and the autotuner.
 // ============================================================================
 extern "C" {
@@ -1046,342 +777,5 @@ gwas_status gwas_autotune(gwas_ctx* c, const int8_t* X, int64_t mb_max, int reps
     out->candidates = tried;
     return GWAS_OK;
 }
-
-}  // extern "C"
-
-// ============================================================================
-// Batches of cohorts: each cohort keeps its own context (factor, L^{-1}, limbs,
-// buffers); a batched solve is ONE grouped launch of the block kernel over every
-// cohort's (row tile, SNP tile) units, optionally captured in a CUDA graph.
-// ============================================================================
-struct gwas_batch {
-    gwas_opts opts{};
-    int device = 0;
-    int n_cohorts = 0;
-    int p = 0, q = 0, t = 0;
-    bool mixed = false;
-    std::vector<gwas_ctx*> ctx;
-    cudaStream_t s = nullptr;
-    BatchJob* d_jobs = nullptr;
-    CohortMx* d_tab = nullptr;
-    CUtensorMap* d_maps = nullptr;
-    int* d_err = nullptr;
-    // configuration the device tables (and the graph) were built for
-    std::vector<uintptr_t> key;
-    int64_t total_snps = 0, units_fp64 = 0, units_mx = 0;
-    int stages = 0;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    std::string err;
-    gwas_stats stats{};
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timed;
-};
-
-namespace {
-
-gwas_status bfail(gwas_batch* b, gwas_status st, const std::string& msg) {
-    if (b) b->err = msg;
-    return st;
-}
-
-#define CKB(call)                                                                       \
-    do {                                                                                \
-        cudaError_t e_ = (call);                                                        \
-        if (e_ != cudaSuccess) {                                                        \
-            cudaGetLastError();                                                         \
-            return bfail(b, e_ == cudaErrorMemoryAllocation ? GWAS_ERR_OOM : GWAS_ERR_CUDA, \
-                         std::string(#call) + ": " + cudaGetErrorString(e_));           \
-        }                                                                               \
-    } while (0)
-
-void batch_free(gwas_batch* b) {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    if (b->graph) cudaGraphDestroy(b->graph);
-    for (auto& pr : b->timed) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
-    cudaFree(b->d_jobs); cudaFree(b->d_tab); cudaFree(b->d_maps); cudaFree(b->d_err);
-    if (b->s) cudaStreamDestroy(b->s);
-    for (auto* c : b->ctx) gwas_finalize(c);
-}
-
-// As fold_timings, for a batch (its events are created per solve and destroyed here).
-void batch_fold_timings(gwas_batch* b, bool wait) {
-    size_t k = 0;
-    for (; k < b->timed.size(); ++k) {
-        auto& pr = b->timed[k];
-        if (!wait && cudaEventQuery(pr.second) != cudaSuccess) break;
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) b->stats.trsm_ms += ms;
-        cudaEventDestroy(pr.first);
-        cudaEventDestroy(pr.second);
-    }
-    b->timed.erase(b->timed.begin(), b->timed.begin() + (std::ptrdiff_t)k);
-}
-
-// Enqueue the batched solve on the batch stream (device tables already current).
-gwas_status batch_enqueue(gwas_batch* b) {
-    const int nc = b->n_cohorts;
-    if (b->mixed) {
-        CKB(launch_geno_bf16_batch(b->d_jobs, nc, b->total_snps, b->s));
-        CKB(launch_block_mixed_batch(b->d_tab, b->d_maps, nc, b->units_mx, b->ctx[0]->mx,
-                                     b->stages, b->d_err, b->ctx[0]->num_sms, b->s));
-        CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, b->p, b->q + 1 + b->t, true, b->s));
-    } else {
-        CKB(launch_block_fp64_batch(b->d_jobs, nc, b->units_fp64, b->s));
-        CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, b->p, b->q + 1 + b->t, false, b->s));
-    }
-    return GWAS_OK;
-}
-
-}  // namespace
-
-extern "C" {
-
-gwas_status gwas_batch_init(int n_cohorts, const int64_t* n, int p, int t, const gwas_opts* opts,
-                            gwas_batch** out) {
-    if (!out) return GWAS_ERR_ARG;
-    *out = nullptr;
-    if (n_cohorts < 1 || !n) return GWAS_ERR_ARG;
-    gwas_opts o;
-    gwas_default_opts(&o);
-    if (opts) o = *opts;
-    gwas_batch* b = new gwas_batch();
-    b->opts = o;
-    b->device = o.device;
-    b->n_cohorts = n_cohorts;
-    b->p = p; b->q = p - 1; b->t = t;
-    b->mixed = (o.precision == GWAS_PREC_MIXED);
-    gwas_opts oc = o;
-    if (b->mixed) oc.tile_cfg = (o.tile_cfg < 0 ? 0 : (o.tile_cfg & ~(3 << 12))) | (1 << 12);
-    for (int c = 0; c < n_cohorts; ++c) {
-        gwas_ctx* cx = nullptr;
-        const gwas_status st = gwas_init(n[c], p, t, &oc, &cx);
-        if (st != GWAS_OK) {
-            DeviceGuard g(b->device);
-            batch_free(b);
-            delete b;
-            return st;
-        }
-        b->ctx.push_back(cx);
-    }
-    DeviceGuard g(b->device);
-    auto bail = [&](cudaError_t e) {
-        cudaGetLastError();
-        batch_free(b);
-        delete b;
-        return e == cudaErrorMemoryAllocation ? GWAS_ERR_OOM : GWAS_ERR_CUDA;
-    };
-    cudaError_t e;
-    if ((e = cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
-    if ((e = cudaMalloc(&b->d_jobs, sizeof(BatchJob) * n_cohorts)) != cudaSuccess) return bail(e);
-    if ((e = cudaMalloc(&b->d_tab, sizeof(CohortMx) * n_cohorts)) != cudaSuccess) return bail(e);
-    if ((e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * 3 * n_cohorts)) != cudaSuccess) return bail(e);
-    if ((e = cudaMalloc(&b->d_err, sizeof(int))) != cudaSuccess) return bail(e);
-    if ((e = cudaMemset(b->d_err, 0, sizeof(int))) != cudaSuccess) return bail(e);
-    if (b->mixed) {
-        const MixedDev& m = b->ctx[0]->mx;
-        b->stages = mixed_stage_count(m);
-        if ((e = mixed_batch_prepare(m, b->stages)) != cudaSuccess) return bail(e);
-    }
-    *out = b;
-    return GWAS_OK;
-}
-
-gwas_status gwas_batch_factor(gwas_batch* b, int cohort, const double* M_or_Phi, int is_phi,
-                              double h, double sigma2, const double* XL, const double* Y) {
-    if (!b) return GWAS_ERR_ARG;
-    if (cohort < 0 || cohort >= b->n_cohorts) return bfail(b, GWAS_ERR_ARG, "cohort out of range");
-    const gwas_status st = gwas_factor(b->ctx[cohort], M_or_Phi, is_phi, h, sigma2, XL, Y);
-    if (st != GWAS_OK) b->err = std::string("cohort ") + std::to_string(cohort) + ": " +
-                                gwas_last_error(b->ctx[cohort]);
-    b->key.clear();  // cohort constants changed: rebuild tables and graph
-    return st;
-}
-
-gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const int64_t* mb,
-                                    double* const* bo, double* const* wald,
-                                    uint8_t* const* status) {
-    Range range_("gwas batch solve");
-    if (!b) return GWAS_ERR_ARG;
-    if (!X || !mb || !bo || !status) return bfail(b, GWAS_ERR_ARG, "batch solve: NULL array");
-    const int nc = b->n_cohorts;
-    std::vector<uintptr_t> key;
-    key.reserve(5 * nc);
-    for (int c = 0; c < nc; ++c) {
-        gwas_ctx* cx = b->ctx[c];
-        if (!cx->factored) return bfail(b, GWAS_ERR_STATE, "batch solve before every cohort's factor");
-        if (!X[c] || !bo[c] || !status[c]) return bfail(b, GWAS_ERR_ARG, "batch solve: NULL pointer");
-        if (mb[c] < 1 || mb[c] > cx->opts.m_blk)
-            return bfail(b, GWAS_ERR_ARG, "batch solve: need 1 <= mb[c] <= m_blk");
-        key.push_back((uintptr_t)X[c]);
-        key.push_back((uintptr_t)mb[c]);
-        key.push_back((uintptr_t)bo[c]);
-        key.push_back((uintptr_t)(wald ? wald[c] : nullptr));
-        key.push_back((uintptr_t)status[c]);
-    }
-    DeviceGuard g(b->device);
-    if (key != b->key) {
-        // rebuild the device tables for this set of pointers and sizes
-        CKB(cudaStreamSynchronize(b->s));
-        std::vector<BatchJob> jobs(nc);
-        std::vector<CohortMx> tab(nc);
-        std::vector<CUtensorMap> maps(3 * nc);
-        int64_t snp = 0, u64 = 0, umx = 0;
-        for (int c = 0; c < nc; ++c) {
-            gwas_ctx* cx = b->ctx[c];
-            BatchJob& j = jobs[c];
-            j.c = cohort_view(cx);
-            j.X = X[c];
-            j.mb = mb[c];
-            j.snp_base = snp;
-            j.unit_base = u64;
-            j.n_rt64 = (int)ceil_div(cx->n, T64);
-            j.n_ct64 = (int)ceil_div(mb[c], T64);
-            j.part = cx->part;
-            j.ldp = cx->mixed ? cx->mx.ldp : cx->ldp;
-            j.bad = cx->bad;
-            j.b = bo[c];
-            j.wald = wald ? wald[c] : nullptr;
-            j.status = status[c];
-            snp += mb[c];
-            if (b->mixed) {
-                j.Xb = cx->mx.Xb;
-                j.n_pad = cx->mx.n_pad;
-                // cohorts given the same dosages (several traits of one cohort, each with
-                // its own M) convert them once and share the BF16 rows and flags
-                int src = c;
-                for (int e = 0; e < c; ++e) {
-                    if (X[e] == X[c] && mb[e] == mb[c] && b->ctx[e]->n == cx->n &&
-                        jobs[e].convert) {
-                        j.Xb = jobs[e].Xb;
-                        j.bad = jobs[e].bad;
-                        j.convert = 0;
-                        src = e;
-                        break;
-                    }
-                }
-                j.sq_part = cx->mx.sq_part;
-                j.lin = cx->mx.lin;
-                j.n_tiles_mx = cx->mx.n_rt;
-                j.lin_tiles = cx->mx.lin_tiles();
-                tab[c] = mixed_cohort_entry(cx->mx, mb[c], umx);
-                umx += mixed_cohort_units(cx->mx, mb[c]);
-                maps[3 * c + 0] = b->ctx[src]->mx.tmX;
-                maps[3 * c + 1] = cx->mx.tmW;
-                maps[3 * c + 2] = cx->mx.tmE;
-            } else {
-                u64 += (int64_t)j.n_rt64 * j.n_ct64;
-            }
-        }
-        CKB(cudaMemcpy(b->d_jobs, jobs.data(), sizeof(BatchJob) * nc, cudaMemcpyHostToDevice));
-        if (b->mixed) {
-            CKB(cudaMemcpy(b->d_tab, tab.data(), sizeof(CohortMx) * nc, cudaMemcpyHostToDevice));
-            CKB(cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * 3 * nc,
-                           cudaMemcpyHostToDevice));
-        }
-        b->total_snps = snp;
-        b->units_fp64 = u64;
-        b->units_mx = umx;
-        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
-        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
-        b->key = key;
-    }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (b->opts.timing) {
-        if (b->timed.size() >= 64) batch_fold_timings(b, false);
-        CKB(cudaEventCreate(&e0));
-        CKB(cudaEventCreate(&e1));
-        CKB(cudaEventRecord(e0, b->s));
-    }
-    if (b->opts.use_graph) {
-        if (!b->gexec) {
-            CKB(cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal));
-            const gwas_status st = batch_enqueue(b);
-            cudaGraph_t gr = nullptr;
-            const cudaError_t ec = cudaStreamEndCapture(b->s, &gr);
-            if (st != GWAS_OK) { if (gr) cudaGraphDestroy(gr); return st; }
-            CKB(ec);
-            b->graph = gr;
-            CKB(cudaGraphInstantiate(&b->gexec, b->graph, 0));
-        }
-        CKB(cudaGraphLaunch(b->gexec, b->s));
-    } else {
-        const gwas_status st = batch_enqueue(b);
-        if (st != GWAS_OK) return st;
-    }
-    if (b->opts.timing) {
-        CKB(cudaEventRecord(e1, b->s));
-        b->timed.emplace_back(e0, e1);
-    }
-    b->stats.blocks += 1;
-    b->stats.snps += b->total_snps;
-    b->stats.kernel_launches += b->mixed ? 4 : 3;
-    b->stats.trsm_launches += 1;
-    return GWAS_OK;
-}
-
-gwas_status gwas_batch_sync(gwas_batch* b, int timeout_ms) {
-    if (!b) return GWAS_ERR_ARG;
-    DeviceGuard g(b->device);
-    if (timeout_ms < 0) {
-        CKB(cudaStreamSynchronize(b->s));
-    } else {
-        const auto t0 = std::chrono::steady_clock::now();
-        for (;;) {
-            const cudaError_t e = cudaStreamQuery(b->s);
-            if (e == cudaSuccess) break;
-            if (e != cudaErrorNotReady) CKB(e);
-            const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(
-                                std::chrono::steady_clock::now() - t0).count();
-            if (el >= timeout_ms) return bfail(b, GWAS_ERR_TIMEOUT, "gwas_batch_sync: timed out");
-            std::this_thread::sleep_for(std::chrono::microseconds(200));
-        }
-    }
-    int code = 0;
-    CKB(cudaMemcpy(&code, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (code != 0) {
-        CKB(cudaMemset(b->d_err, 0, sizeof(int)));
-        return bfail(b, GWAS_ERR_CUDA, "batched mixed kernel: a pipeline wait timed out (site " +
-                                           std::to_string(code) + ")");
-    }
-    return GWAS_OK;
-}
-
-gwas_status gwas_batch_get_stats(gwas_batch* b, gwas_stats* out) {
-    if (!b || !out) return GWAS_ERR_ARG;
-    const gwas_status st = gwas_batch_sync(b, -1);
-    if (st != GWAS_OK) return st;
-    batch_fold_timings(b, true);
-    gwas_stats agg = b->stats;
-    agg.factor_ms = 0;
-    agg.factor_launches = 0;
-    for (auto* c : b->ctx) {
-        agg.factor_ms += c->stats.factor_ms;
-        agg.factor_launches += c->stats.factor_launches;
-    }
-    *out = agg;
-    return GWAS_OK;
-}
-
-gwas_status gwas_batch_reset_stats(gwas_batch* b) {
-    gwas_stats tmp;
-    const gwas_status st = gwas_batch_get_stats(b, &tmp);
-    if (b) b->stats = gwas_stats{};
-    return st;
-}
-
-gwas_status gwas_batch_finalize(gwas_batch* b) {
-    if (!b) return GWAS_OK;
-    {
-        DeviceGuard g(b->device);
-        if (b->s) cudaStreamSynchronize(b->s);
-        batch_free(b);
-    }
-    delete b;
-    return GWAS_OK;
-}
-
-const char* gwas_batch_last_error(const gwas_batch* b) { return b ? b->err.c_str() : "null batch"; }
-
-void* gwas_batch_stream(const gwas_batch* b) { return b ? (void*)b->s : nullptr; }
 
 }  // extern "C"
