@@ -92,3 +92,23 @@ def test_code_sha_ignores_comments_only():
     other = "__global__ void k(int* x) { x[0] = 2; }"
     assert bench.code_sha(src) == bench.code_sha(same)
     assert bench.code_sha(src) != bench.code_sha(other)
+
+
+def test_reference_arm_prints_one_json_line():
+    """`bench.py --impl reference` (the CPU oracle arm) prints one JSON line with the
+    contract's keys, on a small n."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--n", "300",
+                        "--steps", "2", "--warmup", "1"], capture_output=True, text=True,
+                       timeout=600, cwd=str(bench.ROOT))
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "impl", "cpu_baseline", "e2e", "config"):
+        assert k in d
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
