@@ -18,9 +18,10 @@
 // Checkpoint / resume: with --checkpoint every completed block is flushed to disk and then
 // recorded in PREFIX.progress (written to a temporary file and renamed, so it never claims
 // more than is on disk); --resume continues a job from the blocks PREFIX.progress records
-// (the job's sizes and formats must match); --max-blocks K stops cleanly after K new
-// blocks (a time-sliced run; resume it later).
+// (the job's sizes, formats, h, sigma2, input contents and genotype file must match);
+// --max-blocks K stops cleanly after K new blocks (a time-sliced run; resume it later).
 #include <fcntl.h>
+#include <sys/stat.h>
 #include <unistd.h>
 
 #include <chrono>
@@ -119,22 +120,44 @@ void pwrite_all(int fd, const void* p, size_t bytes, off_t off, const std::strin
     }
 }
 
-// The job identity recorded with the progress: a resume must describe the same job.
-std::string job_key(const Args& a, int64_t mblk) {
-    char buf[256];
-    std::snprintf(buf, sizeof buf, "n=%lld m=%lld m_blk=%lld q=%d t=%d input=%s precision=%s limbs=%d",
+// 64-bit checksum of an input array (FNV-1a over its 64-bit words): the progress file
+// of a job records those of Phi, X_L and Y, so that a resume with other inputs is refused.
+uint64_t checksum(const std::vector<double>& v) {
+    uint64_t h = 1469598103934665603ull;
+    for (double x : v) {
+        uint64_t w;
+        std::memcpy(&w, &x, sizeof w);
+        h = (h ^ w) * 1099511628211ull;
+    }
+    return h;
+}
+
+// The job identity recorded with the progress: a resume must describe the same job --
+// the same sizes, formats and model (h, sigma2, the inputs' contents) and the same
+// genotype file (path and size).
+std::string job_key(const Args& a, int64_t mblk, uint64_t sum_phi, uint64_t sum_xl,
+                    uint64_t sum_y, const std::string& geno, int64_t geno_bytes) {
+    char buf[512];
+    std::snprintf(buf, sizeof buf,
+                  "n=%lld m=%lld m_blk=%lld q=%d t=%d input=%s precision=%s limbs=%d h=%.17g "
+                  "sigma2=%.17g m_given=%d phi=%016llx covar=%016llx pheno=%016llx "
+                  "genotype_bytes=%lld genotypes=",
                   (long long)a.n, (long long)a.m, (long long)mblk, a.q, a.t,
-                  a.bed.empty() ? "int8" : "bed", a.mixed ? "mixed" : "fp64", a.limbs);
-    return buf;
+                  a.bed.empty() ? "int8" : "bed", a.mixed ? "mixed" : "fp64", a.limbs, a.h,
+                  a.sigma2, a.m_given ? 1 : 0, (unsigned long long)sum_phi,
+                  (unsigned long long)sum_xl, (unsigned long long)sum_y, (long long)geno_bytes);
+    std::string key = buf + geno;
+    for (char& ch : key)
+        if (ch == '\n' || ch == '\r') ch = '?';
+    return key;
 }
 
 int64_t read_progress(const std::string& path, const std::string& key) {
     FILE* f = std::fopen(path.c_str(), "r");
     if (!f) return 0;  // nothing done yet
-    char line[512] = {0};
-    const bool got = std::fgets(line, sizeof line, f) != nullptr;
+    std::string s;
+    for (int ch; (ch = std::fgetc(f)) != EOF && ch != '\n';) s.push_back((char)ch);
     std::fclose(f);
-    const std::string s = got ? std::string(line) : std::string();
     const std::string head = "gwas_stream-progress " + key + " blocks=";
     if (s.compare(0, head.size(), head) != 0) die(6, path + " belongs to another job");
     return std::stoll(s.substr(head.size()));
@@ -211,7 +234,14 @@ int main(int argc, char** argv) {
         check(ctx, gwas_host_alloc((size_t)mblk, &os[k]), "gwas_host_alloc");
     }
     // outputs, written block by block; blocks [b0, nblk) are this run's
-    const std::string key = job_key(a, mblk), progress = a.out + ".progress";
+    const std::string progress = a.out + ".progress";
+    std::string key;
+    if (a.checkpoint) {
+        struct stat sb;
+        if (::fstat(fd, &sb) != 0) die(3, "cannot stat the genotype file");
+        key = job_key(a, mblk, checksum(phi), checksum(XL), checksum(Y),
+                      packed ? a.bed : a.dosages, (int64_t)sb.st_size);
+    }
     const int64_t b0 = a.resume ? read_progress(progress, key) : 0;
     if (b0 > nblk) die(6, progress + " records more blocks than the job has");
     const int64_t b_end = a.max_blocks >= 0 ? std::min(nblk, b0 + a.max_blocks) : nblk;

@@ -109,3 +109,12 @@ def test_checkpoint_and_resume(gpu, tmp_path):
     other = [*base[:-6], "--m-blk", 32, "--h", c.h, "--sigma2", c.sigma2]
     bad = run_cli([*other, "--resume", "--out", tmp_path / "part"])
     assert bad.returncode == 6 and "another job" in bad.stderr
+    # another model (h) or other phenotype values on the same sizes are another job too
+    first = run_cli([*base, "--checkpoint", "--max-blocks", 2, "--out", tmp_path / "p2"])
+    assert first.returncode == 0, first.stderr
+    other_h = [*base[:-4], "--h", c.h + 0.1, "--sigma2", c.sigma2]
+    bad = run_cli([*other_h, "--resume", "--out", tmp_path / "p2"])
+    assert bad.returncode == 6 and "another job" in bad.stderr
+    np.ascontiguousarray(c.Y.T + 1.0).tofile(tmp_path / "pheno.f64")
+    bad = run_cli([*base, "--resume", "--out", tmp_path / "p2"])
+    assert bad.returncode == 6 and "another job" in bad.stderr
