@@ -331,8 +331,9 @@ gwas_status gwas_autotune(gwas_ctx* ctx, const int8_t* X, int64_t mb_max, int re
  * --------------------------------------------------------------------------------- */
 
 /* Create a batch of n_cohorts contexts with sizes n[c] (host array). opts->m_blk is the
- * largest number of SNPs per cohort in one batched solve. GWAS_PREC_MIXED batches use
- * the one-CTA-per-tile kernel variant. Errors as gwas_init. */
+ * largest number of SNPs per cohort in one batched solve. Every cohort takes
+ * opts->tile_cfg: GWAS_PREC_MIXED batches run the CTA-pair kernel variant unless bit 12
+ * forces one CTA per 128-SNP tile. Errors as gwas_init. */
 gwas_status gwas_batch_init(int n_cohorts, const int64_t* n, int p, int t, const gwas_opts* opts,
                             gwas_batch** out);
 
@@ -376,6 +377,17 @@ void* gwas_batch_stream(const gwas_batch* b);
 gwas_status gwas_selftest_wait(int device, int timeout_ms, double* waited_ms);
 
 /*
+ * Measured FP64 multiply-add rate of a device (the paper has no counterpart): the
+ * roofline denominator of the FP64 block kernel, which is bound by the FP64 FMA pipe.
+ * Times a few shapes of a kernel whose threads run independent chains of dependent
+ * FP64 fma (8 or 16 chains per thread, 2-8 CTAs of 256 threads per SM, ~0.1 s per
+ * launch, best of two launches after a warm-up) and returns the best rate in *tflops
+ * (2 flops per fma). Synchronous, about 1.5 s; allocates a few hundred kB of device
+ * memory. Errors: GWAS_ERR_ARG (NULL tflops), GWAS_ERR_CUDA.
+ */
+gwas_status gwas_fp64_fma_rate(int device, double* tflops);
+
+/*
  * Allocation-free FP64 block solve. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they call in -- their
  * GPU memory is already fully reserved by another allocator (a framework's caching
@@ -401,7 +413,10 @@ gwas_status gwas_selftest_wait(int device, int timeout_ms, double* waited_ms);
  * capture. All calls share the one array and it keeps the last call's contents
  * (nothing in it needs to start at zero): calls that overlap on the GPU -- on
  * different streams, or from different threads -- race on it and must be serialised
- * by the caller. Errors: GWAS_ERR_ARG, GWAS_ERR_TOO_LARGE, GWAS_ERR_CUDA.
+ * by the caller. Before launching, the call checks (cudaPointerGetAttributes, which
+ * allocates nothing) that the first and last byte of every buffer lie in device or
+ * managed memory of the current device; host memory, another device's memory or an
+ * unknown address is GWAS_ERR_ARG. Errors: GWAS_ERR_ARG, GWAS_ERR_TOO_LARGE, GWAS_ERR_CUDA.
  */
 gwas_status gwas_solve_block_noalloc(int64_t n, int p, int t, const double* Linv,
                                      int64_t ld_linv, const double* XLbar, const double* Ybar,

@@ -46,6 +46,25 @@ gwas_status scratch_on_current_device(void** out) {
     return GWAS_OK;
 }
 
+// True when bytes [p, p + bytes) start and end in device (or managed) memory of device
+// `dev`. Allocates nothing; an address the runtime does not know (host memory, a
+// foreign device's pointer, a stray integer) is refused before any kernel sees it.
+bool device_range(const void* p, size_t bytes, int dev) {
+    if (!p || bytes == 0) return false;
+    const unsigned char* ends[2] = {static_cast<const unsigned char*>(p),
+                                    static_cast<const unsigned char*>(p) + (bytes - 1)};
+    for (const unsigned char* q : ends) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return false;
+        if (at.device != dev) return false;
+    }
+    return true;
+}
+
 }  // namespace
 
 extern "C" gwas_status gwas_solve_block_noalloc(int64_t n, int p, int t, const double* Linv,
@@ -64,6 +83,25 @@ extern "C" gwas_status gwas_solve_block_noalloc(int64_t n, int p, int t, const d
     const int64_t part_bytes = round_up(n_rt * nred * ldp * (int64_t)sizeof(double), 256);
     const int64_t bad_bytes = round_up(mb, 256);
     if (part_bytes + bad_bytes > (int64_t)kScratchBytes) return GWAS_ERR_TOO_LARGE;
+
+    // every buffer must be device memory of the current device, large enough for the call
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return GWAS_ERR_CUDA;
+    }
+    const size_t d8 = sizeof(double);
+    const int64_t q = p - 1;
+    if (!device_range(Linv, (size_t)(ld_linv * (n - 1) + n) * d8, dev) ||
+        !device_range(XLbar, (size_t)(n * q) * d8, dev) ||
+        !device_range(Ybar, (size_t)(n * t) * d8, dev) ||
+        !device_range(S_TL, (size_t)(q * q) * d8, dev) ||
+        !device_range(bbar_T, (size_t)(q * t) * d8, dev) ||
+        !device_range(X, (size_t)(n * mb), dev) ||
+        !device_range(b, (size_t)(mb * t * p) * d8, dev) ||
+        (wald && !device_range(wald, (size_t)(mb * t) * d8, dev)) ||
+        !device_range(status, (size_t)mb, dev))
+        return GWAS_ERR_ARG;
 
     void* base = nullptr;
     const gwas_status st = scratch_on_current_device(&base);

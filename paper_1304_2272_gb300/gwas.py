@@ -105,6 +105,7 @@ SIGNATURES = {
                                         _i64, _vp, _vp, _vp, _vp]),
     "gwas_set_tile_cfg": (_int, [_ctx_p, _int]),
     "gwas_selftest_wait": (_int, [_int, _int, ctypes.POINTER(_dbl)]),
+    "gwas_fp64_fma_rate": (_int, [_int, ctypes.POINTER(_dbl)]),
     "gwas_reml": (_int, [_ctx_p, _vp, _dbl, _dbl, _vp, _vp, _int, _int,
                          ctypes.POINTER(gwas_reml_result)]),
     "gwas_solve_block_grad_device": (_int, [_ctx_p, _vp, _i64, _vp, _vp, _vp, _vp]),
@@ -179,11 +180,14 @@ def _require(x, dtype, name: str, order: str = "F"):
 _TORCH_DTYPES = {np.int8: "torch.int8", np.uint8: "torch.uint8", np.float64: "torch.float64"}
 
 
-def _require_dev(x, dtype, name: str):
-    """A device buffer passed as a tensor must have the C ABI's element type and be
-    contiguous (raw addresses and None pass through unchecked)."""
+def _require_dev(x, dtype, name: str, device: int | None = None):
+    """A device buffer passed as a tensor must have the C ABI's element type, be
+    contiguous, live in device memory and (when `device` is given) on that device. Host
+    arrays are refused; raw addresses and None pass through unchecked."""
     if x is None or isinstance(x, int):
         return x
+    if isinstance(x, np.ndarray):
+        raise TypeError(f"{name} must be a device tensor, got a host numpy array")
     if hasattr(x, "is_contiguous") and hasattr(x, "dtype"):
         if str(x.dtype) != _TORCH_DTYPES[dtype]:
             raise TypeError(f"{name} must be {_TORCH_DTYPES[dtype]}, got {x.dtype}")
@@ -191,6 +195,8 @@ def _require_dev(x, dtype, name: str):
             raise ValueError(f"{name} must be contiguous")
         if getattr(x, "is_cuda", True) is False:
             raise ValueError(f"{name} must be in device memory")
+        if device is not None and x.device.index != device:
+            raise ValueError(f"{name} is on cuda:{x.device.index}, the call runs on cuda:{device}")
     return x
 
 
@@ -336,9 +342,22 @@ def gwas_solve_block_noalloc(n: int, p: int, t: int, Linv, ld_linv: int, XLbar, 
     For callers that must not allocate GPU memory at call time (memory already held by
     another allocator, or a serving loop that cannot afford cudaMalloc). All arrays are
     device memory on the current device; see include/gwas.h for layouts and the 16 MiB
-    scratch limit (GWAS_ERR_TOO_LARGE beyond it). ``stream`` is a cudaStream_t address
-    (None = the default stream). Returns once the work is queued.
+    scratch limit (GWAS_ERR_TOO_LARGE beyond it). Tensors must be contiguous, of the C ABI's
+    element type and on the current device (TypeError / ValueError otherwise). ``stream``
+    is a torch.cuda.Stream or a cudaStream_t address (None = the default stream). Returns
+    once the work is queued.
     """
+    bufs = (Linv, XLbar, Ybar, S_TL, bbar_T, X, b, wald, status)
+    dev = None
+    if any(hasattr(x, "is_cuda") for x in bufs):
+        import torch
+        dev = torch.cuda.current_device()
+    for x, nm in ((Linv, "Linv"), (XLbar, "XLbar"), (Ybar, "Ybar"), (S_TL, "S_TL"),
+                  (bbar_T, "bbar_T"), (b, "b"), (wald, "wald")):
+        _require_dev(x, np.float64, nm, dev)
+    _require_dev(X, np.int8, "X", dev)
+    _require_dev(status, np.uint8, "status", dev)
+    stream = getattr(stream, "cuda_stream", stream)  # a torch.cuda.Stream or an address
     st = load().gwas_solve_block_noalloc(
         int(n), int(p), int(t), _addr(Linv), int(ld_linv), _addr(XLbar), _addr(Ybar),
         _addr(S_TL), _addr(bbar_T), _addr(X), int(mb), _addr(b), _addr(wald), _addr(status),
@@ -371,6 +390,15 @@ def gwas_selftest_wait(device: int = 0, timeout_ms: int = 200) -> tuple[int, flo
     w = _dbl(0.0)
     st = load().gwas_selftest_wait(int(device), int(timeout_ms), ctypes.byref(w))
     return st, w.value
+
+
+def gwas_fp64_fma_rate(device: int = 0) -> float:
+    """Measured FP64 multiply-add rate of the device in TFLOP/s (the FP64 roofline)."""
+    r = _dbl(0.0)
+    st = load().gwas_fp64_fma_rate(int(device), ctypes.byref(r))
+    if st != GWAS_OK:
+        raise GwasError(st, "gwas_fp64_fma_rate failed")
+    return r.value
 
 
 def gwas_set_tile_cfg(ctx, tile_cfg: int) -> None:
