@@ -66,7 +66,13 @@ def _parser():
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the REML-fit and db/dh leg (n=10000, FP64)")
     ap.add_argument("--adjoint-steps", type=int, default=3)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    ap.add_argument("--no-fp64-n30k", action="store_true",
+                    help="skip the FP64 leg at n=30000 (blocks of 2048 SNPs)")
+    ap.add_argument("--fp64-n30k-steps", type=int, default=3)
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the oracle check of the sampled outputs of every leg")
+    ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     return ap
 
 
@@ -275,30 +281,191 @@ def fp64_peak_tflops(sm_mhz: float | None) -> tuple[float, str]:
     return 152 * 2 * 2 * mhz * 1e6 / 1e12, f"152 SM x 2 DFMA/clk x 2 flop x {mhz:.0f} MHz"
 
 
-def cpu_baseline(cohort, X_host, seconds: float) -> dict:
-    """The oracle as it stands (Algorithm 1 route), timed on the host cores."""
+# SNPs per oracle call on the host, the same in every CPU leg and in the reference arm
+# (the oracle's per-call rate depends on the size of its triangular solves).
+CPU_BLOCK = 1024
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline records."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def blas_threads():
+    """Threads of the OpenBLAS that numpy loaded (None if it cannot be asked)."""
+    import ctypes
+    libs = set()
+    try:
+        with open("/proc/self/maps") as f:
+            for ln in f:
+                parts = ln.split()
+                if len(parts) >= 6 and "openblas" in os.path.basename(parts[-1]).lower() \
+                        and ".so" in parts[-1]:
+                    libs.add(parts[-1])
+    except OSError:
+        return None
+    for path in sorted(libs):
+        try:
+            lib = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for sym in ("openblas_get_num_threads", "openblas_get_num_threads64_",
+                    "scipy_openblas_get_num_threads64_", "scipy_openblas_get_num_threads"):
+            fn = getattr(lib, sym, None)
+            if fn is not None:
+                fn.restype = ctypes.c_int
+                return int(fn())
+    return None
+
+
+def oracle_rate(L, cohort, X_host, block: int, seconds: float, trsv: str = "auto"):
+    """SNP/s of the oracle's Algorithm 1 route on blocks of `block` SNPs of X_host, run
+    until `seconds` of compute or every column is used. Returns (rate, snps)."""
     import numpy as np
     from oracle import gls as G
-    t0 = time.perf_counter()
-    L = G.factor(cohort.phi, cohort.h, cohort.sigma2)
     setup = G.setup_hoisted(L, cohort.XL, cohort.Y)
-    t_factor = time.perf_counter() - t0
-    m = 64
-    done = 0
-    elapsed = 0.0
-    while True:
-        Xs = np.asfortranarray(X_host[:, done:done + m])
+    done, elapsed = 0, 0.0
+    while done < X_host.shape[1]:
+        Xs = np.asfortranarray(X_host[:, done:done + block])
         t1 = time.perf_counter()
-        G.gls_hoisted(L, cohort.XL, cohort.Y, Xs, setup=setup)
+        G.gls_hoisted(L, cohort.XL, cohort.Y, Xs, trsv=trsv, setup=setup)
         elapsed += time.perf_counter() - t1
         done += Xs.shape[1]
-        if elapsed >= seconds or done >= X_host.shape[1]:
+        if elapsed >= seconds:
             break
-        m = min(2 * m, X_host.shape[1] - done)
-    return {"value": done / elapsed, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{done} SNPs at n={cohort.n} after a one-off factor of {t_factor:.1f} s "
-                      f"(numpy/scipy BLAS threads: library default)",
-            "factor_s": round(t_factor, 2)}
+    return done / elapsed, done
+
+
+def cpu_worker(spec_path: str) -> None:
+    """One single-threaded oracle process of the CPU baselines (the parent set the BLAS
+    threads to 1): load L (memory-mapped), X_L, Y and a dosage chunk, report "ready",
+    wait for "go" on stdin, time the chunk, print one JSON line."""
+    import numpy as np
+    from oracle import gls as G
+    with open(spec_path) as f:
+        spec = json.load(f)
+    L = np.load(spec["L"], mmap_mode="r")
+    d = np.load(spec["data"])
+    XL, Y = d["XL"], d["Y"]
+    X = np.asfortranarray(d["X"][:, spec["lo"]:spec["hi"]])
+    setup = G.setup_hoisted(L, XL, Y)
+    print("ready", flush=True)
+    sys.stdin.readline()
+    t0 = time.perf_counter()
+    for c0 in range(0, X.shape[1], spec["block"]):
+        G.gls_hoisted(L, XL, Y, np.asfortranarray(X[:, c0:c0 + spec["block"]]),
+                      trsv=spec["trsv"], setup=setup)
+    print(json.dumps({"snps": int(X.shape[1]), "seconds": time.perf_counter() - t0,
+                      "blas_threads": blas_threads()}), flush=True)
+
+
+def run_workers(L, cohort, X_host, chunks, block: int, trsv: str) -> dict:
+    """Start one single-threaded oracle process per (lo, hi) chunk of X_host, release them
+    together and time them on the wall clock until the last one is done."""
+    import tempfile
+    import numpy as np
+    base = "/dev/shm" if os.path.isdir("/dev/shm") else None
+    with tempfile.TemporaryDirectory(dir=base) as tmp:
+        np.save(os.path.join(tmp, "L.npy"), L)
+        np.savez(os.path.join(tmp, "data.npz"), XL=cohort.XL, Y=cohort.Y, X=X_host)
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1",
+                   MKL_NUM_THREADS="1")
+        procs = []
+        for k, (lo, hi) in enumerate(chunks):
+            spec = os.path.join(tmp, f"spec{k}.json")
+            with open(spec, "w") as f:
+                json.dump({"L": os.path.join(tmp, "L.npy"), "data": os.path.join(tmp, "data.npz"),
+                           "lo": lo, "hi": hi, "block": block, "trsv": trsv}, f)
+            procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__),
+                                           "--cpu-worker", spec], stdin=subprocess.PIPE,
+                                          stdout=subprocess.PIPE, text=True, env=env, cwd=ROOT))
+        for pr in procs:
+            if pr.stdout.readline().strip() != "ready":
+                raise RuntimeError("a CPU baseline worker failed to start")
+        t0 = time.perf_counter()
+        for pr in procs:
+            pr.stdin.write("go\n")
+            pr.stdin.flush()
+        outs = [json.loads(pr.stdout.readline()) for pr in procs]
+        wall = time.perf_counter() - t0
+        for pr in procs:
+            pr.wait(timeout=60)
+    snps = sum(o["snps"] for o in outs)
+    return {"value": snps / wall, "snps": snps, "wall_s": round(wall, 3),
+            "blas_threads": outs[0]["blas_threads"]}
+
+
+def cpu_baseline(cohort, X_host, seconds: float, flavours: bool = True) -> tuple[dict, object]:
+    """The oracle as it stands, timed on the host cores: Algorithm 1 with multithreaded
+    BLAS on blocks of CPU_BLOCK SNPs (the headline CPU number; a blocked dtrsm over SNP
+    blocks, the shape of the paper's SMP design), and beside it the same route on one
+    thread, the textbook row-loop substitution on one thread, and one single-threaded
+    process per core each on its own SNPs (parallel over SNPs). Returns (record, L)."""
+    from oracle import gls as G
+    cores = os.cpu_count()
+    model = cpu_model()
+    t0 = time.perf_counter()
+    L = G.factor(cohort.phi, cohort.h, cohort.sigma2)
+    t_factor = time.perf_counter() - t0
+    v, done = oracle_rate(L, cohort, X_host, CPU_BLOCK, seconds)
+    threads = blas_threads() or cores
+    rec = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{done} SNPs at n={cohort.n} in blocks of {CPU_BLOCK} after a one-off "
+                     f"factor of {t_factor:.1f} s; Algorithm 1 route (LAPACK dtrsm), "
+                     f"OpenBLAS threads {threads} of {cores} cores",
+           "factor_s": round(t_factor, 2), "cpu_model": model, "host_cores": cores}
+    if flavours:
+        fl = [{"flavour": "algorithm1_blas_all_threads", "value": v, "unit": UNIT,
+               "threads": threads, "snps": done}]
+        try:
+            one = run_workers(L, cohort, X_host, [(0, 256)], 256, "auto")
+            fl.append({"flavour": "algorithm1_blas_1_thread", "value": one["value"],
+                       "unit": UNIT, "threads": one["blas_threads"] or 1, "snps": one["snps"]})
+            plain = run_workers(L, cohort, X_host, [(0, 32)], 32, "plain")
+            fl.append({"flavour": "plain_row_loop_substitution_1_thread",
+                       "value": plain["value"], "unit": UNIT,
+                       "threads": plain["blas_threads"] or 1, "snps": plain["snps"]})
+            procs = max(1, min(cores, X_host.shape[1]))
+            per = min(256, X_host.shape[1] // procs)
+            par = run_workers(L, cohort, X_host, [(k * per, (k + 1) * per) for k in range(procs)],
+                              per, "auto")
+            fl.append({"flavour": f"processes_over_snps_{procs}x1_thread", "value": par["value"],
+                       "unit": UNIT, "threads": procs, "snps": par["snps"]})
+        except (OSError, RuntimeError, ValueError, subprocess.SubprocessError) as e:
+            fl.append({"flavour": "single-threaded workers", "error": str(e)[:200]})
+        rec["flavours"] = fl
+    return rec, L
+
+
+def oracle_errors(L, cohort, sample) -> dict:
+    """Largest error of the sampled outputs of a GPU leg against the FP64 oracle
+    (Algorithm 1 route): b per SNP and phenotype relative to max_c |b_c| of the oracle,
+    the Wald statistic relative to max(W, 1); statuses must agree exactly."""
+    import numpy as np
+    from oracle import gls as G
+    rb, rw, rs = G.gls_hoisted(L, cohort.XL, cohort.Y, sample["X"])
+    ok = rs == 0
+    same = bool(np.array_equal(rs, sample["status"]))
+    b, w = sample["b"][ok], sample["wald"][ok]
+    scale = np.maximum(np.max(np.abs(rb[ok]), axis=-1, keepdims=True), 1e-300)
+    err_b = float(np.max(np.abs(b - rb[ok]) / scale)) if ok.any() else 0.0
+    err_w = float(np.max(np.abs(w - rw[ok]) / np.maximum(rw[ok], 1.0))) if ok.any() else 0.0
+    return {"err_b": err_b, "err_wald": err_w, "status_match": same,
+            "snps_checked": int(sample["snps"])}
 
 
 def run_reference(args, rank, world):
@@ -318,7 +485,8 @@ def run_reference(args, rank, world):
     cohort = synth.make_cohort(0, args.n, t=args.t, device=dev)
     L = G.factor(cohort.phi, cohort.h, cohort.sigma2)
     setup = G.setup_hoisted(L, cohort.XL, cohort.Y)
-    per_step = max(8, int(2e10 / (args.n * args.n)))  # ~1-2 s of BLAS work per step
+    # the CPU baseline's block of SNPs per oracle call (scaled by n^2 away from n = 10k)
+    per_step = max(8, min(CPU_BLOCK, int(CPU_BLOCK * 1e8 / (args.n * args.n))))
     blocks = [cohort.snps(per_step, stream=s) for s in range(args.warmup + args.steps)]
     for s in range(args.warmup):
         G.gls_hoisted(L, cohort.XL, cohort.Y, blocks[s], setup=setup)
@@ -332,8 +500,12 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": workload_config(args),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{per_step} SNPs per step at n={args.n}"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": blas_threads() or os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"{per_step} SNPs per step at n={args.n} (one oracle call, "
+                                       "Algorithm 1 route, LAPACK dtrsm), OpenBLAS threads "
+                                       f"{blas_threads()} of {os.cpu_count()} cores",
+                             "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -349,16 +521,30 @@ def workload_config(args) -> dict:
                   "blocks cycled"}
 
 
-def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
+def sample_index(mb: int, k: int = 252, seed: int = 1):
+    """The SNPs of a block whose outputs are checked against the oracle: the first and
+    last SNP, both sides of the first 128-SNP tile boundary and k seeded others (the
+    sample the parity tests use)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(mb, min(k, mb), replace=False)
+    return np.unique(np.concatenate([[0, min(127, mb - 1), min(128, mb - 1), mb - 1], pick]))
+
+
+def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True, mb=None,
+            packed_steps=None):
     """Factor one cohort, then time `steps` blocks (device-resident) and, if asked,
-    the same blocks end to end from pinned host memory. Returns (result, cohort, pool)."""
+    the same blocks end to end from pinned host memory. Returns (result, cohort, pool);
+    result["sample"] holds sampled dosages and outputs of the last timed block (host
+    arrays) for the oracle check after every GPU leg."""
     import numpy as np
     import torch
     import synth
     from paper_1304_2272_gb300 import gwas
 
     rank, world, local, dev = env
-    mb, t, p = args.m_blk, args.t, 4
+    mb = args.m_blk if mb is None else mb
+    t, p = args.t, 4
     prec = gwas.GWAS_PREC_FP64 if precision == "fp64" else gwas.GWAS_PREC_MIXED
     cohort = synth.make_cohort(0, n, t=t, device=dev)
     ctx = gwas.gwas_init(n, p, t, m_blk=mb, device=local, timing=1, precision=prec,
@@ -407,6 +593,11 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
     stats = gwas.gwas_get_stats(ctx)
     status_ok = int((st == 0).sum().item())
     value = job_rate(steps * mb, world, el_ms / 1e3)
+    idx = sample_index(mb)
+    it = torch.from_numpy(idx).to(dev)
+    sample = {"X": np.asfortranarray(pool[(steps - 1) % args.pool][it].cpu().numpy().T),
+              "b": b[it].cpu().numpy(), "wald": w[it].cpu().numpy(),
+              "status": st[it].cpu().numpy(), "snps": int(idx.size)}
 
     # ---- end to end from pinned host memory (e2e) ------------------------------
     e2e = None
@@ -435,29 +626,38 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
         e2e["h2d_frac"] = e2e["h2d_gbs"] / world / e2e["h2d_peak_gbs"]
         # the same stream as 2-bit calls (n/4 bytes per SNP), unpacked on the GPU
         ppool = [pack_2bit_torch(x).cpu().pin_memory() for x in pool[:2]]
-        for s in range(warmup):
+        pk_steps = steps if packed_steps is None else max(1, min(steps, packed_steps))
+        for s in range(min(warmup, 2)):
             gwas.gwas_solve_block_packed(ctx, ppool[s % 2], mb, gwas.CODE_DOSAGE, hb, hw, hs)
         gwas.gwas_sync(ctx)
         barrier()
         t0 = time.perf_counter()
-        for s in range(steps):
+        for s in range(pk_steps):
             gwas.gwas_solve_block_packed(ctx, ppool[s % 2], mb, gwas.CODE_DOSAGE, hb, hw, hs)
         gwas.gwas_sync(ctx)
         barrier()
         pk_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-        e2e["packed_2bit"] = {"value": job_rate(steps * mb, world, pk_s), "unit": UNIT,
+        e2e["packed_2bit"] = {"value": job_rate(pk_steps * mb, world, pk_s), "unit": UNIT,
+                              "steps": pk_steps,
                               "h2d_bytes_per_step": ppool[0].numel(),
                               "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]}
 
     q = p - 1
     launch_ms = stats["trsm_ms"] / max(1, stats["trsm_launches"])
     if precision == "fp64":
-        peak, how = fp64_peak_tflops(clk.get("sm_mhz"))
+        nominal, how = fp64_peak_tflops(clk.get("sm_mhz"))
         achieved = flops_per_snp(n, q, t) * mb / (launch_ms / 1e3) / 1e12
+        probe = args.fp64_probe or {}
+        peak = probe.get("tflops") or nominal
+        src = ("gwas_fp64_fma_rate: FP64 fma chains timed on this GPU before the timed "
+               f"region at a median {probe.get('sm_mhz')} MHz (of measured)") if probe.get(
+                   "tflops") else how + " (derived, of nominal)"
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic_for("k_block_fp64", n, mb),
                 "kernel": "k_block_fp64",
-                "launch_ms": launch_ms, "peak_source": how + " (derived, of nominal)"}
+                "launch_ms": launch_ms, "peak_source": src,
+                "peak_nominal_derived": nominal, "frac_of_nominal": achieved / nominal,
+                "nominal_source": how}
     else:
         pk = measured_peaks()
         long_run = el_ms >= 1000.0
@@ -476,7 +676,7 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True):
     res = {"value": value, "ms_per_step": el_ms / steps, "steps": steps, "warmup": warmup,
            "setup_ms": setup_ms, "roofline": roof, "e2e": e2e, "autotune": tune,
            "gpu_launches": int(stats["kernel_launches"]), "clocks": clk,
-           "status_ok_last_block": status_ok}
+           "status_ok_last_block": status_ok, "sample": sample, "m_blk": mb}
     gwas.gwas_finalize(ctx)
     return res, cohort, pool
 
@@ -539,7 +739,11 @@ def measure_batch(args, env, precision, snps, steps, warmup):
            "snp_phenotypes_per_s": t * total / (el_ms / 1e3), "ms_per_step": el_ms / steps,
            "fp64_equivalent_tflops": work * steps / (el_ms / 1e3) / 1e12,
            "setup_ms": setup_ms, "graph": True, "gpu_launches": int(st["kernel_launches"]),
-           "status_ok": ok, "clocks": clk}
+           "status_ok": ok, "clocks": clk,
+           "workload": f"{len(ns)} cohorts n ~ U[1000, 8000], p=4, {t} phenotypes, {snps} SNPs "
+                       "per cohort per step" + ("" if snps >= 50000 else
+                                                " (a prefix of the 50,000-SNP cohorts, timed "
+                                                "as a rate)")}
     if precision == "mixed":
         bf16 = sum(args.limbs * (n * (n + 1) + 2.0 * n * (3 + t)) for n in ns) * snps
         res["bf16_tflops"] = bf16 * steps / (el_ms / 1e3) / 1e12
@@ -599,8 +803,26 @@ def measure_adjoint(args, env, steps, warmup):
             "status_ok": ok, "clocks": clk}
 
 
+# Relative tolerance on the Wald statistic (against max(W, 1)) that the parity tests hold
+# each limb count to (tests/test_parity_mixed.py), and that of the FP64 path.
+MIXED_WALD_TOL = {3: 1e-5, 4: 1e-8, 5: 1e-10}
+FP64_TOL = {"b": 1e-10, "wald": 1e-10}
+
+
+def probe_fp64(local: int) -> dict:
+    """Measured FP64 fma rate of this GPU (the FP64 roofline), with the clocks it ran at."""
+    from paper_1304_2272_gb300 import gwas
+    clocks = ClockSampler(local)
+    clocks.start()
+    r = gwas.gwas_fp64_fma_rate(local)
+    clk = clocks.stop()
+    return {"tflops": r, "sm_mhz": clk.get("sm_mhz"), "clocks": clk}
+
+
 def main():
     args = parse()
+    if args.cpu_worker:
+        return cpu_worker(args.cpu_worker)
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
@@ -614,8 +836,28 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(dev))
     env = (rank, world, local, dev)
+    args.fp64_probe = probe_fp64(local) if args.precision == "fp64" else None
     res, cohort, pool = measure(args, env, n=args.n, precision=args.precision,
-                                limbs=args.limbs, steps=args.steps, warmup=args.warmup)
+                                limbs=args.limbs, steps=args.steps, warmup=args.warmup,
+                                packed_steps=5)
+    cohorts = {args.n: cohort}
+    checks = [(res, args.n)]  # (record, n): sampled outputs checked against the oracle
+    fp64_legs = []
+    if args.precision == "fp64" and not args.no_fp64_n30k:
+        # the metric's second FP64 point: n = 30,000 in blocks of 2,048 SNPs (a prefix of
+        # the n = 30k job, timed as a rate; each block is ~1.5 s of FP64 work)
+        r, c30, _ = measure(args, env, n=30000, precision="fp64", limbs=args.limbs,
+                            steps=args.fp64_n30k_steps, warmup=1, want_e2e=False, mb=2048)
+        cohorts[30000] = c30
+        leg = {"n": 30000, "m_blk": 2048, "precision": "fp64",
+               "workload": "FP64 GLS, n=30000, p=4, t=1, blocks of 2048 SNPs (a prefix of the "
+                           "n=30k job timed as a rate)",
+               "tolerance_rel_b": FP64_TOL["b"], "tolerance_wald": FP64_TOL["wald"],
+               "value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+               "steps": r["steps"], "setup_ms": r["setup_ms"], "roofline": r["roofline"],
+               "clocks": r["clocks"], "gpu_launches": r["gpu_launches"], "sample": r["sample"]}
+        fp64_legs.append(leg)
+        checks.append((leg, 30000))
     mixed = []
     if args.precision == "fp64" and not args.no_mixed:
         # the metric's mixed legs (3 limbs: b within 1e-6 of FP64), and 5 limbs at n = 10k,
@@ -624,15 +866,20 @@ def main():
                 (30000, args.limbs, max(1, args.mixed_steps // 8)),
                 (args.n, 5, max(1, args.mixed_steps // 2)))
         for n_mx, limbs_mx, steps_mx in legs:
-            r, _, _ = measure(args, env, n=n_mx, precision="mixed", limbs=limbs_mx,
-                              steps=steps_mx, warmup=args.warmup)
-            mixed.append({"n": n_mx, "limbs": limbs_mx,
-                          "tolerance_rel_b": MIXED_TOL.get(limbs_mx),
-                          "value": r["value"], "unit": UNIT,
-                          "ms_per_step": r["ms_per_step"], "steps": steps_mx,
-                          "setup_ms": r["setup_ms"], "roofline": r["roofline"],
-                          "e2e": r["e2e"], "clocks": r["clocks"], "autotune": r["autotune"],
-                          "gpu_launches": r["gpu_launches"]})
+            r, c_mx, _ = measure(args, env, n=n_mx, precision="mixed", limbs=limbs_mx,
+                                 steps=steps_mx, warmup=args.warmup, packed_steps=steps_mx)
+            cohorts.setdefault(n_mx, c_mx)
+            del c_mx
+            leg = {"n": n_mx, "limbs": limbs_mx,
+                   "tolerance_rel_b": MIXED_TOL.get(limbs_mx),
+                   "tolerance_wald": MIXED_WALD_TOL.get(limbs_mx),
+                   "value": r["value"], "unit": UNIT,
+                   "ms_per_step": r["ms_per_step"], "steps": steps_mx,
+                   "setup_ms": r["setup_ms"], "roofline": r["roofline"],
+                   "e2e": r["e2e"], "clocks": r["clocks"], "autotune": r["autotune"],
+                   "gpu_launches": r["gpu_launches"], "sample": r["sample"]}
+            mixed.append(leg)
+            checks.append((leg, n_mx))
     adjoint = None
     if args.precision == "fp64" and not args.no_adjoint:
         adjoint = measure_adjoint(args, env, args.adjoint_steps, 1)
@@ -649,15 +896,34 @@ def main():
                 "setup_ms": res["setup_ms"], "roofline": res["roofline"], "e2e": res["e2e"],
                 "gpu_launches": res["gpu_launches"], "clocks": res["clocks"],
                 "status_ok_last_block": res["status_ok_last_block"]}
+        if args.fp64_probe:
+            line["fp64_peak_probe"] = {k: v for k, v in args.fp64_probe.items()}
+        if fp64_legs:
+            line["fp64"] = fp64_legs
         if mixed:
             line["mixed"] = mixed
         if batched:
             line["batched"] = batched
         if adjoint:
             line["adjoint"] = adjoint
+        # CPU work only after every timed GPU leg: the oracle on the host cores
+        factors = {}
         if not args.no_cpu_baseline:
             Xh = np.asfortranarray(pool[0][:4096].cpu().numpy().T)
-            line["cpu_baseline"] = cpu_baseline(cohort, Xh, args.cpu_seconds)
+            line["cpu_baseline"], factors[args.n] = cpu_baseline(cohort, Xh, args.cpu_seconds)
+        if not args.no_oracle_check:
+            from oracle import gls as G
+            for rec, n_chk in sorted(checks, key=lambda c: c[1]):
+                c = cohorts[n_chk]
+                if n_chk not in factors:
+                    t0 = time.perf_counter()
+                    factors[n_chk] = G.factor(c.phi, c.h, c.sigma2)
+                    line.setdefault("oracle_factor_s", {})[str(n_chk)] = round(
+                        time.perf_counter() - t0, 1)
+                rec["oracle_check"] = oracle_errors(factors[n_chk], c, rec["sample"])
+            line["oracle_check"] = res["oracle_check"]
+        for rec in [*fp64_legs, *mixed]:
+            rec.pop("sample", None)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

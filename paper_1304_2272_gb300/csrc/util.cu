@@ -1,4 +1,6 @@
 // Small device utilities of the engine.
+#include <algorithm>
+
 #include "../../include/gwas.h"
 #include "common.cuh"
 #include "kernels.h"
@@ -43,7 +45,94 @@ __global__ void k_wait_selftest(uint64_t limit_ns, int* code, unsigned long long
     }
 }
 
+// FP64 multiply-add throughput probe: every thread runs CHAINS independent chains
+// a <- a * beta + gamma (beta = 1 - 2^-20, gamma = 2^-20, so a stays near 1: no overflow,
+// no subnormals) for iters x 16 steps, then stores its sum so no chain is dead code.
+template <int CHAINS>
+__global__ void __launch_bounds__(256) k_dfma_rate(int iters, double beta, double gamma,
+                                                   double* __restrict__ out) {
+    double a[CHAINS];
+#pragma unroll
+    for (int i = 0; i < CHAINS; ++i) a[i] = 1.0 + 1e-3 * (double)((threadIdx.x + i) & 7);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+#pragma unroll
+            for (int i = 0; i < CHAINS; ++i) a[i] = fma(a[i], beta, gamma);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < CHAINS; ++i) s += a[i];
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <int CHAINS>
+static cudaError_t time_dfma(int blocks, int iters, double* out, cudaEvent_t e0, cudaEvent_t e1,
+                             double* tflops) {
+    const double beta = 1.0 - 1.0 / 1048576.0, gamma = 1.0 / 1048576.0;
+    k_dfma_rate<CHAINS><<<blocks, 256>>>(iters, beta, gamma, out);  // warm-up
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    double best = 0.0;
+    for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0);
+        k_dfma_rate<CHAINS><<<blocks, 256>>>(iters, beta, gamma, out);
+        cudaEventRecord(e1);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+        float ms = 0.f;
+        if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return e;
+        const double flops = 2.0 * 16.0 * CHAINS * (double)iters * blocks * 256.0;
+        if (ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+    }
+    *tflops = best;
+    return cudaGetLastError();
+}
+
 }  // namespace gwas
+
+extern "C" gwas_status gwas_fp64_fma_rate(int device, double* tflops) {
+    if (!tflops) return GWAS_ERR_ARG;
+    *tflops = 0.0;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) return GWAS_ERR_CUDA;
+    int sms = 0;
+    gwas_status st = GWAS_ERR_CUDA;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double* out = nullptr;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
+        cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+        cudaMalloc(&out, sizeof(double) * 256 * 8 * (size_t)sms) == cudaSuccess) {
+        // a few shapes (chains per thread x CTAs per SM), each launch ~0.1-0.2 s at
+        // 1.25 TFLOP/s; the best rate is the FP64 FMA peak this device sustains
+        const int shapes[4][2] = {{8, 2}, {8, 4}, {16, 2}, {4, 8}};
+        double best = 0.0;
+        bool ok = true;
+        for (const auto& sh : shapes) {
+            const int chains = sh[0], blocks = sh[1] * sms;
+            const int iters = (int)(1.5e11 / (2.0 * 16.0 * chains * blocks * 256.0));
+            double r = 0.0;
+            cudaError_t e = chains == 4    ? gwas::time_dfma<4>(blocks, iters, out, e0, e1, &r)
+                            : chains == 8  ? gwas::time_dfma<8>(blocks, iters, out, e0, e1, &r)
+                                           : gwas::time_dfma<16>(blocks, iters, out, e0, e1, &r);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                ok = false;
+                break;
+            }
+            best = std::max(best, r);
+        }
+        if (ok) {
+            *tflops = best;
+            st = GWAS_OK;
+        }
+    }
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (prev >= 0) cudaSetDevice(prev);
+    return st;
+}
 
 extern "C" gwas_status gwas_selftest_wait(int device, int timeout_ms, double* waited_ms) {
     if (timeout_ms < 1 || timeout_ms > 10000) return GWAS_ERR_ARG;

@@ -112,3 +112,52 @@ def test_reference_arm_prints_one_json_line():
         assert k in d
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_host_arrays_are_refused_for_device_arguments():
+    import numpy as np
+    import pytest
+    from paper_1304_2272_gb300 import gwas
+    with pytest.raises(TypeError):
+        gwas._require_dev(np.zeros(8, dtype=np.float64), np.float64, "b")
+
+
+def test_cpu_baseline_flavours_on_a_small_cohort():
+    """The CPU legs on a small cohort: the multithreaded Algorithm 1 route and the three
+    single-threaded flavours (same route, textbook substitution, one process per core
+    over disjoint SNPs), each with its rate and thread count."""
+    import synth
+    c = synth.make_cohort(5, 600, n_markers=300)
+    X = c.snps(64)
+    rec, L = bench.cpu_baseline(c, X, 0.2)
+    assert rec["kind"] == "oracle" and rec["value"] > 0 and rec["cores"] >= 1
+    assert L.shape == (600, 600)
+    names = [f["flavour"] for f in rec["flavours"]]
+    assert names[:3] == ["algorithm1_blas_all_threads", "algorithm1_blas_1_thread",
+                         "plain_row_loop_substitution_1_thread"], rec["flavours"]
+    assert names[3].startswith("processes_over_snps_")
+    for f in rec["flavours"]:
+        assert f["value"] > 0 and f["threads"] >= 1 and f["snps"] > 0
+    assert rec["flavours"][1]["threads"] in (1, None) or rec["flavours"][1]["threads"] == 1
+
+
+def test_oracle_errors_report_a_planted_error():
+    """oracle_errors finds an error planted into otherwise exact outputs, in b and in the
+    Wald statistic, and flags a status that differs."""
+    import numpy as np
+    import synth
+    from oracle import gls as G
+    c = synth.make_cohort(6, 300, n_markers=300)
+    X = c.snps(40)
+    L = G.factor(c.phi, c.h, c.sigma2)
+    b, w, st = G.gls_hoisted(L, c.XL, c.Y, X)
+    sample = {"X": X, "b": b.copy(), "wald": w.copy(), "status": st.copy(), "snps": 40}
+    e = bench.oracle_errors(L, c, sample)
+    assert e["err_b"] == 0.0 and e["err_wald"] == 0.0 and e["status_match"]
+    scale = np.max(np.abs(b[7, 0]))
+    sample["b"][7, 0, 3] += 1e-7 * scale
+    sample["wald"][3, 0] += 1e-6 * max(w[3, 0], 1.0)
+    sample["status"][5] = 1
+    e = bench.oracle_errors(L, c, sample)
+    assert abs(e["err_b"] - 1e-7) < 1e-9 and abs(e["err_wald"] - 1e-6) < 1e-8
+    assert not e["status_match"]

@@ -2,9 +2,11 @@
 
 Tolerance (FP64 path): every coefficient of b_i within 1e-10 of the oracle, relative
 to max_c |b_ic| of the same SNP (the intercept included). The Wald statistic is
-derived from b_i; with |db_p| <= 1e-10 max|b| its error is at most
-2 sqrt(W) C_pp 1e-10 (C_pp = 1/sqrt((S^{-1})_pp), below 1e3 here), so the tests use
-|dW| <= 1e-7 max(W, 1). Status codes must match exactly.
+derived from b_i: to first order its error is 2 sqrt(W) C_pp |db_p| (C_pp =
+1/sqrt((S^{-1})_pp), max|b| C_pp below 1e3 here) plus W times the relative error of
+(S^{-1})_pp. The FP64 path's b is within a few n u (u = 2^-53) of the oracle's, about
+1e-12 at n = 10^4, so the tests hold |dW| <= 1e-10 max(W, 1) (2e3 times that). Status
+codes must match exactly.
 """
 import numpy as np
 import pytest
@@ -16,7 +18,7 @@ from tests.golden.load import load
 pytestmark = pytest.mark.gpu
 
 B_TOL = 1e-10
-W_TOL = 1e-7
+W_TOL = 1e-10
 
 
 def rel_b(b, ref):
@@ -31,8 +33,11 @@ def assert_parity(out, ref):
     ok = rs == 0
     assert np.all(np.isnan(b[~ok])) and np.all(np.isnan(w[~ok]))
     if ok.any():
-        assert rel_b(b[ok], rb[ok]) <= B_TOL
-        assert float(np.max(np.abs(w[ok] - rw[ok]) / np.maximum(rw[ok], 1.0))) <= W_TOL
+        eb = rel_b(b[ok], rb[ok])
+        ew = float(np.max(np.abs(w[ok] - rw[ok]) / np.maximum(rw[ok], 1.0)))
+        print(f"[errors] fp64 {b.shape}: b {eb:.3e} wald {ew:.3e}")
+        assert eb <= B_TOL
+        assert ew <= W_TOL
 
 
 @pytest.fixture(scope="module")

@@ -19,6 +19,16 @@ def rel_b(b, ref):
     return float(np.nanmax(np.abs(b - ref) / scale))
 
 
+def wald_err(w, rw):
+    return float(np.max(np.abs(w - rw) / np.maximum(rw, 1.0)))
+
+
+def wald_tol(limbs, bits):
+    """|dW| / max(W, 1) bound of the mixed path: 2e3 * 2^-(bits * limbs), at least 1e-10
+    (the derivation is in test_parity_mixed.py); FP64 is held to 1e-10."""
+    return 1e-10 if limbs is None else max(2e3 * 2.0 ** (-bits * limbs), 1e-10)
+
+
 @pytest.fixture(scope="module")
 def gw(gpu):
     from paper_1304_2272_gb300 import gwas as g
@@ -52,11 +62,15 @@ def test_beyond_32767_takes_8_bit_limbs(gw, limbs):
     Xs = np.asfortranarray(Xd[idx].cpu().numpy().T)
     rb, rw, rs = G.gls_hoisted(L, c.XL, c.Y, Xs)
     b, s = bd.cpu().numpy()[idx], sd.cpu().numpy()[idx]
+    w = wd.cpu().numpy()[idx]
     np.testing.assert_array_equal(s, rs)
     ok = rs == 0
     err = rel_b(b[ok], rb[ok])
-    print(f"n=33000 mixed x{limbs} (8-bit limbs): max rel b err {err:.2e}")
+    ew = wald_err(w[ok], rw[ok])
+    print(f"[errors] n=33000 mixed x{limbs} (8-bit limbs): max rel b err {err:.2e}, "
+          f"Wald err {ew:.2e}")
     assert err <= (1e-6 if limbs == 3 else 1e-10)
+    assert ew <= wald_tol(limbs, 8)
 
 
 def big33k():
@@ -85,11 +99,14 @@ def test_mixed_at_the_exactness_limit(gw):
     L = G.factor(c.phi, c.h, c.sigma2)
     rb, rw, rs = G.gls_hoisted(L, c.XL, c.Y, Xs)
     b, s = bd.cpu().numpy()[idx], sd.cpu().numpy()[idx]
+    w = wd.cpu().numpy()[idx]
     np.testing.assert_array_equal(s, rs)
     ok = rs == 0
     err = rel_b(b[ok], rb[ok])
-    print(f"n=32767 mixed x3: max rel b err {err:.2e}")
+    ew = wald_err(w[ok], rw[ok])
+    print(f"[errors] n=32767 mixed x3: max rel b err {err:.2e}, Wald err {ew:.2e}")
     assert err <= 1e-6
+    assert ew <= wald_tol(3, 9)
 
 
 @pytest.mark.parametrize("precision,limbs,mb,tol", [
@@ -113,12 +130,15 @@ def test_n30k_sampled(gw, big, precision, limbs, mb, tol):
     Xs = np.asfortranarray(Xd[idx].cpu().numpy().T)
     rb, rw, rs = G.gls_hoisted(L, c.XL, c.Y, Xs)
     b, s = bd.cpu().numpy()[idx], sd.cpu().numpy()[idx]
+    w = wd.cpu().numpy()[idx]
     np.testing.assert_array_equal(s, rs)
     assert s[list(idx).index(17)] == 1
     ok = rs == 0
     err = rel_b(b[ok], rb[ok])
-    print(f"n=30000 {precision} x{limbs}: max rel b err {err:.2e}")
+    ew = wald_err(w[ok], rw[ok])
+    print(f"[errors] n=30000 {precision} x{limbs}: max rel b err {err:.2e}, Wald err {ew:.2e}")
     assert err <= tol
+    assert ew <= wald_tol(None if precision == "fp64" else limbs, 9)
 
 
 def test_mixed_refuses_n_beyond_7_bit_limbs(gw):
