@@ -3,8 +3,12 @@
 ``REMLFunction`` is a ``torch.autograd.Function`` whose forward calls ``gwas_reml`` (FP64
 Cholesky and L^-1 on the GPU) and whose backward returns the adjoint gradient the
 library computed with it, so the REML log-likelihood can be used like any other torch
-objective. ``fit_h`` maximises the profiled likelihood (sigma^2 profiled out) by a
-safeguarded secant iteration on its derivative dl/dh, starting from h0.
+objective. ``GLSFunction`` does the same for the per-SNP estimates: its forward returns
+b_i of Eq. (1) for a block of SNPs at (h, sigma^2), its backward forms the
+vector-Jacobian product sum_i <g_i, db_i/dh> from the library's db_i/dh pass (which
+recomputes M^-1 x_i from the dosages instead of storing Xbar). ``fit_h`` maximises the
+profiled likelihood (sigma^2 profiled out) by a safeguarded secant iteration on its
+derivative dl/dh, starting from h0.
 """
 from __future__ import annotations
 
@@ -34,8 +38,15 @@ class REMLEngine:
 
     def eval(self, h: float, sigma2: float, profile: bool = False) -> dict:
         self.evals += 1
-        return gwas.gwas_reml(self.ctx, self.Phi_dev, h, sigma2, self.XL, self.Y, self.pheno,
-                              profile)
+        r = gwas.gwas_reml(self.ctx, self.Phi_dev, h, sigma2, self.XL, self.Y, self.pheno,
+                           profile)
+        self.state = (float(h), float(sigma2))  # the (h, sigma2) the context is factored at
+        return r
+
+    def at(self, h: float, sigma2: float) -> None:
+        """Make the context hold the factor (and db/dh state) of (h, sigma2)."""
+        if getattr(self, "state", None) != (float(h), float(sigma2)):
+            self.eval(h, sigma2)
 
     def close(self):
         if self.ctx:
@@ -78,6 +89,64 @@ def reml_loglik(h, sigma2, engine):
     if REMLFunction is None:
         REMLFunction = _make_function()
     return REMLFunction.apply(h, sigma2, engine)
+
+
+def _make_gls_function():
+    import torch
+
+    def solve(engine, X, with_grad):
+        m = int(X.shape[0])
+        dev = X.device
+        b = torch.empty((m, engine.t, engine.q + 1), dtype=torch.float64, device=dev)
+        st = torch.empty(m, dtype=torch.uint8, device=dev)
+        if with_grad:
+            d = torch.empty_like(b)
+            gwas.gwas_solve_block_grad_device(engine.ctx, X, m, b, None, st, d)
+        else:
+            d = None
+            gwas.gwas_solve_block_device(engine.ctx, X, m, b, None, st)
+        gwas.gwas_sync(engine.ctx)
+        return b, st, d
+
+    class GLSFunction(torch.autograd.Function):
+        """b_i(h, sigma^2) of a block of SNPs (m x t x p, NaN where status != 0), with
+        db_i/dh from the library's adjoint pass. b does not depend on sigma^2 (scaling M
+        scales S_i^-1 and bbar_i inversely), so its sigma^2 gradient is exactly zero."""
+
+        @staticmethod
+        def forward(ctx, h, sigma2, X, engine):
+            engine.at(float(h), float(sigma2))
+            b, st, _ = solve(engine, X, False)
+            ctx.engine, ctx.hs = engine, (float(h), float(sigma2))
+            ctx.save_for_backward(h, sigma2, X)
+            return b
+
+        @staticmethod
+        def backward(ctx, grad_b):
+            h, sigma2, X = ctx.saved_tensors
+            engine = ctx.engine
+            engine.at(*ctx.hs)  # another evaluation may have moved the context since
+            _, st, d = solve(engine, X, True)
+            ok = (st == 0).view(-1, 1, 1)
+            # chain rule: dL/dh = sum_i <dL/db_i, db_i/dh> over the solved SNPs
+            gh = torch.where(ok, grad_b * d, torch.zeros_like(d)).sum()
+            return (gh.to(device=h.device, dtype=h.dtype).reshape(h.shape),
+                    torch.zeros_like(sigma2), None, None)
+
+    return GLSFunction
+
+
+GLSFunction = None
+
+
+def gls_b(h, sigma2, X, engine):
+    """Differentiable b_i of Eq. (1) for the SNPs of X (a device int8 tensor of shape
+    (m, n), i.e. n x m column-major dosages, m <= the engine's m_blk) at heritability h and
+    scale sigma2 (float64 torch scalars); returns an m x t x p device tensor."""
+    global GLSFunction
+    if GLSFunction is None:
+        GLSFunction = _make_gls_function()
+    return GLSFunction.apply(h, sigma2, X, engine)
 
 
 def fit_h(engine: REMLEngine, h0: float = 0.1, lo: float = 1e-4, hi: float = 1 - 1e-4,
