@@ -17,6 +17,17 @@ struct gwas_batch {
     bool mixed = false;
     std::vector<gwas_ctx*> ctx;
     cudaStream_t s = nullptr;
+    // Mixed batches run in parts (contiguous cohort ranges of about equal tensor work) on
+    // two streams: part k's dosage conversion overlaps part k-1's block kernel, part k-1's
+    // p x p solves overlap part k's block kernel, and part k's CTAs fill the tail of part
+    // k-1's persistent grid.
+    cudaStream_t s2 = nullptr;
+    static constexpr int kMaxParts = 4;
+    int n_parts = 1;
+    int part_c0[kMaxParts + 1] = {};          // cohorts of part k: [part_c0[k], part_c0[k+1])
+    int64_t part_snps[kMaxParts] = {}, part_units[kMaxParts] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_conv[kMaxParts] = {};      // part k's conversion done
     BatchJob* d_jobs = nullptr;
     CohortMx* d_tab = nullptr;
     CUtensorMap* d_maps = nullptr;
@@ -54,6 +65,10 @@ void batch_free(gwas_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto& pr : b->timed) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     cudaFree(b->d_jobs); cudaFree(b->d_tab); cudaFree(b->d_maps); cudaFree(b->d_err);
+    for (cudaEvent_t ev : b->ev_conv) if (ev) cudaEventDestroy(ev);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->s2) cudaStreamDestroy(b->s2);
     if (b->s) cudaStreamDestroy(b->s);
     for (auto* c : b->ctx) gwas_finalize(c);
 }
@@ -72,14 +87,35 @@ void batch_fold_timings(gwas_batch* b, bool wait) {
     b->timed.erase(b->timed.begin(), b->timed.begin() + (std::ptrdiff_t)k);
 }
 
-// Enqueue the batched solve on the batch stream (device tables already current).
+// Enqueue the batched solve on the batch stream (device tables already current). A mixed
+// batch in several parts forks onto the second stream and joins back before returning, so
+// the whole solve stays ordered on b->s (and is captured as one graph).
 gwas_status batch_enqueue(gwas_batch* b) {
     const int nc = b->n_cohorts;
     if (b->mixed) {
-        CKB(launch_geno_bf16_batch(b->d_jobs, nc, b->total_snps, b->s));
-        CKB(launch_block_mixed_batch(b->d_tab, b->d_maps, nc, b->units_mx, b->ctx[0]->mx,
-                                     b->stages, b->d_err, b->ctx[0]->num_sms, b->s));
-        CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, b->p, b->q + 1 + b->t, true, b->s));
+        const int P = b->n_parts;
+        if (P > 1) {
+            CKB(cudaEventRecord(b->ev_fork, b->s));
+            CKB(cudaStreamWaitEvent(b->s2, b->ev_fork, 0));
+        }
+        for (int k = 0; k < P; ++k) {
+            cudaStream_t st = (k % 2 == 0) ? b->s : b->s2;
+            const int c0 = b->part_c0[k], nck = b->part_c0[k + 1] - c0;
+            // the conversions run one after another, each beside the previous part's
+            // block kernel
+            if (k > 0) CKB(cudaStreamWaitEvent(st, b->ev_conv[k - 1], 0));
+            CKB(launch_geno_bf16_batch(b->d_jobs + c0, nck, b->part_snps[k], st));
+            if (P > 1) CKB(cudaEventRecord(b->ev_conv[k], st));
+            CKB(launch_block_mixed_batch(b->d_tab + c0, b->d_maps + 3 * c0, nck, b->part_units[k],
+                                         b->ctx[0]->mx, b->stages, b->d_err, b->ctx[0]->num_sms,
+                                         st));
+            CKB(launch_snp_solve_batch(b->d_jobs + c0, nck, b->part_snps[k], b->p,
+                                       b->q + 1 + b->t, true, st));
+        }
+        if (P > 1) {
+            CKB(cudaEventRecord(b->ev_join, b->s2));
+            CKB(cudaStreamWaitEvent(b->s, b->ev_join, 0));
+        }
     } else {
         CKB(launch_block_fp64_batch(b->d_jobs, nc, b->units_fp64, b->s));
         CKB(launch_snp_solve_batch(b->d_jobs, nc, b->total_snps, b->p, b->q + 1 + b->t, false, b->s));
@@ -105,8 +141,9 @@ gwas_status gwas_batch_init(int n_cohorts, const int64_t* n, int p, int t, const
     b->n_cohorts = n_cohorts;
     b->p = p; b->q = p - 1; b->t = t;
     b->mixed = (o.precision == GWAS_PREC_MIXED);
+    // every cohort takes the same tile configuration, hence the same kernel variant (the
+    // tile height depends on the limb count only, the fusion of the linear rows on p, t)
     gwas_opts oc = o;
-    if (b->mixed) oc.tile_cfg = (o.tile_cfg < 0 ? 0 : (o.tile_cfg & ~(3 << 12))) | (1 << 12);
     for (int c = 0; c < n_cohorts; ++c) {
         gwas_ctx* cx = nullptr;
         const gwas_status st = gwas_init(n[c], p, t, &oc, &cx);
@@ -127,6 +164,16 @@ gwas_status gwas_batch_init(int n_cohorts, const int64_t* n, int p, int t, const
     };
     cudaError_t e;
     if ((e = cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
+    if (b->mixed && n_cohorts > 1) {
+        if ((e = cudaStreamCreateWithFlags(&b->s2, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(e);
+        if ((e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+            return bail(e);
+        for (cudaEvent_t& ev : b->ev_conv)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return bail(e);
+    }
     if ((e = cudaMalloc(&b->d_jobs, sizeof(BatchJob) * n_cohorts)) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&b->d_tab, sizeof(CohortMx) * n_cohorts)) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&b->d_maps, sizeof(CUtensorMap) * 3 * n_cohorts)) != cudaSuccess) return bail(e);
@@ -180,8 +227,36 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
         std::vector<BatchJob> jobs(nc);
         std::vector<CohortMx> tab(nc);
         std::vector<CUtensorMap> maps(3 * nc);
-        int64_t snp = 0, u64 = 0, umx = 0;
+        // parts of about equal tensor work (mixed, two or more cohorts): contiguous cohort
+        // ranges, each with its own SNP and unit numbering
+        int P = 1;
+        b->part_c0[0] = 0;
+        if (b->mixed && nc > 1 && b->s2) {
+            std::vector<int64_t> w(nc);
+            int64_t total = 0;
+            for (int c = 0; c < nc; ++c) total += (w[c] = mixed_cohort_units(b->ctx[c]->mx, mb[c]));
+            P = std::min(nc, 2);
+            int64_t acc = 0;
+            int k = 1;
+            for (int c = 0; c < nc && k < P; ++c) {
+                acc += w[c];
+                // close part k-1 after cohort c once it holds its share of the work, leaving
+                // at least one cohort for every later part
+                if (acc * P >= total * k || nc - (c + 1) == P - k) b->part_c0[k++] = c + 1;
+            }
+        }
+        b->part_c0[P] = nc;
+        b->n_parts = P;
+        int64_t snp = 0, u64 = 0, umx = 0, tot_snps = 0, tot_mx = 0;
+        int part = 0;
         for (int c = 0; c < nc; ++c) {
+            if (c == b->part_c0[part + 1]) {  // a new part: numbering restarts
+                b->part_snps[part] = snp;
+                b->part_units[part] = umx;
+                ++part;
+                snp = 0;
+                umx = 0;
+            }
             gwas_ctx* cx = b->ctx[c];
             BatchJob& j = jobs[c];
             j.c = cohort_view(cx);
@@ -198,13 +273,14 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
             j.wald = wald ? wald[c] : nullptr;
             j.status = status[c];
             snp += mb[c];
+            tot_snps += mb[c];
             if (b->mixed) {
                 j.Xb = cx->mx.Xb;
                 j.n_pad = cx->mx.n_pad;
-                // cohorts given the same dosages (several traits of one cohort, each with
-                // its own M) convert them once and share the BF16 rows and flags
+                // cohorts of one part given the same dosages (several traits of one cohort,
+                // each with its own M) convert them once and share the BF16 rows and flags
                 int src = c;
-                for (int e = 0; e < c; ++e) {
+                for (int e = b->part_c0[part]; e < c; ++e) {
                     if (X[e] == X[c] && mb[e] == mb[c] && b->ctx[e]->n == cx->n &&
                         jobs[e].convert) {
                         j.Xb = jobs[e].Xb;
@@ -219,10 +295,13 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
                 j.n_tiles_mx = cx->mx.n_rt;
                 j.lin_tiles = cx->mx.lin_tiles();
                 tab[c] = mixed_cohort_entry(cx->mx, mb[c], umx);
-                umx += mixed_cohort_units(cx->mx, mb[c]);
+                const int64_t uc = mixed_cohort_units(cx->mx, mb[c]);
+                umx += uc;
+                tot_mx += uc;
                 maps[3 * c + 0] = b->ctx[src]->mx.tmX;
-                maps[3 * c + 1] = cx->mx.tmW;
-                maps[3 * c + 2] = cx->mx.tmE;
+                // CTA pairs: each CTA loads half of a limb tile
+                maps[3 * c + 1] = cx->mx.pair ? cx->mx.tmWh : cx->mx.tmW;
+                maps[3 * c + 2] = cx->mx.pair ? cx->mx.tmEh : cx->mx.tmE;
             } else {
                 u64 += (int64_t)j.n_rt64 * j.n_ct64;
             }
@@ -233,9 +312,11 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
             CKB(cudaMemcpy(b->d_maps, maps.data(), sizeof(CUtensorMap) * 3 * nc,
                            cudaMemcpyHostToDevice));
         }
-        b->total_snps = snp;
+        b->part_snps[part] = snp;
+        b->part_units[part] = umx;
+        b->total_snps = tot_snps;
         b->units_fp64 = u64;
-        b->units_mx = umx;
+        b->units_mx = tot_mx;
         if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
         if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
         b->key = key;
@@ -269,7 +350,7 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
     }
     b->stats.blocks += 1;
     b->stats.snps += b->total_snps;
-    b->stats.kernel_launches += b->mixed ? 4 : 3;
+    b->stats.kernel_launches += b->mixed ? 4 * b->n_parts : 3;
     b->stats.trsm_launches += 1;
     return GWAS_OK;
 }

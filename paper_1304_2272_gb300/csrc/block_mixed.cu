@@ -44,11 +44,9 @@ constexpr int SMEM_BUDGET = 200 * 1024;
 
 // Rows of L^{-1} per tile. One UMMA with M = 128 (or 256 across a CTA pair) takes about
 // the same time for any N <= 256, so the tile is made as tall as S limbs allow:
-// N = R * S close to 256 (one CTA: N a multiple of 16; CTA pair: a multiple of 32).
+// N = R * S close to 256, R a multiple of 16. A CTA pair needs N a multiple of 32: its
+// tile is padded with zero rows (or carries the fused linear rows there) up to N = 256.
 __host__ __device__ constexpr int rows_single(int S) { return (256 / S) & ~15; }
-__host__ __device__ constexpr int rows_pair(int S) {
-    return ((256 / S) & ~15) * S % 32 == 0 ? ((256 / S) & ~15) : ((256 / S) & ~31);
-}
 }  // namespace mx
 
 // Launch-wide values (shared by every cohort of a batch).
@@ -153,7 +151,7 @@ __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32
         const double lo = (double)(unsigned long long)acc;
         const double val = ldexp(fma(hi, 18446744073709551616.0, lo), 2 * (a.E_w[rt] - shift0));
         if (snp < a.mb) a.sq_part[(int64_t)rt * a.ldp + snp] = val;
-        if (NT > R * S) {
+        if (NT > R * S && !a.extra) {
             // fused linear rows: Z limbs of this tile's k-range, one partial per (rt, j)
 #pragma unroll 1
             for (int j = 0; j < R_e; ++j) {
@@ -370,11 +368,10 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
 // accumulator buffer on the even CTA's barrier (8 warp arrivals).
 // In this kernel a.n_ct counts pairs of 128-SNP tiles.
 // ----------------------------------------------------------------------------
-template <int S, int R, int NT>
-__global__ void __launch_bounds__(256, 1)
-k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
-               const __grid_constant__ CUtensorMap tmE, const MixedArgs a) {
+template <int S, int R, int NT, class Src>
+__global__ void __launch_bounds__(256, 1) k_block_mixed2(const __grid_constant__ Src src) {
     using namespace tc;
+    const MixedArgs& a = src.a;
     constexpr int N = NT;
     constexpr int NH = N / 2;
     constexpr uint32_t A_BYTES = mx::BM * mx::BK * 2;
@@ -416,9 +413,9 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         tmem_relinquish2();
     }
     if (warp == 1 && lane == 0) {
-        prefetch_tmap(&tmX);
-        prefetch_tmap(&tmW);
-        prefetch_tmap(&tmE);
+        prefetch_tmap(src.mapX(0));
+        prefetch_tmap(src.mapB(0, false));
+        prefetch_tmap(src.mapB(0, true));
     }
     fence_before_sync();
     __syncthreads();
@@ -439,12 +436,13 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         for (int r = 0; r < rounds && !*abort_flag; ++r) {
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
-            int rt, ctp;
-            decode_unit(a.c, u, rt, ctp);
+            int ci, lu, rt, ctp;
+            const CohortMx& cm = *src.locate(u, ci, lu);
+            decode_unit(cm, lu, rt, ctp);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? a.c.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.c.n_kc_full);
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, cm.n_kc_full);
             const int half = ex ? NeH : NH;
-            const int ybase = (ex ? a.c.n_rt * N : rt * N) + (int)rank * half;
+            const int ybase = (ex ? cm.n_rt * N : rt * N) + (int)rank * half;
             const int ct = 2 * ctp + (int)rank;
             const uint32_t pair_bytes = 2u * (A_BYTES + (uint32_t)half * mx::BK * 2);
             for (int kc = 0; kc < nk; ++kc) {
@@ -454,8 +452,9 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
                 }
                 if (leader) mbar_arrive_expect_tx(&full[stage], pair_bytes);
                 const uint32_t fbar = mapa_shared(smem_u32(&full[stage]), 0);
-                tma_load_2d_pair(sA + stage * A_BYTES, &tmX, kc * mx::BK, ct * mx::BM, fbar);
-                tma_load_2d_pair(sB + stage * B_BYTES, ex ? &tmE : &tmW, kc * mx::BK, ybase, fbar);
+                tma_load_2d_pair(sA + stage * A_BYTES, src.mapX(ci), kc * mx::BK, ct * mx::BM,
+                                 fbar);
+                tma_load_2d_pair(sB + stage * B_BYTES, src.mapB(ci, ex), kc * mx::BK, ybase, fbar);
                 issued[stage] = true;
                 issued_parity[stage] = phase;
                 if (++stage == a.stages) {
@@ -477,10 +476,11 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         for (int r = 0; r < rounds && !*abort_flag; ++r) {
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
-            int rt, ctp;
-            decode_unit(a.c, u, rt, ctp);
+            int ci, lu, rt, ctp;
+            const CohortMx& cm = *src.locate(u, ci, lu);
+            decode_unit(cm, lu, rt, ctp);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? a.c.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, a.c.n_kc_full);
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, cm.n_kc_full);
             if (!mbar_wait(&tempty[abuf], aphase ^ 1, mx::WAIT_NS)) {
                 record_error(a.err, abort_flag, 12);
                 break;
@@ -522,8 +522,9 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         for (int r = 0; r < rounds && !*abort_flag; ++r) {
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
-            int rt, ctp;
-            decode_unit(a.c, u, rt, ctp);
+            int ci, lu, rt, ctp;
+            const CohortMx& cm = *src.locate(u, ci, lu);
+            decode_unit(cm, lu, rt, ctp);
             if (!mbar_wait(&tfull[abuf], aphase, mx::WAIT_NS)) {
                 record_error(a.err, abort_flag, 14);
                 break;
@@ -531,7 +532,7 @@ k_block_mixed2(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             fence_after_sync();
             const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
             const int ct = 2 * ctp + (int)rank;
-            epilogue_unit<S, R, NT>(a.c, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
+            epilogue_unit<S, R, NT>(cm, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[abuf]), 0));
@@ -613,21 +614,14 @@ cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk) 
     // Tile height and kernel variant. When the limb rows of the single-CTA tile leave
     // room for the S x R_e linear rows, they ride in the same UMMA (N = 256, which also
     // suits CTA pairs); otherwise the taller UMMA N wins, CTA pairs on a tie.
-    const int rs = mx::rows_single(S), rp = mx::rows_pair(S);
+    const int rs = mx::rows_single(S);
     m.R_e = R_e;
     m.N_e = mixed_linear_n(S, R_e);
     m.fused = !m.cfg_no_fuse && rs * S < 256 && S * R_e <= 256 - rs * S;
-    if (m.fused) {
-        m.R = rs;
-        m.NT = 256;
-        m.pair = !m.cfg_single_cta;
-    } else {
-        if (m.cfg_single_cta) m.pair = false;
-        else if (m.cfg_pair) m.pair = true;
-        else m.pair = (rp >= rs);
-        m.R = m.pair ? rp : rs;
-        m.NT = m.R * S;
-    }
+    m.R = rs;
+    m.pair = !m.cfg_single_cta;
+    if (m.fused) m.NT = 256;
+    else m.NT = m.pair ? (int)round_up((int64_t)rs * S, 32) : rs * S;
     m.n_rt = (int)ceil_div(n, m.R);
     m.n_pad = round_up(n, 64);
     m.rows_total = (int64_t)m.n_rt * m.NT + (m.fused ? 0 : m.N_e);
@@ -702,14 +696,11 @@ static cudaError_t launch_single_t(const MixedDev& m, int64_t mb, int num_sms, c
     return cudaGetLastError();
 }
 
-template <int S, int R, int NT>
-static cudaError_t launch_pair_t(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
-    static_assert(NT % 32 == 0, "CTA pairs need N a multiple of 32");
-    const MixedArgs a = make_args(m, mb, true);
-    const size_t smem = smem_bytes(NT, m.N_e, true, a.stages);
-    cudaError_t e = cudaFuncSetAttribute(k_block_mixed2<S, R, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+// Persistent launch of the CTA-pair kernel: clusters of 2 CTAs, as many as can be resident
+// at once, at most one per unit.
+template <class Src>
+static cudaError_t launch_clusters(void (*kernel)(Src), const Src& src, size_t smem, int n_units,
+                                   int num_sms, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -724,27 +715,41 @@ static cudaError_t launch_pair_t(const MixedDev& m, int64_t mb, int num_sms, cud
     // as many CTA pairs as can be resident at once (persistent), at most one per unit
     cfg.gridDim = dim3((unsigned)(2 * std::max(1, num_sms / 2)), 1, 1);
     int clusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&clusters, k_block_mixed2<S, R, NT>, &cfg);
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, kernel, &cfg);
     if (e != cudaSuccess) return e;
     if (clusters < 1) return cudaErrorLaunchOutOfResources;
     clusters = std::min(clusters, std::max(1, num_sms / 2));
-    clusters = std::min(clusters, a.n_units);
+    clusters = std::min(clusters, n_units);
     cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
-    e = cudaLaunchKernelEx(&cfg, k_block_mixed2<S, R, NT>, m.tmX, m.tmWh, m.tmEh, a);
+    e = cudaLaunchKernelEx(&cfg, kernel, src);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-// The (S, R, NT) combinations the layout can choose (see mixed_layout).
+template <int S, int R, int NT>
+static cudaError_t launch_pair_t(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
+    static_assert(NT % 32 == 0, "CTA pairs need N a multiple of 32");
+    SrcOne src;
+    src.tmX = m.tmX;
+    src.tmW = m.tmWh;  // each CTA of a pair loads half of the limb tile
+    src.tmE = m.tmEh;
+    src.a = make_args(m, mb, true);
+    const size_t smem = smem_bytes(NT, m.N_e, true, src.a.stages);
+    cudaError_t e = cudaFuncSetAttribute(k_block_mixed2<S, R, NT, SrcOne>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_clusters(k_block_mixed2<S, R, NT, SrcOne>, src, smem, src.a.n_units, num_sms, s);
+}
+
+// The (S, R, NT) combinations the layout can choose (see mixed_layout): R S limb rows,
+// padded (CTA pairs) or filled with fused linear rows up to 256.
 #define GWAS_MIXED_SHAPES(X)                                        \
     X(2, mx::rows_single(2), 2 * mx::rows_single(2))                \
     X(3, mx::rows_single(3), 3 * mx::rows_single(3))                \
     X(3, mx::rows_single(3), 256)                                   \
-    X(3, mx::rows_pair(3), 3 * mx::rows_pair(3))                    \
     X(4, mx::rows_single(4), 4 * mx::rows_single(4))                \
     X(5, mx::rows_single(5), 5 * mx::rows_single(5))                \
-    X(5, mx::rows_single(5), 256)                                   \
-    X(5, mx::rows_pair(5), 5 * mx::rows_pair(5))
+    X(5, mx::rows_single(5), 256)
 
 cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
     if (mb < 1 || mb > m.mb_pad_max) return cudaErrorInvalidValue;
@@ -772,33 +777,41 @@ bool mixed_shape_built(const MixedDev& m) {
 // ---- batched cohorts: one persistent launch over a device table of cohorts ----------
 
 int mixed_stage_count(const MixedDev& m) {
-    int st = stage_count(m.NT, m.N_e, false);
+    int st = stage_count(m.NT, m.N_e, m.pair);
     if (m.cfg_stages >= 2) st = std::min(st, m.cfg_stages);
     return st;
 }
 
 CohortMx mixed_cohort_entry(const MixedDev& m, int64_t mb, int64_t unit_base) {
-    CohortMx c = make_cohort(m, mb, false);
+    CohortMx c = make_cohort(m, mb, m.pair);
     c.unit_base = unit_base;
     return c;
 }
 
 int64_t mixed_cohort_units(const MixedDev& m, int64_t mb) {
-    const CohortMx c = make_cohort(m, mb, false);
+    const CohortMx c = make_cohort(m, mb, m.pair);
     return (int64_t)c.n_ct * (c.n_rt + c.extra);
 }
 
 template <int S, int R, int NT>
-static cudaError_t batch_prepare_t(int N_e, int stages) {
-    const size_t smem = smem_bytes(NT, N_e, false, stages);
+static cudaError_t batch_prepare_t(int N_e, int stages, bool pair) {
+    const size_t smem = smem_bytes(NT, N_e, pair, stages);
+    if (pair) {
+        if constexpr (NT % 32 == 0)
+            return cudaFuncSetAttribute(k_block_mixed2<S, R, NT, SrcBatch>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return cudaErrorInvalidValue;
+    }
     return cudaFuncSetAttribute(k_block_mixed<S, R, NT, SrcBatch>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// One grouped launch over a table of cohorts. The map table holds three maps per cohort:
+// dosages, limb row tiles, linear tile (half-height limb boxes for CTA pairs).
 template <int S, int R, int NT>
 static cudaError_t batch_launch_t(const CohortMx* tab, const CUtensorMap* maps, int n_cohorts,
-                                  int n_units, int R_e, int N_e, int stages, int* err, int num_sms,
-                                  cudaStream_t s) {
+                                  int n_units, int R_e, int N_e, int stages, bool pair, int* err,
+                                  int num_sms, cudaStream_t s) {
     SrcBatch src;
     src.tab = tab;
     src.maps = maps;
@@ -809,15 +822,22 @@ static cudaError_t batch_launch_t(const CohortMx* tab, const CUtensorMap* maps, 
     src.a.stages = stages;
     src.a.n_units = n_units;
     src.a.err = err;
-    const size_t smem = smem_bytes(NT, N_e, false, stages);
+    const size_t smem = smem_bytes(NT, N_e, pair, stages);
+    if (pair) {
+        if constexpr (NT % 32 == 0)
+            return launch_clusters(k_block_mixed2<S, R, NT, SrcBatch>, src, smem, n_units, num_sms,
+                                   s);
+        return cudaErrorInvalidValue;
+    }
     const int grid = std::max(1, std::min(num_sms, n_units));
     k_block_mixed<S, R, NT, SrcBatch><<<grid, 256, smem, s>>>(src);
     return cudaGetLastError();
 }
 
 cudaError_t mixed_batch_prepare(const MixedDev& m, int stages) {
-#define GWAS_TRY(SS, RR, NN) \
-    if (m.S == SS && m.R == RR && m.NT == NN) return batch_prepare_t<SS, RR, NN>(m.N_e, stages);
+#define GWAS_TRY(SS, RR, NN)                                          \
+    if (m.S == SS && m.R == RR && m.NT == NN)                         \
+        return batch_prepare_t<SS, RR, NN>(m.N_e, stages, m.pair);
     GWAS_MIXED_SHAPES(GWAS_TRY)
 #undef GWAS_TRY
     return cudaErrorInvalidValue;
@@ -831,7 +851,7 @@ cudaError_t launch_block_mixed_batch(const CohortMx* tab, const CUtensorMap* map
 #define GWAS_TRY(SS, RR, NN)                                                                   \
     if (m.S == SS && m.R == RR && m.NT == NN)                                                  \
         return batch_launch_t<SS, RR, NN>(tab, maps, n_cohorts, (int)n_units, m.R_e, m.N_e,    \
-                                          stages, err, num_sms, s);
+                                          stages, m.pair, err, num_sms, s);
     GWAS_MIXED_SHAPES(GWAS_TRY)
 #undef GWAS_TRY
     return cudaErrorInvalidValue;

@@ -165,7 +165,8 @@ cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const 
                                    int64_t mb, double* b, double* wald, uint8_t* status,
                                    cudaStream_t s, double* cov = nullptr);
 
-// Batched cohorts (one CTA per 128-SNP tile, tile height rows_single(S)).
+// Batched cohorts: one grouped launch of the layout's kernel variant (CTA pairs over
+// 256-SNP tiles, or one CTA per 128-SNP tile) over a device table of cohorts.
 int mixed_stage_count(const MixedDev& m);
 CohortMx mixed_cohort_entry(const MixedDev& m, int64_t mb, int64_t unit_base);
 int64_t mixed_cohort_units(const MixedDev& m, int64_t mb);

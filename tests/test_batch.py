@@ -14,6 +14,8 @@ from oracle import gls as G
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-10, "mixed": 1e-6}
+# |dW| / max(W, 1): 3 limbs of 9 bits, 2e3 * 2^-27 (the derivation is in test_parity_mixed.py)
+WALD_TOL = {"fp64": 1e-10, "mixed": 1.5e-5}
 
 
 def rel_b(b, ref):
@@ -64,13 +66,21 @@ def run_batch(gw, cohorts, Xs, precision, solves=1, **opts):
     return outs, stats
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+# mixed batches: the CTA-pair kernel (default) or one CTA per 128-SNP tile (tile_cfg bit 12)
+VARIANTS = {"pair": -1, "single": 1 << 12}
+
+
+@pytest.mark.parametrize("precision,variant", [("fp64", "pair"), ("mixed", "pair"),
+                                               ("mixed", "single")])
 @pytest.mark.parametrize("use_graph", [1, 0])
-def test_batch_uneven_cohorts_vs_oracle(gw, precision, use_graph):
+def test_batch_uneven_cohorts_vs_oracle(gw, precision, variant, use_graph):
+    # t = 3: the linear rows (3 x 6 limb rows) do not fit beside the limb rows, so the
+    # separate linear tile and, for CTA pairs, the zero-padded N = 256 limb tile are used
     seeds_n = [(1, 129), (2, 300), (3, 64), (4, 1003), (5, 517)]
     cohorts, Xs = make_batch(seeds_n, t=3, m_of=lambda k: [70, 257, 1, 300, 128][k],
                              h_of=lambda k: 0.2 + 0.15 * k)
-    outs, stats = run_batch(gw, cohorts, Xs, precision, solves=2, use_graph=use_graph)
+    outs, stats = run_batch(gw, cohorts, Xs, precision, solves=2, use_graph=use_graph,
+                            tile_cfg=VARIANTS[variant])
     assert stats["trsm_launches"] == 2
     for (b1, w1, s1), (b2, w2, s2) in zip(outs[0], outs[1]):
         np.testing.assert_array_equal(b1, b2)   # a replayed graph gives the same bits
@@ -80,17 +90,22 @@ def test_batch_uneven_cohorts_vs_oracle(gw, precision, use_graph):
         np.testing.assert_array_equal(s, rs)
         ok = rs == 0
         assert rel_b(b[ok], rb[ok]) <= TOL[precision]
+        assert float(np.max(np.abs(w[ok] - rw[ok]) / np.maximum(rw[ok], 1.0))) <= WALD_TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_matches_single_cohort_bitwise(gw, precision):
+@pytest.mark.parametrize("precision,variant,t", [("fp64", "pair", 2), ("mixed", "pair", 2),
+                                                 ("mixed", "single", 2), ("mixed", "pair", 3),
+                                                 ("mixed", "single", 3)])
+def test_batch_matches_single_cohort_bitwise(gw, precision, variant, t):
+    # t = 2: linear rows fused into the limb tiles; t = 3: a separate linear tile
     seeds_n = [(11, 250), (12, 700), (13, 90)]
-    cohorts, Xs = make_batch(seeds_n, t=2, m_of=lambda k: [333, 129, 64][k])
-    outs, _ = run_batch(gw, cohorts, Xs, precision)
+    cohorts, Xs = make_batch(seeds_n, t=t, m_of=lambda k: [333, 129, 64][k])
+    cfg = VARIANTS[variant]
+    outs, _ = run_batch(gw, cohorts, Xs, precision, tile_cfg=cfg)
     prec = gw.GWAS_PREC_FP64 if precision == "fp64" else gw.GWAS_PREC_MIXED
     for c, X, (b, w, s) in zip(cohorts, Xs, outs[0]):
-        # the batch runs the one-CTA-per-tile variant: force it for the single context
-        with gw.GLS(c.n, 4, c.t, precision=prec, m_blk=X.shape[1], tile_cfg=1 << 12) as e:
+        # a single context with the batch's tile configuration runs the same kernel variant
+        with gw.GLS(c.n, 4, c.t, precision=prec, m_blk=X.shape[1], tile_cfg=cfg) as e:
             e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
             rb, rw, rs = e.solve(X)
         np.testing.assert_array_equal(b, rb)
