@@ -175,13 +175,13 @@ def bf16_flops_per_snp(n: int, q: int, t: int, limbs: int) -> float:
 # DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the bench's own launch shape), valid only
 # while the kernel source is the one captured (code_sha of its file) and, for
-# the limb kernel, per L2 group size (captured with CTA pairs and fused rows; the traffic
-# depends on those, not on the pipeline depth).
+# the limb kernel, per L2 group size and layout (CTA pairs or one CTA, fused or separate
+# linear rows; the traffic does not depend on the pipeline depth).
 TRAFFIC = {
     "k_block_fp64": {"file": "block_fp64.cu", "sha": "f12d054bee8830fb", "n": 10000,
                      "m_blk": 16384, "bytes": 2061468160 + 110667520},
     "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "176da42a48ba3994", "n": 10000,
-                         "m_blk": 16384, "single_cta": False, "no_fuse": False,
+                         "m_blk": 16384, "single_cta": False, "fuse": True,
                          "bytes_by_group_mb": {40: 4036415744 + 81025792,
                                                80: 4554571520 + 79876352,
                                                160: 8137596416 + 76032256}},
@@ -190,13 +190,13 @@ TRAFFIC = {
 
 def tile_cfg_fields(tile_cfg) -> dict:
     """The tile_cfg bit fields as the library reads them (a negative value = defaults)."""
-    d = {"stages": 0, "group_mb": 40, "single_cta": False, "pair": False, "no_fuse": False}
+    d = {"stages": 0, "group_mb": 40, "single_cta": False, "pair": False, "fuse": False}
     if tile_cfg is not None and tile_cfg >= 0:
         d["stages"] = tile_cfg & 0xF
         d["group_mb"] = ((tile_cfg >> 4) & 0xFF) or 40
         d["single_cta"] = bool((tile_cfg >> 12) & 1)
         d["pair"] = bool((tile_cfg >> 13) & 1)
-        d["no_fuse"] = bool((tile_cfg >> 14) & 1)
+        d["fuse"] = bool((tile_cfg >> 17) & 1) and not bool((tile_cfg >> 14) & 1)
     return d
 
 
@@ -212,7 +212,7 @@ def traffic_for(kernel: str, n: int, m_blk: int, tile_cfg=None):
     nbytes = rec.get("bytes")
     if "bytes_by_group_mb" in rec:
         f = tile_cfg_fields(tile_cfg)
-        if any(f[k] != rec[k] for k in ("single_cta", "no_fuse")):
+        if any(f[k] != rec[k] for k in ("single_cta", "fuse")):
             return None
         nbytes = rec["bytes_by_group_mb"].get(f["group_mb"])
     path = os.path.join(ROOT, "paper_1304_2272_gb300", "csrc", rec["file"])
@@ -673,6 +673,14 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True, mb=
                 "kernel": f"k_block_mixed<{limbs}>",
                 "launch_ms": launch_ms, "peak_source": src,
                 "fp64_equivalent_tflops": flops_per_snp(n, q, t) * value / world / 1e12}
+    # the clock effect apart from the kernel's efficiency: launch time x median SM clock
+    # of the timed region, and the rate scaled to the maximum SM clock (compute-bound
+    # kernels run in proportion to the clock)
+    mhz, mhz_max = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    if mhz and mhz_max:
+        roof["launch_ms_x_sm_ghz"] = launch_ms * mhz / 1e3
+        roof["achieved_at_max_clock"] = achieved * mhz_max / mhz
+        roof["frac_at_max_clock"] = roof["achieved_at_max_clock"] / roof["peak"]
     res = {"value": value, "ms_per_step": el_ms / steps, "steps": steps, "warmup": warmup,
            "setup_ms": setup_ms, "roofline": roof, "e2e": e2e, "autotune": tune,
            "gpu_launches": int(stats["kernel_launches"]), "clocks": clk,

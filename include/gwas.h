@@ -78,14 +78,15 @@ typedef struct {
                       keep b within ~1e-8 of FP64, 5 within ~1e-13. n < 131072.        */
     int tile_cfg;  /* -1 = library default; for GWAS_PREC_MIXED, bits 0-3 = pipeline
                       stages (2..8, 0 = as many as fit), bits 4-11 = MB of BF16 dosages
-                      per L2 group of SNP tiles (0 = 40), bit 12 = force one CTA per
-                      128-SNP tile, bit 13 = force CTA pairs (cta_group::2), bit 14 = keep
-                      the linear rows in a separate tile instead of fusing them into
-                      the spare N of every limb tile; by default the linear rows are
-                      fused where they fit and the taller UMMA N wins; bits 15-16 = r
-                      caps the bits per limb at 9 - r (the default takes 9 bits for
-                      n < 32768, 8 for n < 65536, 7 for n < 131072, the most for which
-                      the FP32 sums of limb products stay exact)                        */
+                      per L2 group of SNP tiles (0 = 40), bit 12 = one CTA per 128-SNP
+                      tile instead of CTA pairs (cta_group::2, the default), bit 13 =
+                      CTA pairs, bit 17 = fuse the linear rows into the spare N of every
+                      limb tile (fewer rows of L^{-1} per tile) instead of a separate
+                      linear tile (the default; bit 14 also selects it and overrides
+                      bit 17); bits 15-16 = r caps the bits per limb at 9 - r (the
+                      default takes 9 bits for n < 32768, 8 for n < 65536, 7 for
+                      n < 131072, the most for which the FP32 sums of limb products stay
+                      exact)                                                           */
     int device;    /* CUDA device ordinal                                             */
     int timing;    /* 1 = record CUDA events around each dominant-kernel launch       */
     int use_graph; /* batches: 1 = capture the batched solve in a CUDA graph and
@@ -379,11 +380,11 @@ gwas_status gwas_selftest_wait(int device, int timeout_ms, double* waited_ms);
 /*
  * Measured FP64 multiply-add rate of a device (the paper has no counterpart): the
  * roofline denominator of the FP64 block kernel, which is bound by the FP64 FMA pipe.
- * Times a few shapes of a kernel whose threads run independent chains of dependent
- * FP64 fma (8 or 16 chains per thread, 2-8 CTAs of 256 threads per SM, ~0.1 s per
- * launch, best of two launches after a warm-up) and returns the best rate in *tflops
- * (2 flops per fma). Synchronous, about 1.5 s; allocates a few hundred kB of device
- * memory. Errors: GWAS_ERR_ARG (NULL tflops), GWAS_ERR_CUDA.
+ * Times the block kernel's FP64 inner loop on shared-memory operands alone (256 threads
+ * per CTA, each a 4 x 4 register tile of fma over 16-deep chunks; 2, 4 and 8 CTAs per
+ * SM, ~0.12 s per launch, best of two launches after a warm-up) and returns the best
+ * rate in *tflops (2 flops per fma). Synchronous, about 1.2 s; allocates a few hundred
+ * kB of device memory. Errors: GWAS_ERR_ARG (NULL tflops), GWAS_ERR_CUDA.
  */
 gwas_status gwas_fp64_fma_rate(int device, double* tflops);
 

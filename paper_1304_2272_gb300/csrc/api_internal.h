@@ -61,6 +61,10 @@ struct gwas_ctx {
     int num_sms = 0;
     cudaStream_t s_comp = nullptr, s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_h2d[2] = {}, ev_comp[2] = {}, ev_d2h[2] = {};
+    // mixed path: a block is solved in two halves; the second half's dosage conversion
+    // and the first half's p x p solves run on s_aux beside the other half's block kernel
+    cudaStream_t s_aux = nullptr;
+    cudaEvent_t ev_conv0 = nullptr, ev_conv1 = nullptr, ev_blk0 = nullptr, ev_solve0 = nullptr;
     int slot = 0;
     bool factored = false;
     std::string err;

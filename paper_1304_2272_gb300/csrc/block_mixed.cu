@@ -42,11 +42,13 @@ constexpr uint32_t EXTRA = 0xFFFFu;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int SMEM_BUDGET = 200 * 1024;
 
-// Rows of L^{-1} per tile. One UMMA with M = 128 (or 256 across a CTA pair) takes about
-// the same time for any N <= 256, so the tile is made as tall as S limbs allow:
-// N = R * S close to 256, R a multiple of 16. A CTA pair needs N a multiple of 32: its
-// tile is padded with zero rows (or carries the fused linear rows there) up to N = 256.
-__host__ __device__ constexpr int rows_single(int S) { return (256 / S) & ~15; }
+// Every row tile is one UMMA of N = 256: one UMMA with M = 128 (or 256 across a CTA pair)
+// takes about the same time for any N <= 256, so a tile holds as many rows of L^{-1} as
+// S limbs allow, R = floor(256 / S) (85 for 3 limbs), the S limbs of each row side by
+// side (column i S + l), zero rows up to 256. With the linear rows fused into the tile,
+// R = floor((256 - S R_e) / S).
+constexpr int NT = 256;
+__host__ __device__ constexpr int rows_max(int S) { return NT / S; }
 }  // namespace mx
 
 // Launch-wide values (shared by every cohort of a batch).
@@ -119,9 +121,9 @@ struct SrcBatch {
 
 // Epilogue of one unit for the SNP held in TMEM lane `tb` (one thread = one SNP):
 // row tiles -> sum over the tile's R rows of xbar^2, exact in 128-bit integers, plus (when
-// NT > R*S) the tile's partial linear reductions from the fused columns;
+// the linear rows are fused) the tile's partial linear reductions from the fused columns;
 // the linear tile -> the q + t linear reductions.
-template <int S, int R, int NT>
+template <int S>
 __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32_t tb, int rt,
                                               int64_t snp) {
     using namespace tc;
@@ -129,29 +131,41 @@ __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32
     const int B = a.radix;
     const long long base = 1ll << B;
     const int shift0 = (B - 1) + B * (S - 1);
+    const int R = a.R;
     if (rt != (int)mx::EXTRA) {
         unsigned __int128 acc = 0;
+        // 16 rows at a time: rows i0 .. i0+15 are the 16 S columns from i0 S (a multiple of
+        // 16); a last, shorter group loads ceil(rows S / 16) x 16 columns, which end at or
+        // before column 256 because R S <= 256
 #pragma unroll 1
         for (int i0 = 0; i0 < R; i0 += 16) {
+            const int rows = min(16, R - i0);
+            const int nld = (rows * S + 15) / 16;  // the same for every thread of the warp
             uint32_t v[S][16];
 #pragma unroll
-            for (int l = 0; l < S; ++l) tmem_ld16(tb + (uint32_t)(l * R + i0), v[l]);
+            for (int g = 0; g < S; ++g)
+                if (g < nld) tmem_ld16(tb + (uint32_t)(i0 * S + 16 * g), v[g]);
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                long long T = 0;
+                if (i < rows) {
+                    long long T = 0;
 #pragma unroll
-                for (int l = 0; l < S; ++l)
-                    T = T * base + (long long)__float2int_rn(__uint_as_float(v[l][i]));
-                const unsigned long long uT = (unsigned long long)(T < 0 ? -T : T);
-                acc += (unsigned __int128)uT * uT;
+                    for (int l = 0; l < S; ++l) {
+                        const int col = i * S + l;
+                        T = T * base +
+                            (long long)__float2int_rn(__uint_as_float(v[col / 16][col % 16]));
+                    }
+                    const unsigned long long uT = (unsigned long long)(T < 0 ? -T : T);
+                    acc += (unsigned __int128)uT * uT;
+                }
             }
         }
         const double hi = (double)(unsigned long long)(acc >> 64);
         const double lo = (double)(unsigned long long)acc;
         const double val = ldexp(fma(hi, 18446744073709551616.0, lo), 2 * (a.E_w[rt] - shift0));
         if (snp < a.mb) a.sq_part[(int64_t)rt * a.ldp + snp] = val;
-        if (NT > R * S && !a.extra) {
+        if (!a.extra) {
             // fused linear rows: Z limbs of this tile's k-range, one partial per (rt, j)
 #pragma unroll 1
             for (int j = 0; j < R_e; ++j) {
@@ -183,11 +197,11 @@ __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32
     }
 }
 
-template <int S, int R, int NT, class Src>
+template <int S, class Src>
 __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ Src src) {
     using namespace tc;
     const MixedArgs& a = src.a;
-    constexpr int N = NT;  // UMMA N of a row tile (limb rows + fused linear rows)
+    constexpr int N = mx::NT;  // UMMA N of a row tile (limb rows + fused linear rows)
     constexpr uint32_t A_BYTES = mx::BM * mx::BK * 2;
     const int NB = N > a.N_e ? N : a.N_e;
     const uint32_t B_BYTES = (uint32_t)NB * mx::BK * 2;
@@ -250,7 +264,7 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
             const CohortMx& cm = *src.locate(u, ci, lu);
             decode_unit(cm, lu, rt, ct);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, cm.n_kc_full);
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R + mx::BK - 1) / mx::BK, cm.n_kc_full);
             const int ybase = ex ? cm.n_rt * N : rt * N;
             const uint32_t bytes = A_BYTES + (uint32_t)(ex ? a.N_e : N) * mx::BK * 2;
             for (int kc = 0; kc < nk; ++kc) {
@@ -259,7 +273,8 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
                     break;
                 }
                 mbar_arrive_expect_tx(&full[stage], bytes);
-                tma_load_2d(sA + stage * A_BYTES, src.mapX(ci), kc * mx::BK, ct * mx::BM,
+                tma_load_2d(sA + stage * A_BYTES, src.mapX(ci), kc * mx::BK,
+                            (cm.ct_base + ct) * mx::BM,
                             &full[stage]);
                 tma_load_2d(sB + stage * B_BYTES, src.mapB(ci, ex), kc * mx::BK, ybase,
                             &full[stage]);
@@ -289,7 +304,7 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
             const CohortMx& cm = *src.locate(u, ci, lu);
             decode_unit(cm, lu, rt, ct);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, cm.n_kc_full);
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R + mx::BK - 1) / mx::BK, cm.n_kc_full);
             if (!mbar_wait(&tempty[abuf], aphase ^ 1, mx::WAIT_NS)) {
                 record_error(a.err, abort_flag, 2);
                 break;
@@ -341,7 +356,7 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
             }
             fence_after_sync();
             const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
-            epilogue_unit<S, R, NT>(cm, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
+            epilogue_unit<S>(cm, a.R_e, tb, rt, (int64_t)(cm.ct_base + ct) * mx::BM + qd * 32 + lane);
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[abuf]);
@@ -368,11 +383,11 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
 // accumulator buffer on the even CTA's barrier (8 warp arrivals).
 // In this kernel a.n_ct counts pairs of 128-SNP tiles.
 // ----------------------------------------------------------------------------
-template <int S, int R, int NT, class Src>
+template <int S, class Src>
 __global__ void __launch_bounds__(256, 1) k_block_mixed2(const __grid_constant__ Src src) {
     using namespace tc;
     const MixedArgs& a = src.a;
-    constexpr int N = NT;
+    constexpr int N = mx::NT;
     constexpr int NH = N / 2;
     constexpr uint32_t A_BYTES = mx::BM * mx::BK * 2;
     const int NeH = a.N_e / 2;
@@ -440,10 +455,10 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed2(const __grid_constant__
             const CohortMx& cm = *src.locate(u, ci, lu);
             decode_unit(cm, lu, rt, ctp);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, cm.n_kc_full);
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R + mx::BK - 1) / mx::BK, cm.n_kc_full);
             const int half = ex ? NeH : NH;
             const int ybase = (ex ? cm.n_rt * N : rt * N) + (int)rank * half;
-            const int ct = 2 * ctp + (int)rank;
+            const int ct = cm.ct_base + 2 * ctp + (int)rank;
             const uint32_t pair_bytes = 2u * (A_BYTES + (uint32_t)half * mx::BK * 2);
             for (int kc = 0; kc < nk; ++kc) {
                 if (!mbar_wait(&empty[stage], phase ^ 1, mx::WAIT_NS)) {
@@ -480,7 +495,7 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed2(const __grid_constant__
             const CohortMx& cm = *src.locate(u, ci, lu);
             decode_unit(cm, lu, rt, ctp);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * R + mx::BK - 1) / mx::BK, cm.n_kc_full);
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R + mx::BK - 1) / mx::BK, cm.n_kc_full);
             if (!mbar_wait(&tempty[abuf], aphase ^ 1, mx::WAIT_NS)) {
                 record_error(a.err, abort_flag, 12);
                 break;
@@ -531,8 +546,8 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed2(const __grid_constant__
             }
             fence_after_sync();
             const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
-            const int ct = 2 * ctp + (int)rank;
-            epilogue_unit<S, R, NT>(cm, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
+            const int ct = cm.ct_base + 2 * ctp + (int)rank;
+            epilogue_unit<S>(cm, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
             fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[abuf]), 0));
@@ -596,14 +611,14 @@ size_t smem_bytes(int N, int N_e, bool pair, int stages) {
 
 }  // namespace
 
-// UMMA N of the linear tile: a multiple of 32 (so each CTA of a pair holds whole
-// 8-row swizzle groups of it) and at least 32.
 int mixed_radix(int64_t n) {
     for (int B = 9; B >= 7; --B)
         if (n < (int64_t(1) << (24 - B))) return B;
     return 0;
 }
 
+// UMMA N of the linear tile: a multiple of 32 (so each CTA of a pair holds whole
+// 8-row swizzle groups of it) and at least 32.
 int mixed_linear_n(int S, int R_e) { return (int)std::max<int64_t>(32, round_up((int64_t)S * R_e, 32)); }
 
 cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk) {
@@ -611,17 +626,17 @@ cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk) 
     m.n = n;
     m.radix = mixed_radix(n);
     if (m.cfg_radix > 0 && 9 - m.cfg_radix < m.radix) m.radix = std::max(7, 9 - m.cfg_radix);
-    // Tile height and kernel variant. When the limb rows of the single-CTA tile leave
-    // room for the S x R_e linear rows, they ride in the same UMMA (N = 256, which also
-    // suits CTA pairs); otherwise the taller UMMA N wins, CTA pairs on a tie.
-    const int rs = mx::rows_single(S);
+    // Tile height: as many rows as S limbs fit in N = 256. The S x R_e linear rows go to a
+    // separate tile per SNP tile (N_e columns over every k), or, when asked (tile_cfg bit
+    // 17) and at least 16 rows remain, ride in every row tile on its own k-range at the
+    // cost of R_e fewer rows per tile.
     m.R_e = R_e;
     m.N_e = mixed_linear_n(S, R_e);
-    m.fused = !m.cfg_no_fuse && rs * S < 256 && S * R_e <= 256 - rs * S;
-    m.R = rs;
+    const int r_fused = (mx::NT - S * R_e) / S;
+    m.fused = m.cfg_fuse && r_fused >= 16;
+    m.R = m.fused ? r_fused : mx::rows_max(S);
+    m.NT = mx::NT;
     m.pair = !m.cfg_single_cta;
-    if (m.fused) m.NT = 256;
-    else m.NT = m.pair ? (int)round_up((int64_t)rs * S, 32) : rs * S;
     m.n_rt = (int)ceil_div(n, m.R);
     m.n_pad = round_up(n, 64);
     m.rows_total = (int64_t)m.n_rt * m.NT + (m.fused ? 0 : m.N_e);
@@ -648,10 +663,12 @@ cudaError_t mixed_prepare(MixedDev& m, const double* W, int64_t ldw, const doubl
     return cudaSuccess;
 }
 
-static CohortMx make_cohort(const MixedDev& m, int64_t mb, bool pair) {
+// The cohort constants of a launch over SNPs [snp0, mb) (snp0 a multiple of 256).
+static CohortMx make_cohort(const MixedDev& m, int64_t mb, bool pair, int64_t snp0 = 0) {
     CohortMx c;
     c.n_rt = m.n_rt;
-    c.n_ct = (int)ceil_div(mb, pair ? 2 * mx::BM : mx::BM);  // SNP tiles, or pairs of them
+    c.n_ct = (int)ceil_div(mb - snp0, pair ? 2 * mx::BM : mx::BM);  // SNP tiles, or pairs
+    c.ct_base = (int)(snp0 / mx::BM);
     c.n_kc_full = (int)(m.n_pad / mx::BK);
     const int64_t per_tile = (pair ? 2ll : 1ll) * mx::BM * m.n_pad * 2;  // BF16 dosages
     const int64_t budget = (int64_t)std::max(1, m.cfg_group_mb) << 20;
@@ -661,6 +678,7 @@ static CohortMx make_cohort(const MixedDev& m, int64_t mb, bool pair) {
     c.unit_base = 0;
     c.extra = m.fused ? 0 : 1;
     c.radix = m.radix;
+    c.R = m.R;
     c.E_w = m.E;
     c.E_e = m.E + m.n_rt;
     c.sq_part = m.sq_part;
@@ -668,9 +686,9 @@ static CohortMx make_cohort(const MixedDev& m, int64_t mb, bool pair) {
     return c;
 }
 
-static MixedArgs make_args(const MixedDev& m, int64_t mb, bool pair) {
+static MixedArgs make_args(const MixedDev& m, int64_t mb, bool pair, int64_t snp0) {
     MixedArgs a;
-    a.c = make_cohort(m, mb, pair);
+    a.c = make_cohort(m, mb, pair, snp0);
     a.R_e = m.R_e;
     a.N_e = m.N_e;
     a.stages = stage_count(m.NT, m.N_e, pair);
@@ -680,19 +698,20 @@ static MixedArgs make_args(const MixedDev& m, int64_t mb, bool pair) {
     return a;
 }
 
-template <int S, int R, int NT>
-static cudaError_t launch_single_t(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
+template <int S>
+static cudaError_t launch_single_t(const MixedDev& m, int64_t mb, int64_t snp0, int num_sms,
+                                   cudaStream_t s) {
     SrcOne src;
     src.tmX = m.tmX;
     src.tmW = m.tmW;
     src.tmE = m.tmE;
-    src.a = make_args(m, mb, false);
-    const size_t smem = smem_bytes(NT, m.N_e, false, src.a.stages);
-    cudaError_t e = cudaFuncSetAttribute(k_block_mixed<S, R, NT, SrcOne>,
+    src.a = make_args(m, mb, false, snp0);
+    const size_t smem = smem_bytes(mx::NT, m.N_e, false, src.a.stages);
+    cudaError_t e = cudaFuncSetAttribute(k_block_mixed<S, SrcOne>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = std::max(1, std::min(num_sms, src.a.n_units));
-    k_block_mixed<S, R, NT, SrcOne><<<grid, 256, smem, s>>>(src);
+    k_block_mixed<S, SrcOne><<<grid, 256, smem, s>>>(src);
     return cudaGetLastError();
 }
 
@@ -726,50 +745,42 @@ static cudaError_t launch_clusters(void (*kernel)(Src), const Src& src, size_t s
     return cudaGetLastError();
 }
 
-template <int S, int R, int NT>
-static cudaError_t launch_pair_t(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
-    static_assert(NT % 32 == 0, "CTA pairs need N a multiple of 32");
+template <int S>
+static cudaError_t launch_pair_t(const MixedDev& m, int64_t mb, int64_t snp0, int num_sms,
+                                 cudaStream_t s) {
+    static_assert(mx::NT % 32 == 0, "CTA pairs need N a multiple of 32");
     SrcOne src;
     src.tmX = m.tmX;
     src.tmW = m.tmWh;  // each CTA of a pair loads half of the limb tile
     src.tmE = m.tmEh;
-    src.a = make_args(m, mb, true);
-    const size_t smem = smem_bytes(NT, m.N_e, true, src.a.stages);
-    cudaError_t e = cudaFuncSetAttribute(k_block_mixed2<S, R, NT, SrcOne>,
+    src.a = make_args(m, mb, true, snp0);
+    const size_t smem = smem_bytes(mx::NT, m.N_e, true, src.a.stages);
+    cudaError_t e = cudaFuncSetAttribute(k_block_mixed2<S, SrcOne>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return launch_clusters(k_block_mixed2<S, R, NT, SrcOne>, src, smem, src.a.n_units, num_sms, s);
+    return launch_clusters(k_block_mixed2<S, SrcOne>, src, smem, src.a.n_units, num_sms, s);
 }
 
-// The (S, R, NT) combinations the layout can choose (see mixed_layout): R S limb rows,
-// padded (CTA pairs) or filled with fused linear rows up to 256.
-#define GWAS_MIXED_SHAPES(X)                                        \
-    X(2, mx::rows_single(2), 2 * mx::rows_single(2))                \
-    X(3, mx::rows_single(3), 3 * mx::rows_single(3))                \
-    X(3, mx::rows_single(3), 256)                                   \
-    X(4, mx::rows_single(4), 4 * mx::rows_single(4))                \
-    X(5, mx::rows_single(5), 5 * mx::rows_single(5))                \
-    X(5, mx::rows_single(5), 256)
+// The limb counts a kernel is compiled for (the tile height is a run-time value).
+#define GWAS_MIXED_LIMBS(X) X(2) X(3) X(4) X(5)
 
-cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s) {
-    if (mb < 1 || mb > m.mb_pad_max) return cudaErrorInvalidValue;
-#define GWAS_TRY(SS, RR, NN)                                                                  \
-    if (m.S == SS && m.R == RR && m.NT == NN) {                                               \
-        if (m.pair) {                                                                         \
-            if constexpr ((NN) % 32 == 0) return launch_pair_t<SS, RR, NN>(m, mb, num_sms, s); \
-            return cudaErrorInvalidValue;                                                     \
-        }                                                                                     \
-        return launch_single_t<SS, RR, NN>(m, mb, num_sms, s);                                \
-    }
-    GWAS_MIXED_SHAPES(GWAS_TRY)
+cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s,
+                               int64_t snp0) {
+    if (mb < 1 || mb > m.mb_pad_max || snp0 < 0 || snp0 >= mb || snp0 % (2 * mx::BM) != 0)
+        return cudaErrorInvalidValue;
+#define GWAS_TRY(SS)                                                          \
+    if (m.S == SS)                                                            \
+        return m.pair ? launch_pair_t<SS>(m, mb, snp0, num_sms, s)           \
+                      : launch_single_t<SS>(m, mb, snp0, num_sms, s);
+    GWAS_MIXED_LIMBS(GWAS_TRY)
 #undef GWAS_TRY
     return cudaErrorInvalidValue;
 }
 
 bool mixed_shape_built(const MixedDev& m) {
-#define GWAS_HAS(SS, RR, NN) \
-    if (m.S == SS && m.R == RR && m.NT == NN) return !m.pair || (NN) % 32 == 0;
-    GWAS_MIXED_SHAPES(GWAS_HAS)
+#define GWAS_HAS(SS) \
+    if (m.S == SS) return m.R >= 16 && m.R * SS + (m.fused ? SS * m.R_e : 0) <= mx::NT;
+    GWAS_MIXED_LIMBS(GWAS_HAS)
 #undef GWAS_HAS
     return false;
 }
@@ -793,22 +804,19 @@ int64_t mixed_cohort_units(const MixedDev& m, int64_t mb) {
     return (int64_t)c.n_ct * (c.n_rt + c.extra);
 }
 
-template <int S, int R, int NT>
+template <int S>
 static cudaError_t batch_prepare_t(int N_e, int stages, bool pair) {
-    const size_t smem = smem_bytes(NT, N_e, pair, stages);
-    if (pair) {
-        if constexpr (NT % 32 == 0)
-            return cudaFuncSetAttribute(k_block_mixed2<S, R, NT, SrcBatch>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        return cudaErrorInvalidValue;
-    }
-    return cudaFuncSetAttribute(k_block_mixed<S, R, NT, SrcBatch>,
+    const size_t smem = smem_bytes(mx::NT, N_e, pair, stages);
+    if (pair)
+        return cudaFuncSetAttribute(k_block_mixed2<S, SrcBatch>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_block_mixed<S, SrcBatch>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 // One grouped launch over a table of cohorts. The map table holds three maps per cohort:
 // dosages, limb row tiles, linear tile (half-height limb boxes for CTA pairs).
-template <int S, int R, int NT>
+template <int S>
 static cudaError_t batch_launch_t(const CohortMx* tab, const CUtensorMap* maps, int n_cohorts,
                                   int n_units, int R_e, int N_e, int stages, bool pair, int* err,
                                   int num_sms, cudaStream_t s) {
@@ -822,23 +830,17 @@ static cudaError_t batch_launch_t(const CohortMx* tab, const CUtensorMap* maps, 
     src.a.stages = stages;
     src.a.n_units = n_units;
     src.a.err = err;
-    const size_t smem = smem_bytes(NT, N_e, pair, stages);
-    if (pair) {
-        if constexpr (NT % 32 == 0)
-            return launch_clusters(k_block_mixed2<S, R, NT, SrcBatch>, src, smem, n_units, num_sms,
-                                   s);
-        return cudaErrorInvalidValue;
-    }
+    const size_t smem = smem_bytes(mx::NT, N_e, pair, stages);
+    if (pair) return launch_clusters(k_block_mixed2<S, SrcBatch>, src, smem, n_units, num_sms, s);
     const int grid = std::max(1, std::min(num_sms, n_units));
-    k_block_mixed<S, R, NT, SrcBatch><<<grid, 256, smem, s>>>(src);
+    k_block_mixed<S, SrcBatch><<<grid, 256, smem, s>>>(src);
     return cudaGetLastError();
 }
 
 cudaError_t mixed_batch_prepare(const MixedDev& m, int stages) {
-#define GWAS_TRY(SS, RR, NN)                                          \
-    if (m.S == SS && m.R == RR && m.NT == NN)                         \
-        return batch_prepare_t<SS, RR, NN>(m.N_e, stages, m.pair);
-    GWAS_MIXED_SHAPES(GWAS_TRY)
+#define GWAS_TRY(SS) \
+    if (m.S == SS) return batch_prepare_t<SS>(m.N_e, stages, m.pair);
+    GWAS_MIXED_LIMBS(GWAS_TRY)
 #undef GWAS_TRY
     return cudaErrorInvalidValue;
 }
@@ -848,11 +850,11 @@ cudaError_t launch_block_mixed_batch(const CohortMx* tab, const CUtensorMap* map
                                      int num_sms, cudaStream_t s) {
     if (n_units <= 0) return cudaSuccess;
     if (n_units > 0x7fffffffLL) return cudaErrorInvalidValue;
-#define GWAS_TRY(SS, RR, NN)                                                                   \
-    if (m.S == SS && m.R == RR && m.NT == NN)                                                  \
-        return batch_launch_t<SS, RR, NN>(tab, maps, n_cohorts, (int)n_units, m.R_e, m.N_e,    \
-                                          stages, m.pair, err, num_sms, s);
-    GWAS_MIXED_SHAPES(GWAS_TRY)
+#define GWAS_TRY(SS)                                                                     \
+    if (m.S == SS)                                                                       \
+        return batch_launch_t<SS>(tab, maps, n_cohorts, (int)n_units, m.R_e, m.N_e, stages, \
+                                  m.pair, err, num_sms, s);
+    GWAS_MIXED_LIMBS(GWAS_TRY)
 #undef GWAS_TRY
     return cudaErrorInvalidValue;
 }

@@ -69,16 +69,29 @@ gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, doubl
         e1 = pooled_event(c);
         CK(cudaEventRecord(e0, c->s_comp));
     }
+    // mixed blocks of 1024 SNPs or more go in two halves [0, h) and [h, mb) (h a multiple
+    // of 256): s_comp runs conversion(0) -> block(0) -> block(1) -> solves(1), s_aux runs
+    // conversion(1) beside block(0) and solves(0) beside block(1); s_comp waits for s_aux
+    // before the call returns, so the block stays ordered on the context's stream
+    const int64_t h = (c->mixed && c->s_aux && mb >= 1024) ? round_up(ceil_div(mb, 2), 256) : mb;
+    const bool split = h < mb;
     if (c->mixed) {
         // the dosage conversion runs before the timed region of the dominant kernel
-        if (c->opts.timing) {
-            CK(cudaEventRecord(e1, c->s_comp));
-            CK(launch_geno_bf16(c->mx, X, c->n, mb, c->bad, c->s_comp));
-            CK(cudaEventRecord(e0, c->s_comp));
-        } else {
-            CK(launch_geno_bf16(c->mx, X, c->n, mb, c->bad, c->s_comp));
+        if (c->opts.timing) CK(cudaEventRecord(e1, c->s_comp));
+        CK(launch_geno_bf16(c->mx, X, c->n, h, c->bad, c->s_comp));
+        if (split) {
+            CK(cudaEventRecord(c->ev_conv0, c->s_comp));
+            CK(cudaStreamWaitEvent(c->s_aux, c->ev_conv0, 0));
+            CK(launch_geno_bf16(c->mx, X, c->n, mb, c->bad, c->s_aux, h));
+            CK(cudaEventRecord(c->ev_conv1, c->s_aux));
         }
-        CK(launch_block_mixed(c->mx, mb, c->num_sms, c->s_comp));
+        if (c->opts.timing) CK(cudaEventRecord(e0, c->s_comp));
+        CK(launch_block_mixed(c->mx, h, c->num_sms, c->s_comp));
+        if (split) {
+            CK(cudaEventRecord(c->ev_blk0, c->s_comp));
+            CK(cudaStreamWaitEvent(c->s_comp, c->ev_conv1, 0));
+            CK(launch_block_mixed(c->mx, mb, c->num_sms, c->s_comp, h));
+        }
     } else {
         CK(launch_block_fp64(cv, X, c->n, mb, c->part, c->ldp, c->bad, c->s_comp));
     }
@@ -87,8 +100,17 @@ gwas_status run_block(gwas_ctx* c, const int8_t* X, int64_t mb, double* b, doubl
         c->timed.emplace_back(e0, e1);
     }
     if (c->mixed) {
-        CK(launch_snp_solve_mixed(cv, c->mx, c->bad, mb, b, wald, status, c->s_comp, cov));
-        c->stats.kernel_launches += 2;
+        if (split) {
+            CK(cudaStreamWaitEvent(c->s_aux, c->ev_blk0, 0));
+            CK(launch_snp_solve_mixed(cv, c->mx, c->bad, h, b, wald, status, c->s_aux, cov));
+            CK(cudaEventRecord(c->ev_solve0, c->s_aux));
+            CK(launch_snp_solve_mixed(cv, c->mx, c->bad, mb, b, wald, status, c->s_comp, cov, h));
+            CK(cudaStreamWaitEvent(c->s_comp, c->ev_solve0, 0));
+            c->stats.kernel_launches += 6;  // a second conversion, block kernel and solve
+        } else {
+            CK(launch_snp_solve_mixed(cv, c->mx, c->bad, mb, b, wald, status, c->s_comp, cov));
+            c->stats.kernel_launches += 2;
+        }
     } else {
         CK(launch_snp_solve(cv, c->part, c->ldp, (int)ceil_div(c->n, T64), c->bad, mb, b, wald,
                             status, c->s_comp, cov));
@@ -106,7 +128,7 @@ void apply_tile_cfg(MixedDev& m, int tile_cfg) {
     m.cfg_group_mb = 40;
     m.cfg_single_cta = false;
     m.cfg_pair = false;
-    m.cfg_no_fuse = false;
+    m.cfg_fuse = false;
     m.cfg_radix = 0;
     if (tile_cfg >= 0) {
         m.cfg_stages = tile_cfg & 0xF;
@@ -114,7 +136,9 @@ void apply_tile_cfg(MixedDev& m, int tile_cfg) {
         if (g > 0) m.cfg_group_mb = g;
         m.cfg_single_cta = ((tile_cfg >> 12) & 1) != 0;
         m.cfg_pair = ((tile_cfg >> 13) & 1) != 0;
-        m.cfg_no_fuse = ((tile_cfg >> 14) & 1) != 0;
+        // bit 17 fuses the linear rows into the limb tiles; bit 14 (a separate linear
+        // tile, the default) takes precedence
+        m.cfg_fuse = ((tile_cfg >> 17) & 1) != 0 && ((tile_cfg >> 14) & 1) == 0;
         m.cfg_radix = (tile_cfg >> 15) & 3;
     }
 }
@@ -149,6 +173,9 @@ void free_all(gwas_ctx* c) {
     for (auto& pr : c->timed) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto e : c->done_ev) cudaEventDestroy(e);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t ev : {c->ev_conv0, c->ev_conv1, c->ev_blk0, c->ev_solve0})
+        if (ev) cudaEventDestroy(ev);
+    if (c->s_aux) cudaStreamDestroy(c->s_aux);
     if (c->s_comp) cudaStreamDestroy(c->s_comp);
     if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
     if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
@@ -191,8 +218,8 @@ gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx**
     if (o.precision == GWAS_PREC_MIXED) {
         // exact FP32 accumulation of integer limb products needs n 2^B < 2^24 with B >= 7
         // bits per limb (n < 2^17); the linear tile must fit one UMMA (N <= 256); with 5
-        // limbs of 9 bits the recombined value stays below 2^61 and a tile's sum of R <= 48
-        // squares below 2^126 (int64, int128)
+        // limbs of 9 bits the recombined value stays below 2^61 and a tile's sum of
+        // R <= 51 squares below 2^126 (int64, unsigned int128)
         if (o.n_limbs < 2 || o.n_limbs > 5 || mixed_radix(n) == 0 ||
             o.n_limbs * ((p - 1) + t) > 256)
             return GWAS_ERR_UNSUPPORTED;
@@ -255,6 +282,11 @@ gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx**
         CKI(cudaEventCreateWithFlags(&c->ev_d2h[s], cudaEventDisableTiming));
     }
     CKI(cudaStreamCreateWithFlags(&c->s_comp, cudaStreamNonBlocking));
+    if (c->mixed) {
+        CKI(cudaStreamCreateWithFlags(&c->s_aux, cudaStreamNonBlocking));
+        for (cudaEvent_t* ev : {&c->ev_conv0, &c->ev_conv1, &c->ev_blk0, &c->ev_solve0})
+            CKI(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    }
     CKI(cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking));
     CKI(cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking));
 #undef CKI
@@ -685,7 +717,7 @@ gwas_status gwas_autotune(gwas_ctx* c, const int8_t* X, int64_t mb_max, int reps
     if (c->mixed) {
         // a radix cap set by the caller (tile_cfg bits 15-16) is kept
         const int keep = c->opts.tile_cfg >= 0 ? (c->opts.tile_cfg & (3 << 15)) : 0;
-        for (int variant : {1 << 12, 1 << 13, (1 << 14) | (1 << 12), (1 << 14) | (1 << 13)})
+        for (int variant : {1 << 12, 1 << 13, (1 << 17) | (1 << 12), (1 << 17) | (1 << 13)})
             for (int group : {40, 80, 160})
                 for (int stages : {0, 4}) cfgs.push_back(keep | variant | (group << 4) | stages);
     } else {
@@ -759,6 +791,21 @@ gwas_status gwas_autotune(gwas_ctx* c, const int8_t* X, int64_t mb_max, int reps
             best = v;
             best_cfg = coarse[k].cfg;
             best_mb = coarse[k].mb;
+        }
+    }
+    // Short timings run below the power cap and do not see the power that DRAM traffic
+    // costs in a long run; larger L2 groups of SNP tiles re-read more dosages (n = 10k:
+    // 3.9 GB per block with 40 MB groups, 7.9 GB with 160 MB at equal short-run time). So
+    // among the candidates within 1 % of the fastest, the one with the smallest group wins.
+    if (c->mixed && coarse.size() > 1) {
+        const double best_time = best;
+        auto group_of = [](int cfg) { return ((cfg >> 4) & 0xFF) ? ((cfg >> 4) & 0xFF) : 40; };
+        for (size_t k = 0; k < coarse.size(); ++k) {
+            if (fine[k] <= 1.01 * best_time && group_of(coarse[k].cfg) < group_of(best_cfg)) {
+                best = fine[k];
+                best_cfg = coarse[k].cfg;
+                best_mb = coarse[k].mb;
+            }
         }
     }
     c->ev_pool.push_back(e0);

@@ -100,6 +100,8 @@ struct CohortMx {
     int64_t unit_base;  // first unit of this cohort in a batched launch
     int extra;          // 1: a separate linear tile per SNP tile; 0: linear rows fused
     int radix;          // bits per limb B: limbs in [-2^(B-1), 2^(B-1)]
+    int R;              // rows of L^{-1} per row tile (limb i, l in column i*S + l)
+    int ct_base;        // first 128-SNP tile of the launch (its SNPs start at 128 ct_base)
     const int* E_w;     // exponent per row tile
     const int* E_e;     // exponent per linear row (fused: per (row tile, linear row))
     double* sq_part;    // [n_rt][ldp]
@@ -111,8 +113,9 @@ struct MixedDev {
     int S = 3;                  // BF16 limbs per element of L^{-1} and Z
     int radix = 9;              // bits per limb: 9 for n < 2^15, 8 for n < 2^16, 7 for n < 2^17
     int64_t n = 0;
-    int R = 64;                 // rows of L^{-1} per tile
-    int NT = 256;               // UMMA N (limb rows, plus fused linear rows) of a row tile
+    int R = 64;                 // rows of L^{-1} per tile (S R <= 256)
+    int NT = 256;               // UMMA N of a row tile: its S R limb rows (row i's limbs
+                                // side by side), fused linear rows, zero rows up to 256
     bool fused = false;         // linear rows ride in the spare N of every row tile
     bool pair = true;           // CTA-pair kernel (cta_group::2) instead of one CTA per tile
     int n_rt = 0;               // R-row tiles of L^{-1}
@@ -133,7 +136,7 @@ struct MixedDev {
     int cfg_group_mb = 40;      // MB of BF16 dosages per L2 group of SNP tiles
     bool cfg_single_cta = false;  // force one CTA per 128-SNP tile
     bool cfg_pair = false;        // force CTA pairs
-    bool cfg_no_fuse = false;     // keep the linear rows in a separate tile
+    bool cfg_fuse = false;        // fuse the linear rows into the limb tiles (lower R)
     int cfg_radix = 0;            // bits per limb at most 9 - cfg_radix (tile_cfg bits 15-16)
     int lin_tiles() const { return fused ? n_rt : 1; }
     int n_exp() const { return n_rt + (fused ? n_rt * R_e : R_e); }
@@ -155,15 +158,19 @@ cudaError_t launch_limb_split(MixedDev& m, const double* W, int64_t ldw, const d
 // launch_limb_split, then the tensor maps over m's buffers.
 cudaError_t mixed_prepare(MixedDev& m, const double* W, int64_t ldw, const double* Z,
                           cudaStream_t s, int64_t* launches);
-// Dosages (n x mb int8, column-major) -> BF16 rows of m.Xb and bad-dosage flags (limbs.cu).
+// Dosages of SNPs [snp0, mb) (n x mb int8, column-major) -> BF16 rows of m.Xb and their
+// bad-dosage flags (limbs.cu).
 cudaError_t launch_geno_bf16(const MixedDev& m, const int8_t* X, int64_t ldx, int64_t mb,
-                             uint8_t* bad, cudaStream_t s);
-// The tcgen05 kernel: row-tile partials of S_BRi into m.sq_part, S_BLi / bbar_Bi into m.lin.
-cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s);
-// p x p solves from the mixed partial layout.
+                             uint8_t* bad, cudaStream_t s, int64_t snp0 = 0);
+// The tcgen05 kernel over SNPs [snp0, mb) (snp0 a multiple of 256): row-tile partials of
+// S_BRi into m.sq_part, S_BLi / bbar_Bi into m.lin (columns snp0 .. mb-1).
+cudaError_t launch_block_mixed(const MixedDev& m, int64_t mb, int num_sms, cudaStream_t s,
+                               int64_t snp0 = 0);
+// p x p solves of SNPs [snp0, mb) from the mixed partial layout (b, wald, status, cov and
+// bad index SNPs of the whole block).
 cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const uint8_t* bad,
                                    int64_t mb, double* b, double* wald, uint8_t* status,
-                                   cudaStream_t s, double* cov = nullptr);
+                                   cudaStream_t s, double* cov = nullptr, int64_t snp0 = 0);
 
 // Batched cohorts: one grouped launch of the layout's kernel variant (CTA pairs over
 // 256-SNP tiles, or one CTA per 128-SNP tile) over a device table of cohorts.

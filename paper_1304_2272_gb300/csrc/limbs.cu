@@ -199,8 +199,8 @@ __device__ __forceinline__ void split_limbs(double w, int E, int B, uint16_t (&o
     }
 }
 
-// Lower triangle of W (column-major) -> limb rows rt*NT + l*R + i of WL (k contiguous),
-// R rows of L^{-1} per tile, row tiles NT rows apart.
+// Lower triangle of W (column-major) -> limb rows rt*NT + i*S + l of WL (k contiguous):
+// R rows of L^{-1} per tile, the S limbs of row i side by side, row tiles NT rows apart.
 template <int S>
 __global__ void __launch_bounds__(256)
 k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int NT, int B,
@@ -222,7 +222,7 @@ k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int NT, i
         uint16_t limbs[S];
         split_limbs<S>(tile[tx][j], E_w[rt], B, limbs);
 #pragma unroll
-        for (int l = 0; l < S; ++l) WL[(rt * N + (int64_t)l * R + i) * n_pad + k] = limbs[l];
+        for (int l = 0; l < S; ++l) WL[(rt * N + i * S + l) * n_pad + k] = limbs[l];
     }
 }
 
@@ -318,9 +318,12 @@ cudaError_t launch_limb_split(MixedDev& m, const double* W, int64_t ldw, const d
 }
 
 cudaError_t launch_geno_bf16(const MixedDev& m, const int8_t* X, int64_t ldx, int64_t mb,
-                             uint8_t* bad, cudaStream_t s) {
-    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(mb, GENO_WARPS), 1 << 20);
-    k_geno_bf16<<<grid, GENO_WARPS * 32, 0, s>>>(X, ldx, m.n, mb, m.Xb, m.n_pad, bad);
+                             uint8_t* bad, cudaStream_t s, int64_t snp0) {
+    const int64_t count = mb - snp0;
+    if (count <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(count, GENO_WARPS), 1 << 20);
+    k_geno_bf16<<<grid, GENO_WARPS * 32, 0, s>>>(X + snp0 * ldx, ldx, m.n, count,
+                                                 m.Xb + snp0 * m.n_pad, m.n_pad, bad + snp0);
     return cudaGetLastError();
 }
 

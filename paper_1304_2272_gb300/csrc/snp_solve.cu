@@ -310,14 +310,19 @@ cudaError_t launch_snp_solve_batch(const BatchJob* jobs, int n_jobs, int64_t n_s
 
 cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const uint8_t* bad,
                                    int64_t mb, double* b, double* wald, uint8_t* status,
-                                   cudaStream_t s, double* cov) {
-    if (mb <= 0) return cudaSuccess;
-    const int q = c.q;
-    cudaError_t e = reduce_partials(RedMixed{m.sq_part, m.lin, m.ldp, m.n_rt, q, m.lin_tiles(), m.R_e},
-                                    n_red(c), mb, s);
+                                   cudaStream_t s, double* cov, int64_t snp0) {
+    const int64_t count = mb - snp0;
+    if (count <= 0) return cudaSuccess;
+    const int q = c.q, p = q + 1;
+    // SNPs snp0 .. mb-1: their partials are columns snp0 .. of every partial row
+    double* sq = m.sq_part + snp0;
+    double* lin = m.lin + snp0;
+    cudaError_t e = reduce_partials(RedMixed{sq, lin, m.ldp, m.n_rt, q, m.lin_tiles(), m.R_e},
+                                    n_red(c), count, s);
     if (e != cudaSuccess) return e;
-    return launch_solve(c, RedMixed{m.sq_part, m.lin, m.ldp, 1, q, 1, m.R_e}, bad, mb, b, wald,
-                        status, cov, s);
+    return launch_solve(c, RedMixed{sq, lin, m.ldp, 1, q, 1, m.R_e}, bad + snp0, count,
+                        b + snp0 * c.t * p, wald ? wald + snp0 * c.t : nullptr, status + snp0,
+                        cov ? cov + snp0 * p * p : nullptr, s);
 }
 
 }  // namespace gwas

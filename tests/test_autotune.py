@@ -26,8 +26,9 @@ def test_set_tile_cfg_resplits_and_keeps_parity(gw):
     ref = G.gls(c.phi, c.h, c.sigma2, c.XL, c.Y, X)
     with gw.GLS(c.n, 4, 1, precision=gw.GWAS_PREC_MIXED, n_limbs=3, m_blk=1024) as e:
         e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
-        for cfg in (1 << 13, 1 << 12, (1 << 12) | (20 << 4) | 3, -1):
-            gw.gwas_set_tile_cfg(e.ctx, cfg)   # pair (64 rows) <-> single (80 rows)
+        # pair <-> single, separate <-> fused linear rows (85 <-> 81 rows per tile)
+        for cfg in (1 << 13, 1 << 12, (1 << 12) | (20 << 4) | 3, (1 << 17) | (1 << 13), -1):
+            gw.gwas_set_tile_cfg(e.ctx, cfg)
             b, w, s = e.solve(X)
             np.testing.assert_array_equal(s, ref[2])
             assert rel_b(b, ref[0]) <= 1e-6

@@ -66,16 +66,16 @@ def run_batch(gw, cohorts, Xs, precision, solves=1, **opts):
     return outs, stats
 
 
-# mixed batches: the CTA-pair kernel (default) or one CTA per 128-SNP tile (tile_cfg bit 12)
-VARIANTS = {"pair": -1, "single": 1 << 12}
+# mixed batches: the CTA-pair kernel (default) or one CTA per 128-SNP tile (tile_cfg bit 12);
+# a separate linear tile (default) or linear rows fused into the limb tiles (bit 17)
+VARIANTS = {"pair": -1, "single": 1 << 12, "pair_fused": 1 << 17,
+            "single_fused": (1 << 17) | (1 << 12)}
 
 
 @pytest.mark.parametrize("precision,variant", [("fp64", "pair"), ("mixed", "pair"),
                                                ("mixed", "single")])
 @pytest.mark.parametrize("use_graph", [1, 0])
 def test_batch_uneven_cohorts_vs_oracle(gw, precision, variant, use_graph):
-    # t = 3: the linear rows (3 x 6 limb rows) do not fit beside the limb rows, so the
-    # separate linear tile and, for CTA pairs, the zero-padded N = 256 limb tile are used
     seeds_n = [(1, 129), (2, 300), (3, 64), (4, 1003), (5, 517)]
     cohorts, Xs = make_batch(seeds_n, t=3, m_of=lambda k: [70, 257, 1, 300, 128][k],
                              h_of=lambda k: 0.2 + 0.15 * k)
@@ -94,10 +94,9 @@ def test_batch_uneven_cohorts_vs_oracle(gw, precision, variant, use_graph):
 
 
 @pytest.mark.parametrize("precision,variant,t", [("fp64", "pair", 2), ("mixed", "pair", 2),
-                                                 ("mixed", "single", 2), ("mixed", "pair", 3),
-                                                 ("mixed", "single", 3)])
+                                                 ("mixed", "single", 3), ("mixed", "pair_fused", 2),
+                                                 ("mixed", "single_fused", 3)])
 def test_batch_matches_single_cohort_bitwise(gw, precision, variant, t):
-    # t = 2: linear rows fused into the limb tiles; t = 3: a separate linear tile
     seeds_n = [(11, 250), (12, 700), (13, 90)]
     cohorts, Xs = make_batch(seeds_n, t=t, m_of=lambda k: [333, 129, 64][k])
     cfg = VARIANTS[variant]

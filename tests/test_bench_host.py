@@ -13,9 +13,10 @@ def test_tile_cfg_fields_match_the_bit_layout():
     assert bench.tile_cfg_fields(None) == bench.tile_cfg_fields(-1)
     d = bench.tile_cfg_fields(8832)           # pair forced, group 40 MB, stages auto
     assert d == {"stages": 0, "group_mb": 40, "single_cta": False, "pair": True,
-                 "no_fuse": False}
-    d = bench.tile_cfg_fields(4 | (160 << 4) | (1 << 12) | (1 << 14))
-    assert d["stages"] == 4 and d["group_mb"] == 160 and d["single_cta"] and d["no_fuse"]
+                 "fuse": False}
+    d = bench.tile_cfg_fields(4 | (160 << 4) | (1 << 12) | (1 << 17))
+    assert d["stages"] == 4 and d["group_mb"] == 160 and d["single_cta"] and d["fuse"]
+    assert not bench.tile_cfg_fields((1 << 17) | (1 << 14))["fuse"]   # bit 14 wins
     assert bench.tile_cfg_fields(0)["group_mb"] == 40   # group 0 = the default
 
 
@@ -28,11 +29,12 @@ def test_traffic_guard_rejects_other_shapes_and_groupings():
     assert bench.traffic_for("k_block_mixed<3>", n, mb, 1 << 12) is None
     assert bench.traffic_for("k_block_mixed<9>", n, mb) is None
     for g in (40, 80, 160):
-        got = bench.traffic_for("k_block_mixed<3>", n, mb, (1 << 13) | (g << 4))
+        got = bench.traffic_for("k_block_mixed<3>", n, mb, (1 << 13) | (g << 4) | (rec["fuse"] << 17))
         # None once the kernel source changes
         assert got is None or got == rec["bytes_by_group_mb"][g]
-    assert bench.traffic_for("k_block_mixed<3>", n, mb, 8832) == \
-        bench.traffic_for("k_block_mixed<3>", n, mb, -1)
+    fused = rec["fuse"] << 17
+    assert bench.traffic_for("k_block_mixed<3>", n, mb, 8832 | fused) == \
+        bench.traffic_for("k_block_mixed<3>", n, mb, (1 << 13) | fused)
 
 
 def test_pack_2bit_layout():

@@ -30,10 +30,10 @@ def wald_tol(limbs, bits=9):
 
 
 WALD_TOL = {s: wald_tol(s) for s in (2, 3, 4, 5)}
-# tile_cfg bits: 12 forces one CTA per 128-SNP tile, 13 forces CTA pairs (cta_group::2)
-# 14 keeps the linear rows in a separate tile (no fusion into the limb tiles)
+# tile_cfg bits: 12 forces one CTA per 128-SNP tile, 13 forces CTA pairs (cta_group::2),
+# 17 fuses the linear rows into the limb tiles (a separate linear tile by default)
 VARIANTS = {"default": -1, "single": 1 << 12, "pair": 1 << 13,
-            "single_sep": (1 << 14) | (1 << 12), "pair_sep": (1 << 14) | (1 << 13)}
+            "single_fused": (1 << 17) | (1 << 12), "pair_fused": (1 << 17) | (1 << 13)}
 
 
 def rel_b(b, ref):
@@ -77,14 +77,14 @@ def oracle(c, X):
     return G.gls(c.phi, c.h, c.sigma2, c.XL, c.Y, X)
 
 
-@pytest.mark.parametrize("variant", ["single_sep", "single", "pair", "pair_sep", "default"])
+@pytest.mark.parametrize("variant", ["single_fused", "single", "pair", "pair_fused", "default"])
 def test_mixed_small_first(gwas, variant):
     c = synth.make_cohort(3, 128, n_markers=200)
     X = c.snps(130)
     check(run(gwas, c, X, m_blk=256, tile_cfg=VARIANTS[variant]), oracle(c, X), 3)
 
 
-@pytest.mark.parametrize("variant", ["default", "pair", "single", "pair_sep", "single_sep"])
+@pytest.mark.parametrize("variant", ["default", "pair", "single", "pair_fused", "single_fused"])
 def test_mixed_small_workload_full(gwas, variant):
     # n = 1000, p = 4, m = 10,000 (the oracle-sized workload), 3 limbs
     c = synth.make_cohort(0, 1000)
@@ -107,14 +107,14 @@ def test_smaller_limb_radix(gwas, cap, bits, limbs):
     c = synth.make_cohort(0, 1000)
     X = c.snps(3000)
     ref = oracle(c, X)
-    for extra in (0, 1 << 14):
+    for extra in (0, 1 << 17):
         out = run(gwas, c, X, limbs=limbs, m_blk=1024, tile_cfg=(cap << 15) | extra)
         b, w, s = out
         np.testing.assert_array_equal(s, ref[2])
         ok = ref[2] == 0
         eb = rel_b(b[ok], ref[0][ok])
         ew = wald_err(w[ok], ref[1][ok])
-        print(f"[errors] n=1000 mixed x{limbs} of {bits} bits (sep={bool(extra)}): max rel b "
+        print(f"[errors] n=1000 mixed x{limbs} of {bits} bits (fused={bool(extra)}): max rel b "
               f"err {eb:.2e}, Wald err {ew:.2e}")
         assert eb <= tol_bits(bits, limbs)
         assert ew <= wald_tol(limbs, bits)
@@ -131,22 +131,21 @@ def test_mixed_more_limbs_full(gwas, limbs, variant):
     print(f"n=1000 mixed x{limbs} ({variant}): max rel b err {eb:.2e}, Wald err {ew:.2e}")
 
 
-@pytest.mark.parametrize("sep", [False, True])
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("limbs", [2, 3, 4, 5])
-def test_pair_and_single_cta_bitwise(gwas, limbs, sep):
-    # both variants use the same tile height (the pair's tile padded with zero rows or
-    # filled with the fused linear rows up to N = 256), hence the same limbs and the same
-    # partial sums
+def test_pair_and_single_cta_bitwise(gwas, limbs, fused):
+    # both variants use the same tile height and N = 256 tile (limb rows, fused linear
+    # rows, zero rows), hence the same limbs and the same partial sums
     c = synth.make_cohort(23, 700, n_markers=700)
     X = c.snps(777)
-    v1, v2 = ("pair_sep", "single_sep") if sep else ("pair", "single")
+    v1, v2 = ("pair_fused", "single_fused") if fused else ("pair", "single")
     b1, w1, _ = run(gwas, c, X, limbs=limbs, m_blk=1024, tile_cfg=VARIANTS[v1])
     b2, w2, _ = run(gwas, c, X, limbs=limbs, m_blk=1024, tile_cfg=VARIANTS[v2])
     np.testing.assert_array_equal(b1, b2)
     np.testing.assert_array_equal(w1, w2)
 
 
-@pytest.mark.parametrize("variant", ["pair", "single", "pair_sep", "single_sep"])
+@pytest.mark.parametrize("variant", ["pair", "single", "pair_fused", "single_fused"])
 @pytest.mark.parametrize("limbs", [2, 3, 4, 5])
 @pytest.mark.parametrize("n,m,p,t,mblk", [
     (64, 1, 4, 1, 64), (65, 127, 4, 1, 128), (130, 129, 3, 2, 128), (1003, 300, 4, 3, 512),
@@ -229,12 +228,19 @@ def test_mixed_multi_phenotype(gwas):
 
 
 def test_mixed_block_size_and_order_bitwise(gwas):
+    # blocks of 128 SNPs run whole; a block of 2,500 runs as two launches over its halves
+    # (SNPs 0-1279 and 1280-2499) with the second half's conversion and the first half's
+    # solves on a second stream; blocks of 1,100 split at 768; all give the same bits
     c = synth.make_cohort(22, 600, n_markers=700)
-    X = c.snps(500)
-    b1, _, _ = run(gwas, c, X, m_blk=128)
-    b2, _, _ = run(gwas, c, X, m_blk=4096)
+    X = c.snps(2500)
+    b1, w1, s1 = run(gwas, c, X, m_blk=128)
+    b2, w2, s2 = run(gwas, c, X, m_blk=4096)
     np.testing.assert_array_equal(b1, b2)
-    perm = np.random.default_rng(4).permutation(500)
+    np.testing.assert_array_equal(w1, w2)
+    np.testing.assert_array_equal(s1, s2)
+    b4, _, _ = run(gwas, c, X, m_blk=1100)
+    np.testing.assert_array_equal(b1, b4)
+    perm = np.random.default_rng(4).permutation(2500)
     b3, _, _ = run(gwas, c, np.asfortranarray(X[:, perm]), m_blk=256)
     np.testing.assert_array_equal(b3, b1[perm])
 
