@@ -91,7 +91,16 @@ template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
-    const int64_t i0 = (int64_t)blockIdx.x * T64, j0 = (int64_t)blockIdx.y * T64;
+    // With a lower-triangular op(A) a row tile's k-range grows with its row: take the
+    // tiles heaviest row first (row tiles in descending order, the column fastest), so the
+    // long ones do not form the tail of the grid.
+    int64_t bi = blockIdx.x, bj = blockIdx.y;
+    if (g.a_lower) {
+        const int64_t lin = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        bi = gridDim.x - 1 - lin / gridDim.y;
+        bj = lin % gridDim.y;
+    }
+    const int64_t i0 = bi * T64, j0 = bj * T64;
     if (g.c_lower && j0 > i0) return;
     int64_t kbeg = 0, kend = g.K;
     if (g.a_lower) kend = min64(kend, i0 + T64);
@@ -178,36 +187,45 @@ cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s) {
 
 // ----------------------------------------------------------------------------
 // a2 diagonal block: unblocked Cholesky of one kb x kb block (kb <= 64) in shared
-// memory, then D = L_kk^{-1} by column-wise forward substitution.
+// memory, then D = L_kk^{-1} by recursive halving: the four 16 x 16 diagonal blocks are
+// inverted by forward substitution (one thread per column), then merged into 32 x 32 and
+// 64 x 64 inverses with [[A, 0], [B, C]]^{-1} = [[A^{-1}, 0], [-C^{-1} B A^{-1}, C^{-1}]].
 // ----------------------------------------------------------------------------
+constexpr int POTRF_SMEM = (2 * T64 * (T64 + 1) + 32 * 33 + 2 * T64) * (int)sizeof(double);
+
 __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int64_t lda, int kb,
                                                     int64_t base, double* __restrict__ D,
                                                     int* __restrict__ info) {
-    // 2 x 64 x 65 doubles (66,560 bytes): dynamic shared memory, opted in at launch.
+    // S (64 x 65), Dn (64 x 65), Tm (32 x 33), the pivots and their reciprocals: dynamic
+    // shared memory, opted in at launch.
     extern __shared__ double smem_potrf[];
     double (*S)[T64 + 1] = reinterpret_cast<double (*)[T64 + 1]>(smem_potrf);
     double (*Dn)[T64 + 1] = reinterpret_cast<double (*)[T64 + 1]>(smem_potrf + T64 * (T64 + 1));
+    double (*Tm)[33] = reinterpret_cast<double (*)[33]>(smem_potrf + 2 * T64 * (T64 + 1));
+    double* rinv = smem_potrf + 2 * T64 * (T64 + 1) + 32 * 33;
+    double* pv = rinv + T64;
     __shared__ int fail;
     const int tid = threadIdx.x;
     if (tid == 0) fail = -1;
+    // rows and columns beyond kb carry the identity, so the 64 x 64 inverse below is that
+    // of [[L_kk, 0], [0, I]]; they are written back as zeros
     for (int e = tid; e < T64 * T64; e += blockDim.x) {
         const int i = e % T64, j = e / T64;
-        S[i][j] = (i < kb && j < kb && i >= j) ? A[i + j * lda] : 0.0;
+        S[i][j] = (i < kb && j < kb && i >= j) ? A[i + j * lda] : (i == j ? 1.0 : 0.0);
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
+        // every thread takes the pivot itself (S[j][j] is not written in this loop; the
+        // pivots go to pv and replace the diagonal at the end); thread 0 records them
+        const double d = S[j][j];
+        const double piv = d > 0.0 ? sqrt(d) : nan("");
+        const double rp = 1.0 / piv;
         if (tid == 0) {
-            const double d = S[j][j];
-            if (!(d > 0.0)) {
-                if (fail < 0) fail = j;
-                S[j][j] = nan("");
-            } else {
-                S[j][j] = sqrt(d);
-            }
+            pv[j] = piv;
+            rinv[j] = rp;
+            if (!(d > 0.0) && fail < 0) fail = j;
         }
-        __syncthreads();
-        const double piv = S[j][j];
-        for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[i][j] /= piv;
+        for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[i][j] *= rp;
         __syncthreads();
         const int w = kb - j - 1;  // trailing (w x w) lower update
         for (int e = tid; e < w * w; e += blockDim.x) {
@@ -216,24 +234,55 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int6
         }
         __syncthreads();
     }
-    // D = L_kk^{-1}: thread c solves L d_c = e_c for column c (rows c..kb-1).
+    if (tid >= kb && tid < T64) rinv[tid] = 1.0;  // the identity rows
+    if (tid < kb) S[tid][tid] = pv[tid];
+    __syncthreads();
+
+    // 16 x 16 diagonal blocks: thread (b, c) solves L_bb d = e_c, its column in registers
     if (tid < T64) {
-        const int c = tid;
-        for (int i = 0; i < T64; ++i) Dn[i][c] = 0.0;
-        if (c < kb) {
-            Dn[c][c] = 1.0 / S[c][c];
-            for (int i = c + 1; i < kb; ++i) {
-                double acc = 0.0;
-                for (int k = c; k < i; ++k) acc = fma(S[i][k], Dn[k][c], acc);
-                Dn[i][c] = -acc / S[i][i];
-            }
+        const int b = tid / 16, c = tid % 16, o = 16 * b;
+        double dc[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            double acc = 0.0;
+#pragma unroll
+            for (int k = 0; k < i; ++k) acc = fma(S[o + i][o + k], dc[k], acc);
+            dc[i] = ((i == c ? 1.0 : 0.0) - acc) * rinv[o + i];
         }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) Dn[o + i][o + c] = dc[i];
+    }
+    // strictly upper parts stay zero
+    for (int e = tid; e < T64 * T64; e += blockDim.x) {
+        const int i = e % T64, j = e / T64;
+        if (i / 16 <= j / 16 && !(i / 16 == j / 16)) Dn[i][j] = 0.0;
     }
     __syncthreads();
+    // merge pairs of h x h inverses into 2h x 2h ones, h = 16 then 32
+    for (int h = 16; h < T64; h *= 2) {
+        const int nb = T64 / (2 * h);          // merged blocks at this level
+        const int outs = nb * h * h;           // entries of B A^{-1} (and of the new block)
+        // Tm = B A^{-1}: B = L[o+h .. o+2h, o .. o+h], A^{-1} = Dn[o .. o+h, o .. o+h]
+        for (int e = tid; e < outs; e += blockDim.x) {
+            const int m = e / (h * h), r = e % (h * h), i = r % h, j = r / h, o = 2 * h * m;
+            double acc = 0.0;
+            for (int k = j; k < h; ++k) acc = fma(S[o + h + i][o + k], Dn[o + k][o + j], acc);
+            Tm[m * h + i][j] = acc;            // nb * h = 32 rows of Tm
+        }
+        __syncthreads();
+        // Dn[o+h .., o ..] = -C^{-1} Tm with C^{-1} = Dn[o+h .., o+h ..] (lower)
+        for (int e = tid; e < outs; e += blockDim.x) {
+            const int m = e / (h * h), r = e % (h * h), i = r % h, j = r / h, o = 2 * h * m;
+            double acc = 0.0;
+            for (int k = 0; k <= i; ++k) acc = fma(Dn[o + h + i][o + h + k], Tm[m * h + k][j], acc);
+            Dn[o + h + i][o + j] = -acc;
+        }
+        __syncthreads();
+    }
     for (int e = tid; e < T64 * T64; e += blockDim.x) {
         const int i = e % T64, j = e / T64;
         if (i < kb && j < kb) A[i + j * lda] = (i >= j) ? S[i][j] : 0.0;
-        D[i + j * T64] = Dn[i][j];
+        D[i + j * T64] = (i < kb && j < kb) ? Dn[i][j] : 0.0;
     }
     if (tid == 0 && fail >= 0) atomicMin(info, (int)(base + fail));
 }
@@ -246,7 +295,7 @@ cudaError_t cholesky_blocked(double* A, int64_t lda, int64_t n, double* Dinv, in
                              cudaStream_t s, int64_t* launches) {
     constexpr int64_t NB = 4 * T64;
     int64_t nl = 0;
-    const int smem = 2 * T64 * (T64 + 1) * (int)sizeof(double);
+    const int smem = POTRF_SMEM;
     cudaError_t e = cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     for (int64_t p0 = 0; p0 < n; p0 += NB) {
