@@ -45,43 +45,66 @@ __global__ void k_wait_selftest(uint64_t limit_ns, int* code, unsigned long long
     }
 }
 
-// FP64 multiply-add throughput probe: every thread runs CHAINS independent chains
-// a <- a * beta + gamma (beta = 1 - 2^-20, gamma = 2^-20, so a stays near 1: no overflow,
-// no subnormals) for iters x 16 steps, then stores its sum so no chain is dead code.
-template <int CHAINS>
+// FP64 multiply-add throughput probe with the FP64 block kernel's inner loop: 256
+// threads, each a 4 x 4 register tile acc[a][b] += As[k][a] Bs[k][b] over 16-deep chunks
+// re-read from shared memory after a barrier (dependent chains of fma on shared
+// constants run slower on this part, so they would not bound the block kernel).
+// Operands are near 1 (no overflow, no subnormals); each thread stores its sum.
 __global__ void __launch_bounds__(256) k_dfma_rate(int iters, double beta, double gamma,
                                                    double* __restrict__ out) {
-    double a[CHAINS];
+    __shared__ double As[KC64][T64 + 1];
+    __shared__ double Bs[KC64][T64 + 1];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    for (int e = tid; e < KC64 * T64; e += blockDim.x) {
+        As[e / T64][e % T64] = beta * (1.0 + 1e-6 * (double)(e & 31));
+        Bs[e / T64][e % T64] = gamma * (1.0 - 1e-6 * (double)(e & 15));
+    }
+    double acc[4][4];
 #pragma unroll
-    for (int i = 0; i < CHAINS; ++i) a[i] = 1.0 + 1e-3 * (double)((threadIdx.x + i) & 7);
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
     for (int it = 0; it < iters; ++it) {
+        __syncthreads();
 #pragma unroll
-        for (int u = 0; u < 16; ++u)
+        for (int kk = 0; kk < KC64; ++kk) {
+            double av[4], bv[4];
 #pragma unroll
-            for (int i = 0; i < CHAINS; ++i) a[i] = fma(a[i], beta, gamma);
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][tx + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][ty + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
     }
     double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < CHAINS; ++i) s += a[i];
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) s += acc[a][b];
     out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
-template <int CHAINS>
+// fma per thread and iteration of k_dfma_rate
+constexpr double kFmaPerIter = 16.0 * KC64;
+
 static cudaError_t time_dfma(int blocks, int iters, double* out, cudaEvent_t e0, cudaEvent_t e1,
                              double* tflops) {
     const double beta = 1.0 - 1.0 / 1048576.0, gamma = 1.0 / 1048576.0;
-    k_dfma_rate<CHAINS><<<blocks, 256>>>(iters, beta, gamma, out);  // warm-up
+    k_dfma_rate<<<blocks, 256>>>(iters, beta, gamma, out);  // warm-up
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     double best = 0.0;
     for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0);
-        k_dfma_rate<CHAINS><<<blocks, 256>>>(iters, beta, gamma, out);
+        k_dfma_rate<<<blocks, 256>>>(iters, beta, gamma, out);
         cudaEventRecord(e1);
         if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
         float ms = 0.f;
         if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return e;
-        const double flops = 2.0 * 16.0 * CHAINS * (double)iters * blocks * 256.0;
+        const double flops = 2.0 * kFmaPerIter * (double)iters * blocks * 256.0;
         if (ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
     }
     *tflops = best;
@@ -103,18 +126,16 @@ extern "C" gwas_status gwas_fp64_fma_rate(int device, double* tflops) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
         cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
         cudaMalloc(&out, sizeof(double) * 256 * 8 * (size_t)sms) == cudaSuccess) {
-        // a few shapes (chains per thread x CTAs per SM), each launch ~0.1-0.2 s at
-        // 1.25 TFLOP/s; the best rate is the FP64 FMA peak this device sustains
-        const int shapes[4][2] = {{8, 2}, {8, 4}, {16, 2}, {4, 8}};
+        // 2, 4 and 8 CTAs per SM, each launch ~0.12 s at 1.25 TFLOP/s; the best rate is
+        // the FP64 FMA rate this device sustains
+        const int per_sm[3] = {2, 4, 8};
         double best = 0.0;
         bool ok = true;
-        for (const auto& sh : shapes) {
-            const int chains = sh[0], blocks = sh[1] * sms;
-            const int iters = (int)(1.5e11 / (2.0 * 16.0 * chains * blocks * 256.0));
+        for (int ps : per_sm) {
+            const int blocks = ps * sms;
+            const int iters = (int)(1.5e11 / (2.0 * gwas::kFmaPerIter * blocks * 256.0));
             double r = 0.0;
-            cudaError_t e = chains == 4    ? gwas::time_dfma<4>(blocks, iters, out, e0, e1, &r)
-                            : chains == 8  ? gwas::time_dfma<8>(blocks, iters, out, e0, e1, &r)
-                                           : gwas::time_dfma<16>(blocks, iters, out, e0, e1, &r);
+            cudaError_t e = gwas::time_dfma(blocks, iters, out, e0, e1, &r);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 ok = false;
