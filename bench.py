@@ -172,19 +172,24 @@ def bf16_flops_per_snp(n: int, q: int, t: int, limbs: int) -> float:
     return limbs * (n * (n + 1) + 2.0 * n * (q + t))
 
 
-# DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of the bench's own launch shape), valid only
-# while the kernel source is the one captured (code_sha of its file) and, for
-# the limb kernel, per L2 group size and layout (CTA pairs or one CTA, fused or separate
-# linear rows; the traffic does not depend on the pipeline depth).
+# DRAM traffic of the dominant kernel per block (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the bench's own launch shape, summed over
+# the block's launches: the limb kernel runs two per block of 1024 SNPs or more), valid only
+# while the kernel source is the one captured (code_sha of its file) and, for the limb
+# kernel, per L2 group size and layout (CTA pairs or one CTA, fused or separate linear
+# rows; the traffic does not depend on the pipeline depth).
 TRAFFIC = {
-    "k_block_fp64": {"file": "block_fp64.cu", "sha": "f12d054bee8830fb", "n": 10000,
-                     "m_blk": 16384, "bytes": 2061468160 + 110667520},
-    "k_block_mixed<3>": {"file": "block_mixed.cu", "sha": "176da42a48ba3994", "n": 10000,
-                         "m_blk": 16384, "single_cta": False, "fuse": True,
-                         "bytes_by_group_mb": {40: 4036415744 + 81025792,
-                                               80: 4554571520 + 79876352,
-                                               160: 8137596416 + 76032256}},
+    "k_block_fp64": [{"file": "block_fp64.cu", "sha": "f12d054bee8830fb", "n": 10000,
+                      "m_blk": 16384, "bytes": 2061468160 + 110667520}],
+    "k_block_mixed<3>": [
+        {"file": "block_mixed.cu", "sha": "9ac88a032c802cc0", "n": 10000, "m_blk": 16384,
+         "single_cta": False, "fuse": False,
+         "bytes_by_group_mb": {40: 3781793024 + 17790976, 80: 4030348288 + 16826880,
+                               160: 7517394432 + 14878464}},
+        {"file": "block_mixed.cu", "sha": "9ac88a032c802cc0", "n": 30000, "m_blk": 16384,
+         "single_cta": False, "fuse": False,
+         "bytes_by_group_mb": {40: 125145158656 + 51067904, 80: 91655307776 + 51416064,
+                               160: 78482764032 + 50951936}}],
 }
 
 
@@ -206,9 +211,10 @@ MIXED_TOL = {2: 1e-4, 3: 1e-6, 4: 1e-9, 5: 1e-10}
 
 
 def traffic_for(kernel: str, n: int, m_blk: int, tile_cfg=None):
-    rec = TRAFFIC.get(kernel)
-    if not rec or rec["n"] != n or rec["m_blk"] != m_blk:
+    recs = [r for r in TRAFFIC.get(kernel, []) if r["n"] == n and r["m_blk"] == m_blk]
+    if not recs:
         return None
+    rec = recs[0]
     nbytes = rec.get("bytes")
     if "bytes_by_group_mb" in rec:
         f = tile_cfg_fields(tile_cfg)

@@ -21,7 +21,7 @@ def test_tile_cfg_fields_match_the_bit_layout():
 
 
 def test_traffic_guard_rejects_other_shapes_and_groupings():
-    rec = bench.TRAFFIC["k_block_mixed<3>"]
+    rec = bench.TRAFFIC["k_block_mixed<3>"][0]
     n, mb = rec["n"], rec["m_blk"]
     assert bench.traffic_for("k_block_mixed<3>", n + 1, mb) is None
     assert bench.traffic_for("k_block_mixed<3>", n, mb // 2) is None
