@@ -4,6 +4,7 @@
 // FP64 arithmetic stays on the CUDA cores (DFMA): the setup is O(n^3) once per
 // cohort, and its stability needs FP64 (Section 2: L L^T := M, triangular solves).
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -87,19 +88,11 @@ __device__ __forceinline__ void gemm_tile(const GemmF64& g, int64_t i0, int64_t 
     }
 }
 
+// One 64 x 64 output tile (bi, bj) of C := alpha op(A) op(B) + beta C.
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
+__device__ __forceinline__ void gemm_tile_job(const GemmF64& g, int64_t bi, int64_t bj) {
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
-    // With a lower-triangular op(A) a row tile's k-range grows with its row: take the
-    // tiles heaviest row first (row tiles in descending order, the column fastest), so the
-    // long ones do not form the tail of the grid.
-    int64_t bi = blockIdx.x, bj = blockIdx.y;
-    if (g.a_lower) {
-        const int64_t lin = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-        bi = gridDim.x - 1 - lin / gridDim.y;
-        bj = lin % gridDim.y;
-    }
     const int64_t i0 = bi * T64, j0 = bj * T64;
     if (g.c_lower && j0 > i0) return;
     int64_t kbeg = 0, kend = g.K;
@@ -126,6 +119,39 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
             *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
         }
     }
+}
+
+// Tile (bx, by) of an mt x nt tile grid, renumbered so that with a lower-triangular op(A)
+// (a row tile's k-range grows with its row) the heaviest row tiles come first (row tiles
+// in descending order, the column fastest) and the long ones do not form the tail.
+__device__ __forceinline__ void tile_order(const GemmF64& g, int64_t bx, int64_t by, int64_t mt,
+                                           int64_t nt, int64_t& bi, int64_t& bj) {
+    bi = bx;
+    bj = by;
+    if (g.a_lower) {
+        const int64_t lin = by * mt + bx;
+        bi = mt - 1 - lin / nt;
+        bj = lin % nt;
+    }
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm_f64(GemmF64 g) {
+    int64_t bi, bj;
+    tile_order(g, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y, bi, bj);
+    gemm_tile_job<TA, TB>(g, bi, bj);
+}
+
+// Several independent products in one launch (grid z = product); the grid covers the
+// largest product's tiles and each CTA outside its own product's tiles returns.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm_f64_batched(const GemmF64* __restrict__ gs) {
+    const GemmF64 g = gs[blockIdx.z];
+    const int64_t mt = (g.M + T64 - 1) / T64, nt = (g.N + T64 - 1) / T64;
+    if ((int64_t)blockIdx.x >= mt || (int64_t)blockIdx.y >= nt) return;
+    int64_t bi, bj;
+    tile_order(g, blockIdx.x, blockIdx.y, mt, nt, bi, bj);
+    gemm_tile_job<TA, TB>(g, bi, bj);
 }
 
 // Skinny products (one 64 x 64 output tile, long K: the Gram matrices A^T B of n x q
@@ -347,54 +373,103 @@ cudaError_t cholesky_blocked(double* A, int64_t lda, int64_t n, double* Dinv, in
 }
 
 // ----------------------------------------------------------------------------
-// a3: W := L^{-1} by recursive halving on 64-aligned splits.
+// a3: W := L^{-1} by recursive halving on 64-aligned splits,
+//   [[L11, 0], [L21, L22]]^{-1} = [[W11, 0], [-W22 L21 W11, W22]],
+// evaluated level by level from the leaves (the 64 x 64 diagonal inverses D_k) up: the
+// nodes of one level are independent, so each level is two batched launches over all
+// of its nodes (T := L21 W11, then W21 := -W22 T) instead of two launches per node.
 // ----------------------------------------------------------------------------
-__global__ void k_copy_diag_inv(const double* __restrict__ D, int kb, double* __restrict__ W,
+__global__ void k_copy_diag_inv(const double* __restrict__ Dinv, int64_t n, double* __restrict__ W,
                                 int64_t ldw) {
+    const int64_t r0 = (int64_t)blockIdx.x * T64;
+    const int kb = (int)min64(T64, n - r0);
+    const double* D = Dinv + (int64_t)blockIdx.x * T64 * T64;
     for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
         const int i = e % kb, j = e / kb;
-        W[i + j * ldw] = D[i + j * T64];
+        W[(r0 + i) + (r0 + j) * ldw] = D[i + j * T64];
     }
 }
 
-static cudaError_t trtri_rec(const double* L, int64_t ldl, int64_t r0, int64_t size,
-                             const double* Dinv, double* W, int64_t ldw, double* tmp,
-                             cudaStream_t s, int64_t* nl) {
-    if (size <= T64) {
-        k_copy_diag_inv<<<1, 256, 0, s>>>(Dinv + (r0 / T64) * T64 * T64, (int)size,
-                                          W + r0 + r0 * ldw, ldw);
-        ++*nl;
-        return cudaGetLastError();
-    }
+namespace {
+
+struct TrtriNode {
+    int64_t r0, s1, s2;
+};
+
+void trtri_nodes(int64_t r0, int64_t size, size_t depth, std::vector<std::vector<TrtriNode>>& lv) {
+    if (size <= T64) return;
     const int64_t s1 = round_up(ceil_div(size, 2), T64);
     const int64_t s2 = size - s1;
-    cudaError_t e = trtri_rec(L, ldl, r0, s1, Dinv, W, ldw, tmp, s, nl);
-    if (e != cudaSuccess) return e;
-    if ((e = trtri_rec(L, ldl, r0 + s1, s2, Dinv, W, ldw, tmp, s, nl)) != cudaSuccess) return e;
-    // T := L21 W11   (s2 x s1; W11 lower triangular)
-    GemmF64 g;
-    g.M = s2; g.N = s1; g.K = s1;
-    g.A = L + (r0 + s1) + r0 * ldl; g.lda = ldl;
-    g.B = W + r0 + r0 * ldw; g.ldb = ldw; g.b_lower = true;
-    g.C = tmp; g.ldc = s2;
-    if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
-    // W21 := -W22 T   (W22 lower triangular)
-    GemmF64 h;
-    h.M = s2; h.N = s1; h.K = s2;
-    h.A = W + (r0 + s1) + (r0 + s1) * ldw; h.lda = ldw; h.a_lower = true;
-    h.B = tmp; h.ldb = s2;
-    h.C = W + (r0 + s1) + r0 * ldw; h.ldc = ldw; h.alpha = -1.0;
-    if ((e = gemm_f64(h, s)) != cudaSuccess) return e;
-    *nl += 2;
-    return cudaSuccess;
+    if (lv.size() <= depth) lv.resize(depth + 1);
+    lv[depth].push_back({r0, s1, s2});
+    trtri_nodes(r0, s1, depth + 1, lv);
+    trtri_nodes(r0 + s1, s2, depth + 1, lv);
 }
+
+}  // namespace
 
 cudaError_t trtri_lower(const double* L, int64_t ldl, int64_t n, const double* Dinv, double* W,
                         int64_t ldw, double* tmp, cudaStream_t s, int64_t* launches) {
     int64_t nl = 0;
-    cudaError_t e = trtri_rec(L, ldl, 0, n, Dinv, W, ldw, tmp, s, &nl);
+    const int64_t nt = ceil_div(n, T64);
+    k_copy_diag_inv<<<(unsigned)nt, 256, 0, s>>>(Dinv, n, W, ldw);
+    ++nl;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    std::vector<std::vector<TrtriNode>> lv;
+    trtri_nodes(0, n, 0, lv);
+    // descriptors level by level: the level's T products, then its W21 products; each
+    // node's T gets its own part of tmp (a level's T blocks take at most (n/2)^2 doubles,
+    // the size of tmp)
+    std::vector<GemmF64> gs;
+    std::vector<size_t> level_first;
+    for (size_t d = 0; d < lv.size(); ++d) {
+        level_first.push_back(gs.size());
+        std::vector<GemmF64> wprod;
+        int64_t off = 0;
+        for (const TrtriNode& nd : lv[d]) {
+            GemmF64 g;  // T := L21 W11   (s2 x s1; W11 lower triangular)
+            g.M = nd.s2; g.N = nd.s1; g.K = nd.s1;
+            g.A = L + (nd.r0 + nd.s1) + nd.r0 * ldl; g.lda = ldl;
+            g.B = W + nd.r0 + nd.r0 * ldw; g.ldb = ldw; g.b_lower = true;
+            g.C = tmp + off; g.ldc = nd.s2;
+            GemmF64 h;  // W21 := -W22 T   (W22 lower triangular)
+            h.M = nd.s2; h.N = nd.s1; h.K = nd.s2;
+            h.A = W + (nd.r0 + nd.s1) + (nd.r0 + nd.s1) * ldw; h.lda = ldw; h.a_lower = true;
+            h.B = tmp + off; h.ldb = nd.s2;
+            h.C = W + (nd.r0 + nd.s1) + nd.r0 * ldw; h.ldc = ldw; h.alpha = -1.0;
+            gs.push_back(g);
+            wprod.push_back(h);
+            off += nd.s2 * nd.s1;
+        }
+        gs.insert(gs.end(), wprod.begin(), wprod.end());
+    }
+    level_first.push_back(gs.size());
+    if (gs.empty()) {
+        if (launches) *launches += nl;
+        return cudaSuccess;
+    }
+    GemmF64* d_gs = nullptr;
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&d_gs), gs.size() * sizeof(GemmF64), s)) !=
+        cudaSuccess)
+        return e;
+    e = cudaMemcpyAsync(d_gs, gs.data(), gs.size() * sizeof(GemmF64), cudaMemcpyHostToDevice, s);
+    for (size_t d = lv.size(); e == cudaSuccess && d-- > 0;) {
+        const size_t first = level_first[d], count = (level_first[d + 1] - first) / 2;
+        int64_t mt = 0, ntl = 0;  // both products of a node have the same s2 x s1 shape
+        for (size_t k = 0; k < count; ++k) {
+            mt = std::max(mt, ceil_div(gs[first + k].M, T64));
+            ntl = std::max(ntl, ceil_div(gs[first + k].N, T64));
+        }
+        const dim3 grid((unsigned)mt, (unsigned)ntl, (unsigned)count);
+        k_gemm_f64_batched<false, false><<<grid, 256, 0, s>>>(d_gs + first);          // T
+        k_gemm_f64_batched<false, false><<<grid, 256, 0, s>>>(d_gs + first + count);  // W21
+        nl += 2;
+        e = cudaGetLastError();
+    }
+    const cudaError_t f = cudaFreeAsync(d_gs, s);
     if (launches) *launches += nl;
-    return e;
+    return e != cudaSuccess ? e : f;
 }
 
 }  // namespace gwas

@@ -24,7 +24,8 @@ cudaError_t cholesky_blocked(double* A, int64_t lda, int64_t n, double* Dinv, in
 
 // W := L^{-1} (lower triangular, zeros above the diagonal) by the recursive block
 // formula [[L11,0],[L21,L22]]^{-1} = [[W11,0],[-W22 L21 W11, W22]], with the
-// diagonal 64 x 64 inverses taken from Dinv. tmp needs ceil(n/2/64)*64 squared doubles.
+// diagonal 64 x 64 inverses taken from Dinv, evaluated level by level (two batched
+// launches per level). tmp needs ceil(n/2/64)*64 squared doubles.
 cudaError_t trtri_lower(const double* L, int64_t ldl, int64_t n, const double* Dinv, double* W,
                         int64_t ldw, double* tmp, cudaStream_t s, int64_t* launches);
 
