@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
             const CohortMx& cm = *src.locate(u, ci, lu);
             decode_unit(cm, lu, rt, ct);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R + mx::BK - 1) / mx::BK, cm.n_kc_full);
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R - cm.off + mx::BK - 1) / mx::BK, cm.n_kc_full);
             const int ybase = ex ? cm.n_rt * N : rt * N;
             const uint32_t bytes = A_BYTES + (uint32_t)(ex ? a.N_e : N) * mx::BK * 2;
             for (int kc = 0; kc < nk; ++kc) {
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
             const CohortMx& cm = *src.locate(u, ci, lu);
             decode_unit(cm, lu, rt, ct);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R + mx::BK - 1) / mx::BK, cm.n_kc_full);
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R - cm.off + mx::BK - 1) / mx::BK, cm.n_kc_full);
             if (!mbar_wait(&tempty[abuf], aphase ^ 1, mx::WAIT_NS)) {
                 record_error(a.err, abort_flag, 2);
                 break;
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed2(const __grid_constant__
             const CohortMx& cm = *src.locate(u, ci, lu);
             decode_unit(cm, lu, rt, ctp);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R + mx::BK - 1) / mx::BK, cm.n_kc_full);
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R - cm.off + mx::BK - 1) / mx::BK, cm.n_kc_full);
             const int half = ex ? NeH : NH;
             const int ybase = (ex ? cm.n_rt * N : rt * N) + (int)rank * half;
             const int ct = cm.ct_base + 2 * ctp + (int)rank;
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed2(const __grid_constant__
             const CohortMx& cm = *src.locate(u, ci, lu);
             decode_unit(cm, lu, rt, ctp);
             const bool ex = (rt == (int)mx::EXTRA);
-            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R + mx::BK - 1) / mx::BK, cm.n_kc_full);
+            const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R - cm.off + mx::BK - 1) / mx::BK, cm.n_kc_full);
             if (!mbar_wait(&tempty[abuf], aphase ^ 1, mx::WAIT_NS)) {
                 record_error(a.err, abort_flag, 12);
                 break;
@@ -679,6 +679,7 @@ static CohortMx make_cohort(const MixedDev& m, int64_t mb, bool pair, int64_t sn
     c.extra = m.fused ? 0 : 1;
     c.radix = m.radix;
     c.R = m.R;
+    c.off = m.row_off();
     c.E_w = m.E;
     c.E_e = m.E + m.n_rt;
     c.sq_part = m.sq_part;

@@ -241,16 +241,18 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int6
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
-        // every thread takes the pivot itself (S[j][j] is not written in this loop; the
-        // pivots go to pv and replace the diagonal at the end); thread 0 records them
-        const double d = S[j][j];
-        const double piv = d > 0.0 ? sqrt(d) : nan("");
-        const double rp = 1.0 / piv;
+        // one thread takes the pivot and its reciprocal (FP64 square roots and divisions
+        // are slow on this part: 256 redundant ones cost more than the barrier); the
+        // pivots go to pv and replace the diagonal at the end
         if (tid == 0) {
+            const double d = S[j][j];
+            const double piv = d > 0.0 ? sqrt(d) : nan("");
             pv[j] = piv;
-            rinv[j] = rp;
+            rinv[j] = 1.0 / piv;
             if (!(d > 0.0) && fail < 0) fail = j;
         }
+        __syncthreads();
+        const double rp = rinv[j];
         for (int i = j + 1 + tid; i < kb; i += blockDim.x) S[i][j] *= rp;
         __syncthreads();
         const int w = kb - j - 1;  // trailing (w x w) lower update

@@ -613,6 +613,7 @@ gwas_status gwas_finalize(gwas_ctx* c) {
         DeviceGuard g(c->device);
         cudaStreamSynchronize(c->s_h2d);
         cudaStreamSynchronize(c->s_comp);
+        if (c->s_aux) cudaStreamSynchronize(c->s_aux);
         cudaStreamSynchronize(c->s_d2h);
         free_all(c);
     }

@@ -102,6 +102,7 @@ struct CohortMx {
     int extra;          // 1: a separate linear tile per SNP tile; 0: linear rows fused
     int radix;          // bits per limb B: limbs in [-2^(B-1), 2^(B-1)]
     int R;              // rows of L^{-1} per row tile (limb i, l in column i*S + l)
+    int off;            // n_rt R - n: row tile rt holds rows rt R - off .. (rt + 1) R - off
     int ct_base;        // first 128-SNP tile of the launch (its SNPs start at 128 ct_base)
     const int* E_w;     // exponent per row tile
     const int* E_e;     // exponent per linear row (fused: per (row tile, linear row))
@@ -140,6 +141,8 @@ struct MixedDev {
     bool cfg_fuse = false;        // fuse the linear rows into the limb tiles (lower R)
     int cfg_radix = 0;            // bits per limb at most 9 - cfg_radix (tile_cfg bits 15-16)
     int lin_tiles() const { return fused ? n_rt : 1; }
+    // rows of padding before row 0: the row tiles end at row n, so the first is the short one
+    int row_off() const { return (int)((int64_t)n_rt * R - n); }
     int n_exp() const { return n_rt + (fused ? n_rt * R_e : R_e); }
     CUtensorMap tmX, tmW, tmE;  // TMA maps of Xb, WL (row tiles), WL (linear tile)
     CUtensorMap tmWh, tmEh;     // the same WL maps with half-height boxes (CTA pairs)

@@ -134,15 +134,17 @@ k_geno_bf16_batch(const BatchJob* __restrict__ jobs, int n_jobs, int64_t n_snps)
 // Exponents and limb split of L^{-1} (row tiles) and of Z (linear rows).
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-k_absmax_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, unsigned long long* bits) {
-    // grid: x = k chunks of 256, y = row tile of R rows; elements (i, k) of the tile's
-    // lower part, i fastest (coalesced along the column-major rows)
+k_absmax_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int off,
+           unsigned long long* bits) {
+    // grid: x = k chunks of 256, y = row tile of R rows (tile rt holds rows rt R - off ..,
+    // so the first tile is the short one); elements (i, k) of the tile's lower part, i
+    // fastest (coalesced along the column-major rows)
     const int rt = blockIdx.y;
-    const int64_t r0 = (int64_t)rt * R, k0 = (int64_t)blockIdx.x * 256;
+    const int64_t r0 = (int64_t)rt * R - off, k0 = (int64_t)blockIdx.x * 256;
     double m = 0.0;
     for (int e = threadIdx.x; e < R * 256; e += blockDim.x) {
         const int64_t r = r0 + e % R, k = k0 + e / R;
-        if (r < n && k <= r) m = fmax(m, fabs(W[r + k * ldw]));
+        if (r >= 0 && r < n && k <= r) m = fmax(m, fabs(W[r + k * ldw]));
     }
     __shared__ double red[256];
     red[threadIdx.x] = m;
@@ -200,10 +202,12 @@ __device__ __forceinline__ void split_limbs(double w, int E, int B, uint16_t (&o
 }
 
 // Lower triangle of W (column-major) -> limb rows rt*NT + i*S + l of WL (k contiguous):
-// R rows of L^{-1} per tile, the S limbs of row i side by side, row tiles NT rows apart.
+// R rows of L^{-1} per tile, row r in tile rt = (r + off) / R at i = (r + off) % R (the
+// tiles end at row n, the first one is short), the S limbs of row i side by side, row tiles
+// NT rows apart.
 template <int S>
 __global__ void __launch_bounds__(256)
-k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int NT, int B,
+k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int off, int NT, int B,
           const int* __restrict__ E_w, uint16_t* __restrict__ WL, int64_t n_pad) {
     __shared__ double tile[32][33];
     const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
@@ -218,7 +222,7 @@ k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int NT, i
     for (int j = ty; j < 32; j += 8) {
         const int64_t r = r0 + j, k = k0 + tx;
         if (r >= n || k >= n || k > r) continue;
-        const int64_t rt = r / R, i = r % R;
+        const int64_t rt = (r + off) / R, i = (r + off) % R;
         uint16_t limbs[S];
         split_limbs<S>(tile[tx][j], E_w[rt], B, limbs);
 #pragma unroll
@@ -243,9 +247,10 @@ k_split_z(const double* __restrict__ Z, int64_t n, int R_e, int B, const int* __
 
 // Fused linear rows: exponent per (row tile rt, linear row j) over k in the tile's range.
 __global__ void __launch_bounds__(256)
-k_absmax_zf(const double* __restrict__ Z, int64_t n, int R, unsigned long long* bits) {
+k_absmax_zf(const double* __restrict__ Z, int64_t n, int R, int off, unsigned long long* bits) {
     const int rt = blockIdx.x, j = blockIdx.y, R_e = gridDim.y;
-    const int64_t k0 = (int64_t)rt * R, k1 = min64(n, k0 + R);
+    const int64_t k1 = min64(n, (int64_t)(rt + 1) * R - off);
+    const int64_t k0 = (int64_t)rt * R - off < 0 ? 0 : (int64_t)rt * R - off;
     double m = 0.0;
     for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) m = fmax(m, fabs(Z[k + (int64_t)j * n]));
     __shared__ double red[256];
@@ -259,16 +264,17 @@ k_absmax_zf(const double* __restrict__ Z, int64_t n, int R, unsigned long long* 
         atomicMax(&bits[(int64_t)rt * R_e + j], (unsigned long long)__double_as_longlong(red[0]));
 }
 
-// Z (n x R_e) -> for every k, limb rows rt*NT + R*S + l*R_e + j of row tile rt = k / R:
-// each tile carries Z only on its own k-range, so the tiles' partial sums add up to Z^T x.
+// Z (n x R_e) -> for every k, limb rows rt*NT + R*S + l*R_e + j of row tile
+// rt = (k + off) / R: each tile carries Z only on its own k-range (the k of its own rows),
+// so the tiles' partial sums add up to Z^T x.
 template <int S>
 __global__ void __launch_bounds__(256)
-k_split_zf(const double* __restrict__ Z, int64_t n, int R, int NT, int R_e, int B,
+k_split_zf(const double* __restrict__ Z, int64_t n, int R, int off, int NT, int R_e, int B,
            const int* __restrict__ E_e, uint16_t* __restrict__ WL, int64_t n_pad) {
     const int j = blockIdx.y;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t rt = k / R;
+        const int64_t rt = (k + off) / R;
         uint16_t limbs[S];
         split_limbs<S>(Z[k + (int64_t)j * n], E_e[rt * R_e + j], B, limbs);
 #pragma unroll
@@ -286,10 +292,12 @@ cudaError_t launch_limb_split(MixedDev& m, const double* W, int64_t ldw, const d
     const int64_t n = m.n;
     if ((e = cudaMemsetAsync(m.WL, 0, (size_t)m.rows_total * m.n_pad * 2, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(m.bits, 0, (size_t)m.n_exp() * 8, s)) != cudaSuccess) return e;
+    const int off = m.row_off();
     k_absmax_w<<<dim3((unsigned)ceil_div(n, 256), (unsigned)m.n_rt), 256, 0, s>>>(W, ldw, n, m.R,
-                                                                                 m.bits);
+                                                                                 off, m.bits);
     if (m.fused)
-        k_absmax_zf<<<dim3((unsigned)m.n_rt, (unsigned)m.R_e), 256, 0, s>>>(Z, n, m.R, m.bits + m.n_rt);
+        k_absmax_zf<<<dim3((unsigned)m.n_rt, (unsigned)m.R_e), 256, 0, s>>>(Z, n, m.R, off,
+                                                                           m.bits + m.n_rt);
     else
         k_absmax_z<<<dim3(64, (unsigned)m.R_e), 256, 0, s>>>(Z, n, m.bits + m.n_rt);
     k_exponents<<<(unsigned)ceil_div(m.n_exp(), 128), 128, 0, s>>>(m.bits, m.n_exp(), m.E);
@@ -297,10 +305,10 @@ cudaError_t launch_limb_split(MixedDev& m, const double* W, int64_t ldw, const d
     const dim3 gz(64, (unsigned)m.R_e);
     const int64_t zbase = (int64_t)m.n_rt * m.NT;
 #define GWAS_SPLIT(SS)                                                                       \
-    k_split_w<SS><<<gw, 256, 0, s>>>(W, ldw, n, m.R, m.NT, m.radix, m.E, m.WL, m.n_pad);     \
+    k_split_w<SS><<<gw, 256, 0, s>>>(W, ldw, n, m.R, off, m.NT, m.radix, m.E, m.WL, m.n_pad); \
     if (m.fused)                                                                             \
-        k_split_zf<SS><<<gz, 256, 0, s>>>(Z, n, m.R, m.NT, m.R_e, m.radix, m.E + m.n_rt, m.WL,  \
-                                          m.n_pad);                                          \
+        k_split_zf<SS><<<gz, 256, 0, s>>>(Z, n, m.R, off, m.NT, m.R_e, m.radix, m.E + m.n_rt,   \
+                                          m.WL, m.n_pad);                                    \
     else                                                                                     \
         k_split_z<SS><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.radix, m.E + m.n_rt, m.WL, m.n_pad, zbase);
     switch (m.S) {
