@@ -53,6 +53,8 @@ def _parser():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision legs (n and n=30000) of an FP64 run")
     ap.add_argument("--mixed-steps", type=int, default=240)
+    ap.add_argument("--mixed-n30k-snps", type=int, default=5000000,
+                    help="SNPs of the n=30000 mixed leg (default: the whole 5e6-SNP job)")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (mixed legs)")
     ap.add_argument("--tile-cfg", type=int, default=None,
                     help="fixed tile configuration for the mixed legs (skips the autotuner)")
@@ -876,8 +878,10 @@ def main():
     if args.precision == "fp64" and not args.no_mixed:
         # the metric's mixed legs (3 limbs: b within 1e-6 of FP64), and 5 limbs at n = 10k,
         # whose b agrees with the FP64 oracle to the FP64 path's own 1e-10
+        # n = 30k: every block of the 5,000,000-SNP job (4 distinct dosage blocks cycled)
+        n30k_steps = max(1, -(-args.mixed_n30k_snps // args.m_blk))
         legs = ((args.n, args.limbs, args.mixed_steps),
-                (30000, args.limbs, max(1, args.mixed_steps // 8)),
+                (30000, args.limbs, n30k_steps),
                 (args.n, 5, max(1, args.mixed_steps // 2)))
         for n_mx, limbs_mx, steps_mx in legs:
             r, c_mx, _ = measure(args, env, n=n_mx, precision="mixed", limbs=limbs_mx,
@@ -885,6 +889,11 @@ def main():
             cohorts.setdefault(n_mx, c_mx)
             del c_mx
             leg = {"n": n_mx, "limbs": limbs_mx,
+                   "workload": f"mixed BF16x{limbs_mx} GLS, n={n_mx}, p=4, t={args.t}, "
+                               f"{steps_mx} blocks of {args.m_blk} SNPs"
+                               + (f" ({steps_mx * args.m_blk} SNPs: the whole "
+                                  f"{args.mixed_n30k_snps}-SNP job, 4 distinct dosage blocks "
+                                  "cycled)" if n_mx == 30000 else ""),
                    "tolerance_rel_b": MIXED_TOL.get(limbs_mx),
                    "tolerance_wald": MIXED_WALD_TOL.get(limbs_mx),
                    "value": r["value"], "unit": UNIT,
