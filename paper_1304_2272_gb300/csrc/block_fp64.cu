@@ -16,8 +16,8 @@
 namespace gwas {
 
 // One CTA = one 64-row x 64-SNP unit; 256 threads, 4 rows x 4 SNPs per thread.
-// Thread (tx, ty): rows tx + 16 a, SNPs ty + 16 b. Within an L2 group of SNP tiles the
-// units are ordered heaviest row tile first (a row tile r needs k < (r+1)*64) so the
+// Thread (tx, ty): rows r0 + tx + 16 a, SNPs ty + 16 b. Within an L2 group of SNP tiles the
+// units are ordered heaviest row tile first (a row tile needs k below its last row) so the
 // tail of the grid is short.
 __device__ __forceinline__ void block_fp64_unit(const CohortDev& c, const int8_t* __restrict__ X,
                                                 int64_t ldx, int64_t mb, int n_rt, int rt, int ct,
@@ -29,7 +29,10 @@ __device__ __forceinline__ void block_fp64_unit(const CohortDev& c, const int8_t
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
     const int64_t n = c.n;
-    const int64_t r0 = (int64_t)rt * T64, c0 = (int64_t)ct * T64;
+    // the row tiles end at row n (tile rt holds rows rt*64 - off ..), so the one short tile
+    // is the first, whose k-range is the shortest
+    const int64_t off = (int64_t)n_rt * T64 - n;
+    const int64_t r0 = (int64_t)rt * T64 - off, c0 = (int64_t)ct * T64;
     const int64_t kend = c.dense ? n : min64(n, r0 + T64);
     const bool check = (rt == n_rt - 1);  // this unit reads every dosage of its SNPs
     if (tid < T64) sbad[tid] = 0;
@@ -47,7 +50,7 @@ __device__ __forceinline__ void block_fp64_unit(const CohortDev& c, const int8_t
             const int e = tid + 256 * r;
             const int ii = e % T64, kk = e / T64;
             const int64_t gi = r0 + ii, gk = k0 + kk;
-            As[kk][ii] = (gi < n && gk < kend) ? c.W[gi + gk * c.ldw] : 0.0;
+            As[kk][ii] = (gi >= 0 && gi < n && gk < kend) ? c.W[gi + gk * c.ldw] : 0.0;
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -87,7 +90,7 @@ __device__ __forceinline__ void block_fp64_unit(const CohortDev& c, const int8_t
         for (int a = 0; a < 4; ++a) {
             const int64_t gi = r0 + tx + 16 * a;
             double z = 0.0;
-            if (gi < n) {
+            if (gi >= 0 && gi < n) {
                 if (v < q) z = c.XLbar[gi + (int64_t)v * n];
                 else if (v > q) z = c.Ybar[gi + (int64_t)(v - q - 1) * n];
             }
