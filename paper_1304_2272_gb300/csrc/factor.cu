@@ -185,6 +185,107 @@ __global__ void k_splitk_reduce(GemmF64 g, int splits, const double* __restrict_
     *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
 }
 
+// Skinny B (N <= 16 columns, M large: Xbar_L = W X_L, Ybar = W Y, Z = W^T [Xbar_L | Ybar]).
+// A 64 x 64 output tile would run these at N/64 of its FP64 work; here a CTA covers all
+// NC columns of a few rows, B's k-chunk is staged in shared memory and the partial sums
+// over k are added in a fixed order. Grid y = chunks of NC columns.
+constexpr int SKB = 64;  // k per staged chunk of B
+
+// op(A) = A: 32 rows x 8 k-slices per CTA (each warp loads 32 consecutive rows of a
+// column of A); a lower-triangular A takes its row tiles heaviest first.
+template <int NC>
+__global__ void __launch_bounds__(256) k_gemm_skinny_n(GemmF64 g) {
+    __shared__ double Bs[SKB][NC];
+    __shared__ double red[8][32][NC + 1];
+    const int tid = threadIdx.x, r = tid % 32, ks = tid / 32;
+    const int64_t nbx = gridDim.x;
+    const int64_t bx = g.a_lower ? nbx - 1 - blockIdx.x : blockIdx.x;
+    const int64_t i0 = bx * 32, i = i0 + r, j0 = (int64_t)blockIdx.y * NC;
+    int64_t kbeg = 0, kend = g.K;
+    if (g.a_lower) kend = min64(kend, i0 + 32);
+    if (g.a_upper) kbeg = i0;
+    double acc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = 0.0;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += SKB) {
+        for (int e = tid; e < SKB * NC; e += 256) {
+            const int kk = e / NC, jj = e % NC;
+            const int64_t k = k0 + kk, j = j0 + jj;
+            Bs[kk][jj] = (k < kend && j < g.N) ? g.B[k + j * g.ldb] : 0.0;
+        }
+        __syncthreads();
+        for (int kk = ks; kk < SKB; kk += 8) {
+            const int64_t k = k0 + kk;
+            const double a = (i < g.M && k < kend) ? g.A[i + k * g.lda] : 0.0;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) acc[j] = fma(a, Bs[kk][j], acc[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < NC; ++j) red[ks][r][j] = acc[j];
+    __syncthreads();
+    if (ks == 0 && i < g.M) {
+        for (int j = 0; j < NC && j0 + j < g.N; ++j) {
+            double v = 0.0;
+            for (int q = 0; q < 8; ++q) v += red[q][r][j];
+            double* c = g.C + i + (j0 + j) * g.ldc;
+            *c = (g.beta == 0.0) ? g.alpha * v : fma(g.beta, *c, g.alpha * v);
+        }
+    }
+}
+
+// op(A) = A^T: 8 output rows x 32 k-lanes per CTA (each warp reads 32 consecutive k of one
+// column of A); an upper-triangular op(A) starts at the CTA's first row.
+template <int NC>
+__global__ void __launch_bounds__(256) k_gemm_skinny_t(GemmF64 g) {
+    __shared__ double Bs[SKB][NC];
+    const int tid = threadIdx.x, lane = tid % 32, w = tid / 32;
+    const int64_t i0 = (int64_t)blockIdx.x * 8, i = i0 + w, j0 = (int64_t)blockIdx.y * NC;
+    int64_t kbeg = 0, kend = g.K;
+    if (g.a_upper) kbeg = i0;
+    if (g.a_lower) kend = min64(kend, i0 + 8);
+    double acc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = 0.0;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += SKB) {
+        for (int e = tid; e < SKB * NC; e += 256) {
+            const int kk = e / NC, jj = e % NC;
+            const int64_t k = k0 + kk, j = j0 + jj;
+            Bs[kk][jj] = (k < kend && j < g.N) ? g.B[k + j * g.ldb] : 0.0;
+        }
+        __syncthreads();
+        for (int kk = lane; kk < SKB; kk += 32) {
+            const int64_t k = k0 + kk;
+            const double a = (i < g.M && k < kend) ? g.A[k + i * g.lda] : 0.0;
+#pragma unroll
+            for (int j = 0; j < NC; ++j) acc[j] = fma(a, Bs[kk][j], acc[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        double v = acc[j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        acc[j] = v;
+    }
+    if (lane == 0 && i < g.M) {
+        for (int j = 0; j < NC && j0 + j < g.N; ++j) {
+            double* c = g.C + i + (j0 + j) * g.ldc;
+            *c = (g.beta == 0.0) ? g.alpha * acc[j] : fma(g.beta, *c, g.alpha * acc[j]);
+        }
+    }
+}
+
+template <int NC>
+static cudaError_t launch_skinny(const GemmF64& g, cudaStream_t s) {
+    const unsigned gy = (unsigned)ceil_div(g.N, NC);
+    if (g.transA) k_gemm_skinny_t<NC><<<dim3((unsigned)ceil_div(g.M, 8), gy), 256, 0, s>>>(g);
+    else k_gemm_skinny_n<NC><<<dim3((unsigned)ceil_div(g.M, 32), gy), 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
 cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
     const bool skinny = g.transA && !g.transB && g.M <= T64 && g.N <= T64 && g.K >= 8192 &&
@@ -202,6 +303,12 @@ cudaError_t gemm_f64(const GemmF64& g, cudaStream_t s) {
         e = cudaGetLastError();
         const cudaError_t f = cudaFreeAsync(ws, s);
         return e != cudaSuccess ? e : f;
+    }
+    // skinny B: all of its columns per CTA (products of L^{-1} with a few vectors)
+    if (!g.transB && g.N <= 16 && g.M >= 256 && g.K >= 256 && !g.b_lower && !g.c_lower) {
+        if (g.N <= 4) return launch_skinny<4>(g, s);
+        if (g.N <= 8) return launch_skinny<8>(g, s);
+        return launch_skinny<16>(g, s);
     }
     dim3 grid((unsigned)ceil_div(g.M, T64), (unsigned)ceil_div(g.N, T64));
     if (!g.transA && !g.transB) k_gemm_f64<false, false><<<grid, 256, 0, s>>>(g);
