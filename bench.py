@@ -381,9 +381,10 @@ def cpu_worker(spec_path: str) -> None:
                       "blas_threads": blas_threads()}), flush=True)
 
 
-def run_workers(L, cohort, X_host, chunks, block: int, trsv: str) -> dict:
+def run_workers(L, cohort, X_host, chunks, block: int, trsv: str, deadline_s: float = 300.0) -> dict:
     """Start one single-threaded oracle process per (lo, hi) chunk of X_host, release them
-    together and time them on the wall clock until the last one is done."""
+    together and time them on the wall clock until the last one is done. Workers still
+    running after deadline_s are killed (their output ends, which raises below)."""
     import tempfile
     import numpy as np
     base = "/dev/shm" if os.path.isdir("/dev/shm") else None
@@ -401,17 +402,30 @@ def run_workers(L, cohort, X_host, chunks, block: int, trsv: str) -> dict:
             procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__),
                                            "--cpu-worker", spec], stdin=subprocess.PIPE,
                                           stdout=subprocess.PIPE, text=True, env=env, cwd=ROOT))
-        for pr in procs:
-            if pr.stdout.readline().strip() != "ready":
-                raise RuntimeError("a CPU baseline worker failed to start")
-        t0 = time.perf_counter()
-        for pr in procs:
-            pr.stdin.write("go\n")
-            pr.stdin.flush()
-        outs = [json.loads(pr.stdout.readline()) for pr in procs]
-        wall = time.perf_counter() - t0
-        for pr in procs:
-            pr.wait(timeout=60)
+        def kill_all():
+            for pr in procs:
+                if pr.poll() is None:
+                    pr.kill()
+        watchdog = threading.Timer(deadline_s, kill_all)
+        watchdog.start()
+        try:
+            for pr in procs:
+                if pr.stdout.readline().strip() != "ready":
+                    raise RuntimeError("a CPU baseline worker failed to start")
+            t0 = time.perf_counter()
+            for pr in procs:
+                pr.stdin.write("go\n")
+                pr.stdin.flush()
+            lines = [pr.stdout.readline() for pr in procs]
+            wall = time.perf_counter() - t0
+            if not all(ln.strip() for ln in lines):
+                raise RuntimeError("a CPU baseline worker ended without a result")
+            outs = [json.loads(ln) for ln in lines]
+            for pr in procs:
+                pr.wait(timeout=60)
+        finally:
+            watchdog.cancel()
+            kill_all()
     snps = sum(o["snps"] for o in outs)
     return {"value": snps / wall, "snps": snps, "wall_s": round(wall, 3),
             "blas_threads": outs[0]["blas_threads"]}
