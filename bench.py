@@ -181,17 +181,23 @@ def bf16_flops_per_snp(n: int, q: int, t: int, limbs: int) -> float:
 # kernel, per L2 group size and layout (CTA pairs or one CTA, fused or separate linear
 # rows; the traffic does not depend on the pipeline depth).
 TRAFFIC = {
-    "k_block_fp64": [{"file": "block_fp64.cu", "sha": "f12d054bee8830fb", "n": 10000,
-                      "m_blk": 16384, "bytes": 2061468160 + 110667520}],
+    "k_block_fp64": [
+        {"file": "block_fp64.cu", "sha": "9b94cec0bf31ad7a", "n": 10000, "m_blk": 16384,
+         "bytes": 2062744832 + 111498752},
+        {"file": "block_fp64.cu", "sha": "9b94cec0bf31ad7a", "n": 30000, "m_blk": 2048,
+         "bytes": 9495486464 + 60372992}],
+    # a mixed block of 16,384 SNPs is two launches of 8,192 (the two halves): bytes per block
     "k_block_mixed<3>": [
-        {"file": "block_mixed.cu", "sha": "9ac88a032c802cc0", "n": 10000, "m_blk": 16384,
+        {"file": "block_mixed.cu", "sha": "dd0df3ef5be84c55", "n": 10000, "m_blk": 16384,
          "single_cta": False, "fuse": False,
-         "bytes_by_group_mb": {40: 3781793024 + 17790976, 80: 4030348288 + 16826880,
-                               160: 7517394432 + 14878464}},
-        {"file": "block_mixed.cu", "sha": "9ac88a032c802cc0", "n": 30000, "m_blk": 16384,
+         "bytes_by_group_mb": {40: 1864541440 + 1865809664 + 10432000 + 7203584,
+                               80: 1991927808 + 1994817280 + 9809920 + 7133696,
+                               160: 3778045184 + 3756617728 + 9096192 + 6043392}},
+        {"file": "block_mixed.cu", "sha": "dd0df3ef5be84c55", "n": 30000, "m_blk": 16384,
          "single_cta": False, "fuse": False,
-         "bytes_by_group_mb": {40: 125145158656 + 51067904, 80: 91655307776 + 51416064,
-                               160: 78482764032 + 50951936}}],
+         "bytes_by_group_mb": {40: 55779521024 + 54989144320 + 26972672 + 24396544,
+                               80: 52567564288 + 52031463424 + 27138048 + 23599104,
+                               160: 45582212608 + 49648010752 + 27142912 + 23671808}}],
 }
 
 
