@@ -63,6 +63,8 @@ def _parser():
     ap.add_argument("--batch-cohorts", type=int, default=48)
     ap.add_argument("--batch-snps", type=int, default=50000,
                     help="SNPs per cohort in the mixed batched leg")
+    ap.add_argument("--batch-tile-cfg", type=int, default=None,
+                    help="tile configuration of the batched legs (gwas_opts.tile_cfg)")
     ap.add_argument("--batch-snps-fp64", type=int, default=2048,
                     help="SNPs per cohort per step in the FP64 batched leg")
     ap.add_argument("--no-adjoint", action="store_true",
@@ -199,6 +201,23 @@ TRAFFIC = {
                                80: 52567564288 + 52031463424 + 27138048 + 23599104,
                                160: 45582212608 + 49648010752 + 27142912 + 23671808}}],
 }
+
+
+def factor_record(stats: dict, n: int, args) -> dict:
+    """The per-cohort factor (M, Cholesky, L^{-1}, the setup products) from gwas_factor's
+    counters: its CUDA-event time without the upload of Phi, X_L and Y from host memory, at
+    2n^3/3 FP64 flops (Cholesky n^3/3 + triangular inverse n^3/3; the n^2 terms are not
+    counted), against the measured FP64 fma rate when it was probed."""
+    up = float(stats.get("factor_upload_ms", 0.0))
+    compute_ms = float(stats["factor_ms"]) - up
+    flops = 2.0 * n ** 3 / 3.0
+    rec = {"ms": float(stats["factor_ms"]), "upload_ms": up, "compute_ms": compute_ms,
+           "launches": int(stats["factor_launches"]), "flops": flops,
+           "fp64_tflops": flops / (compute_ms / 1e3) / 1e12 if compute_ms > 0 else None}
+    probe = getattr(args, "fp64_probe", None)
+    if probe and probe.get("tflops") and rec["fp64_tflops"]:
+        rec["frac_of_fma_rate"] = rec["fp64_tflops"] / probe["tflops"]
+    return rec
 
 
 def tile_cfg_fields(tile_cfg) -> dict:
@@ -579,7 +598,9 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True, mb=
                          n_limbs=limbs)
     gwas.gwas_factor(ctx, np.asfortranarray(cohort.phi), True, cohort.h, cohort.sigma2,
                      cohort.XL, cohort.Y)
-    setup_ms = gwas.gwas_get_stats(ctx)["factor_ms"]
+    fst = gwas.gwas_get_stats(ctx)
+    setup_ms = fst["factor_ms"]
+    factor = factor_record(fst, n, args)
     tune = None
     if precision == "mixed" and args.tile_cfg is not None:
         gwas.gwas_set_tile_cfg(ctx, args.tile_cfg)
@@ -710,8 +731,8 @@ def measure(args, env, *, n, precision, limbs, steps, warmup, want_e2e=True, mb=
         roof["achieved_at_max_clock"] = achieved * mhz_max / mhz
         roof["frac_at_max_clock"] = roof["achieved_at_max_clock"] / roof["peak"]
     res = {"value": value, "ms_per_step": el_ms / steps, "steps": steps, "warmup": warmup,
-           "setup_ms": setup_ms, "roofline": roof, "e2e": e2e, "autotune": tune,
-           "gpu_launches": int(stats["kernel_launches"]), "clocks": clk,
+           "setup_ms": setup_ms, "factor": factor, "roofline": roof, "e2e": e2e,
+           "autotune": tune, "gpu_launches": int(stats["kernel_launches"]), "clocks": clk,
            "status_ok_last_block": status_ok, "sample": sample, "m_blk": mb}
     gwas.gwas_finalize(ctx)
     return res, cohort, pool
@@ -732,8 +753,9 @@ def measure_batch(args, env, precision, snps, steps, warmup):
     hs = rng.uniform(0.2, 0.8, size=args.batch_cohorts)
     t, p = 16, 4
     prec = gwas.GWAS_PREC_FP64 if precision == "fp64" else gwas.GWAS_PREC_MIXED
+    kw = {} if getattr(args, "batch_tile_cfg", None) is None else {"tile_cfg": args.batch_tile_cfg}
     b = gwas.gwas_batch_init(ns, p, t, precision=prec, m_blk=snps, device=local, timing=1,
-                             n_limbs=args.limbs, use_graph=1)
+                             n_limbs=args.limbs, use_graph=1, **kw)
     for k, n in enumerate(ns):
         c = synth.make_cohort(3000 + k, n, t=t, h=float(hs[k]), device=dev)
         gwas.gwas_batch_factor(b, k, np.asfortranarray(c.phi), True, c.h, c.sigma2, c.XL, c.Y)
@@ -890,8 +912,9 @@ def main():
                            "n=30k job timed as a rate)",
                "tolerance_rel_b": FP64_TOL["b"], "tolerance_wald": FP64_TOL["wald"],
                "value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
-               "steps": r["steps"], "setup_ms": r["setup_ms"], "roofline": r["roofline"],
-               "clocks": r["clocks"], "gpu_launches": r["gpu_launches"], "sample": r["sample"]}
+               "steps": r["steps"], "setup_ms": r["setup_ms"], "factor": r["factor"],
+               "roofline": r["roofline"], "clocks": r["clocks"],
+               "gpu_launches": r["gpu_launches"], "sample": r["sample"]}
         fp64_legs.append(leg)
         checks.append((leg, 30000))
     mixed = []
@@ -936,7 +959,8 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.limbs}+f64",
                 "data": "synthetic", "config": workload_config(args),
-                "setup_ms": res["setup_ms"], "roofline": res["roofline"], "e2e": res["e2e"],
+                "setup_ms": res["setup_ms"], "factor": res["factor"],
+                "roofline": res["roofline"], "e2e": res["e2e"],
                 "gpu_launches": res["gpu_launches"], "clocks": res["clocks"],
                 "status_ok_last_block": res["status_ok_last_block"]}
         if args.fp64_probe:

@@ -65,6 +65,9 @@ struct gwas_ctx {
     // and the first half's p x p solves run on s_aux beside the other half's block kernel
     cudaStream_t s_aux = nullptr;
     cudaEvent_t ev_conv0 = nullptr, ev_conv1 = nullptr, ev_blk0 = nullptr, ev_solve0 = nullptr;
+    // the blocked Cholesky's panel chain (highest stream priority) beside its trailing
+    // updates on s_comp
+    CholLookahead chol;
     int slot = 0;
     bool factored = false;
     std::string err;

@@ -26,6 +26,7 @@ struct gwas_batch {
     int n_parts = 1;
     int part_c0[kMaxParts + 1] = {};          // cohorts of part k: [part_c0[k], part_c0[k+1])
     int64_t part_snps[kMaxParts] = {}, part_units[kMaxParts] = {};
+    bool part_small[kMaxParts] = {};          // every cohort of part k has small limb sums
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_conv[kMaxParts] = {};      // part k's conversion done
     BatchJob* d_jobs = nullptr;
@@ -107,8 +108,8 @@ gwas_status batch_enqueue(gwas_batch* b) {
             CKB(launch_geno_bf16_batch(b->d_jobs + c0, nck, b->part_snps[k], st));
             if (P > 1) CKB(cudaEventRecord(b->ev_conv[k], st));
             CKB(launch_block_mixed_batch(b->d_tab + c0, b->d_maps + 3 * c0, nck, b->part_units[k],
-                                         b->ctx[0]->mx, b->stages, b->d_err, b->ctx[0]->num_sms,
-                                         st));
+                                         b->ctx[0]->mx, b->stages, b->d_err, b->part_small[k],
+                                         b->ctx[0]->num_sms, st));
             CKB(launch_snp_solve_batch(b->d_jobs + c0, nck, b->part_snps[k], b->p,
                                        b->q + 1 + b->t, true, st));
         }
@@ -234,8 +235,10 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
         if (b->mixed && nc > 1 && b->s2) {
             std::vector<int64_t> w(nc);
             int64_t total = 0;
-            for (int c = 0; c < nc; ++c) total += (w[c] = mixed_cohort_units(b->ctx[c]->mx, mb[c]));
-            P = std::min(nc, 2);
+            for (int c = 0; c < nc; ++c) total += (w[c] = mixed_cohort_work(b->ctx[c]->mx, mb[c]));
+            // tile_cfg bits 18-20: the number of parts (0 = two)
+            const int want = b->opts.tile_cfg >= 0 ? (b->opts.tile_cfg >> 18) & 7 : 0;
+            P = std::min(nc, std::min(gwas_batch::kMaxParts, want > 0 ? want : 2));
             int64_t acc = 0;
             int k = 1;
             for (int c = 0; c < nc && k < P; ++c) {
@@ -314,6 +317,11 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
         }
         b->part_snps[part] = snp;
         b->part_units[part] = umx;
+        for (int k = 0; k < P; ++k) {
+            b->part_small[k] = true;
+            for (int c = b->part_c0[k]; c < b->part_c0[k + 1]; ++c)
+                if (!b->mixed || !tab[c].small_sums) b->part_small[k] = false;
+        }
         b->total_snps = tot_snps;
         b->units_fp64 = u64;
         b->units_mx = tot_mx;
@@ -389,9 +397,11 @@ gwas_status gwas_batch_get_stats(gwas_batch* b, gwas_stats* out) {
     batch_fold_timings(b, true);
     gwas_stats agg = b->stats;
     agg.factor_ms = 0;
+    agg.factor_upload_ms = 0;
     agg.factor_launches = 0;
     for (auto* c : b->ctx) {
         agg.factor_ms += c->stats.factor_ms;
+        agg.factor_upload_ms += c->stats.factor_upload_ms;
         agg.factor_launches += c->stats.factor_launches;
     }
     *out = agg;

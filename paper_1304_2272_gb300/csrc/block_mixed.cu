@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -59,6 +60,7 @@ struct MixedArgs {
     int stages;
     int n_units;
     int* err;
+    int small_sums;  // every cohort of the launch has n 2^B < 2^22 (CohortMx::small_sums)
 };
 
 // Unit u -> (rt, ct) inside one cohort. Groups of `group` SNP tiles; inside a group the
@@ -88,7 +90,7 @@ __device__ __forceinline__ void record_error(int* err, volatile int* abort_flag,
 struct SrcOne {
     CUtensorMap tmX, tmW, tmE;
     MixedArgs a;
-    __device__ __forceinline__ const CohortMx* locate(int u, int& ci, int& local) const {
+    __device__ __forceinline__ const CohortMx* locate(int u, int& ci, int& local, int&) const {
         ci = 0;
         local = u;
         return &a.c;
@@ -102,16 +104,16 @@ struct SrcBatch {
     const CUtensorMap* maps;
     int n_cohorts;
     MixedArgs a;  // launch-wide fields; a.c unused
-    __device__ __forceinline__ const CohortMx* locate(int u, int& ci, int& local) const {
-        int lo = 0, hi = n_cohorts - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) / 2;
-            if (tab[mid].unit_base <= (int64_t)u) lo = mid;
-            else hi = mid - 1;
-        }
-        ci = lo;
-        local = (int)(u - tab[lo].unit_base);
-        return &tab[lo];
+    // cur: the cohort of the caller's previous unit. A CTA role takes its units in
+    // increasing order and the table's unit_base increases, so the cohort only moves
+    // forward: one table read per unit instead of a binary search of dependent reads.
+    __device__ __forceinline__ const CohortMx* locate(int u, int& ci, int& local, int& cur) const {
+        int c = cur;
+        while (c + 1 < n_cohorts && tab[c + 1].unit_base <= (int64_t)u) ++c;
+        cur = c;
+        ci = c;
+        local = (int)(u - tab[c].unit_base);
+        return &tab[c];
     }
     __device__ __forceinline__ const CUtensorMap* mapX(int ci) const { return maps + 3 * ci; }
     __device__ __forceinline__ const CUtensorMap* mapB(int ci, bool ex) const {
@@ -119,81 +121,137 @@ struct SrcBatch {
     }
 };
 
+// An exact integer held in an FP32 accumulator as an int. With |v| < 2^22, v + 1.5 2^23
+// lies in [2^23, 2^24), where the float spacing is 1, so the sum is exact and its low
+// mantissa bits are v + 2^22: one add and one integer subtract instead of a conversion.
+template <bool SMALL>
+__device__ __forceinline__ int limb_int(uint32_t bits) {
+    if (SMALL) return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
+    return __float2int_rn(__uint_as_float(bits));
+}
+
+// Adds T_i^2 over the rows of one 16-row group, T_i = sum_l C_il 2^(B (S-1-l)) exact in 64
+// bits (|C_il| < 2^24, so |T_i| < 2^60.01) and its square exact in 128 bits (a tile's sum of
+// squares stays below 2^126).
+template <int S, bool SMALL>
+__device__ __forceinline__ void sumsq_group(const uint32_t (&v)[S][16], int rows, int B,
+                                            unsigned __int128& acc) {
+    const long long base = 1ll << B;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (i < rows) {
+            long long T = 0;
+#pragma unroll
+            for (int l = 0; l < S; ++l) {
+                const int col = i * S + l;
+                T = T * base + (long long)limb_int<SMALL>(v[col / 16][col % 16]);
+            }
+            const unsigned long long uT = (unsigned long long)(T < 0 ? -T : T);
+            acc += (unsigned __int128)uT * uT;
+        }
+    }
+}
+
+// Rows 16 g .. 16 g + 15 of a row tile are the 16 S columns from 16 g S (a multiple of 16);
+// a last, shorter group loads ceil(rows S / 16) x 16 columns, which end at or before column
+// 256 because R S <= 256.
+template <int S>
+__device__ __forceinline__ void sumsq_load(uint32_t tb, int R, int g, uint32_t (&v)[S][16]) {
+    const int rows = min(16, R - 16 * g);
+    const int nld = (rows * S + 15) / 16;  // the same for every thread of the warp
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+        if (q < nld) tc::tmem_ld16(tb + (uint32_t)(16 * g * S + 16 * q), v[q]);
+}
+
+// Sum over the R rows of a row tile of T_i^2, the C_il being the S limb sums of row i in
+// TMEM columns i S + l. Up to 3 limbs the next 16-row group's TMEM loads are in flight
+// while a group is summed.
+template <int S, bool SMALL>
+__device__ __forceinline__ unsigned __int128 tile_sumsq(uint32_t tb, int R, int B) {
+    constexpr int G = (256 / S + 15) / 16;  // 16-row groups of the tallest tile
+    unsigned __int128 acc = 0;
+    if constexpr (S <= 3) {
+        uint32_t v[2][S][16];
+        sumsq_load<S>(tb, R, 0, v[0]);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (16 * g < R) {
+                tc::tmem_wait_ld();
+                if (16 * (g + 1) < R) sumsq_load<S>(tb, R, g + 1, v[(g + 1) & 1]);
+                sumsq_group<S, SMALL>(v[g & 1], min(16, R - 16 * g), B, acc);
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int g = 0; 16 * g < R; ++g) {
+            uint32_t v[S][16];
+            sumsq_load<S>(tb, R, g, v);
+            tc::tmem_wait_ld();
+            sumsq_group<S, SMALL>(v, min(16, R - 16 * g), B, acc);
+        }
+    }
+    return acc;
+}
+
+// The linear reductions of one unit: R_e values T_j = sum_l C_lj 2^(B (S-1-l)) whose limb
+// sums sit in TMEM columns col0 + l R_e + j, written as T_j 2^(E_j - shift0) to
+// lin[(e0 + j) ldp + snp]. The loads of JB linear rows (JB S columns) are issued together
+// and waited for once.
+template <int S>
+__device__ __forceinline__ void linear_rows(const CohortMx& a, int R_e, uint32_t col0, int64_t e0,
+                                            int64_t snp) {
+    using namespace tc;
+    constexpr int JB = 8;
+    const int B = a.radix;
+    const long long base = 1ll << B;
+    const int shift0 = (B - 1) + B * (S - 1);
+#pragma unroll 1
+    for (int j0 = 0; j0 < R_e; j0 += JB) {
+        const int nj = min(JB, R_e - j0);  // the same for every thread of the warp
+        uint32_t x[S][JB];
+#pragma unroll
+        for (int l = 0; l < S; ++l)
+#pragma unroll
+            for (int j = 0; j < JB; ++j)
+                if (j < nj) tmem_ld1(col0 + (uint32_t)(l * R_e + j0 + j), x[l][j]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < JB; ++j) {
+            if (j < nj) {
+                long long T = 0;
+#pragma unroll
+                for (int l = 0; l < S; ++l)
+                    T = T * base + (long long)__float2int_rn(__uint_as_float(x[l][j]));
+                const int64_t e = e0 + j0 + j;
+                if (snp < a.mb) a.lin[e * a.ldp + snp] = ldexp((double)T, a.E_e[e] - shift0);
+            }
+        }
+    }
+}
+
 // Epilogue of one unit for the SNP held in TMEM lane `tb` (one thread = one SNP):
 // row tiles -> sum over the tile's R rows of xbar^2, exact in 128-bit integers, plus (when
 // the linear rows are fused) the tile's partial linear reductions from the fused columns;
 // the linear tile -> the q + t linear reductions.
-template <int S>
+template <int S, bool SMALL>
 __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32_t tb, int rt,
                                               int64_t snp) {
     using namespace tc;
     // x = 2^(E - shift0) T with T = sum_l C_l 2^(B (S-1-l)), B = a.radix bits per limb
     const int B = a.radix;
-    const long long base = 1ll << B;
     const int shift0 = (B - 1) + B * (S - 1);
     const int R = a.R;
     if (rt != (int)mx::EXTRA) {
-        unsigned __int128 acc = 0;
-        // 16 rows at a time: rows i0 .. i0+15 are the 16 S columns from i0 S (a multiple of
-        // 16); a last, shorter group loads ceil(rows S / 16) x 16 columns, which end at or
-        // before column 256 because R S <= 256
-#pragma unroll 1
-        for (int i0 = 0; i0 < R; i0 += 16) {
-            const int rows = min(16, R - i0);
-            const int nld = (rows * S + 15) / 16;  // the same for every thread of the warp
-            uint32_t v[S][16];
-#pragma unroll
-            for (int g = 0; g < S; ++g)
-                if (g < nld) tmem_ld16(tb + (uint32_t)(i0 * S + 16 * g), v[g]);
-            tmem_wait_ld();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                if (i < rows) {
-                    long long T = 0;
-#pragma unroll
-                    for (int l = 0; l < S; ++l) {
-                        const int col = i * S + l;
-                        T = T * base +
-                            (long long)__float2int_rn(__uint_as_float(v[col / 16][col % 16]));
-                    }
-                    const unsigned long long uT = (unsigned long long)(T < 0 ? -T : T);
-                    acc += (unsigned __int128)uT * uT;
-                }
-            }
-        }
+        const unsigned __int128 acc = tile_sumsq<S, SMALL>(tb, R, B);
         const double hi = (double)(unsigned long long)(acc >> 64);
         const double lo = (double)(unsigned long long)acc;
         const double val = ldexp(fma(hi, 18446744073709551616.0, lo), 2 * (a.E_w[rt] - shift0));
         if (snp < a.mb) a.sq_part[(int64_t)rt * a.ldp + snp] = val;
-        if (!a.extra) {
-            // fused linear rows: Z limbs of this tile's k-range, one partial per (rt, j)
-#pragma unroll 1
-            for (int j = 0; j < R_e; ++j) {
-                long long T = 0;
-#pragma unroll
-                for (int l = 0; l < S; ++l) {
-                    uint32_t x;
-                    tmem_ld1(tb + (uint32_t)(R * S + l * R_e + j), x);
-                    tmem_wait_ld();
-                    T = T * base + (long long)__float2int_rn(__uint_as_float(x));
-                }
-                const int64_t e = (int64_t)rt * R_e + j;
-                if (snp < a.mb) a.lin[e * a.ldp + snp] = ldexp((double)T, a.E_e[e] - shift0);
-            }
-        }
+        // fused linear rows: Z limbs of this tile's k-range, one partial per (rt, j)
+        if (!a.extra) linear_rows<S>(a, R_e, tb + (uint32_t)(R * S), (int64_t)rt * R_e, snp);
     } else {
-#pragma unroll 1
-        for (int j = 0; j < R_e; ++j) {
-            long long T = 0;
-#pragma unroll
-            for (int l = 0; l < S; ++l) {
-                uint32_t x;
-                tmem_ld1(tb + (uint32_t)(l * R_e + j), x);
-                tmem_wait_ld();
-                T = T * base + (long long)__float2int_rn(__uint_as_float(x));
-            }
-            if (snp < a.mb) a.lin[(int64_t)j * a.ldp + snp] = ldexp((double)T, a.E_e[j] - shift0);
-        }
+        linear_rows<S>(a, R_e, tb, 0, snp);
     }
 }
 
@@ -257,11 +315,12 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
         uint32_t issued_parity[16];
         bool issued[16];
         for (int s = 0; s < 16; ++s) issued[s] = false;
+        int cur = 0;  // cohort cursor (see SrcBatch::locate)
         for (int r = 0; r < rounds && !*abort_flag; ++r) {
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
             int ci, lu, rt, ct;
-            const CohortMx& cm = *src.locate(u, ci, lu);
+            const CohortMx& cm = *src.locate(u, ci, lu, cur);
             decode_unit(cm, lu, rt, ct);
             const bool ex = (rt == (int)mx::EXTRA);
             const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R - cm.off + mx::BK - 1) / mx::BK, cm.n_kc_full);
@@ -297,11 +356,12 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
         uint32_t phase = 0;
         int abuf = 0;
         uint32_t aphase = 0;
+        int cur = 0;  // cohort cursor (see SrcBatch::locate)
         for (int r = 0; r < rounds && !*abort_flag; ++r) {
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
             int ci, lu, rt, ct;
-            const CohortMx& cm = *src.locate(u, ci, lu);
+            const CohortMx& cm = *src.locate(u, ci, lu, cur);
             decode_unit(cm, lu, rt, ct);
             const bool ex = (rt == (int)mx::EXTRA);
             const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R - cm.off + mx::BK - 1) / mx::BK, cm.n_kc_full);
@@ -341,28 +401,37 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed(const __grid_constant__ 
         mbar_wait(done, 0, mx::WAIT_NS);
     } else if (warp >= 4) {
         // ---------------- epilogue: one SNP per thread ----------------
-        const int qd = warp & 3;
-        int abuf = 0;
-        uint32_t aphase = 0;
-        for (int r = 0; r < rounds && !*abort_flag; ++r) {
-            const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
-            if (u >= a.n_units) continue;
-            int ci, lu, rt, ct;
-            const CohortMx& cm = *src.locate(u, ci, lu);
-            decode_unit(cm, lu, rt, ct);
-            if (!mbar_wait(&tfull[abuf], aphase, mx::WAIT_NS)) {
-                record_error(a.err, abort_flag, 4);
-                break;
+        // (one copy of the loop per conversion: a branch inside it would keep both live)
+        auto role = [&](auto small) {
+            constexpr bool SMALL = decltype(small)::value;
+            const int qd = warp & 3;
+            int abuf = 0;
+            uint32_t aphase = 0;
+            int cur = 0;  // cohort cursor (see SrcBatch::locate)
+            for (int r = 0; r < rounds && !*abort_flag; ++r) {
+                const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
+                if (u >= a.n_units) continue;
+                int ci, lu, rt, ct;
+                const CohortMx& cm = *src.locate(u, ci, lu, cur);
+                decode_unit(cm, lu, rt, ct);
+                if (!mbar_wait(&tfull[abuf], aphase, mx::WAIT_NS)) {
+                    record_error(a.err, abort_flag, 4);
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t tb =
+                    tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
+                epilogue_unit<S, SMALL>(cm, a.R_e, tb, rt,
+                                        (int64_t)(cm.ct_base + ct) * mx::BM + qd * 32 + lane);
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[abuf]);
+                abuf ^= 1;
+                if (abuf == 0) aphase ^= 1;
             }
-            fence_after_sync();
-            const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
-            epilogue_unit<S>(cm, a.R_e, tb, rt, (int64_t)(cm.ct_base + ct) * mx::BM + qd * 32 + lane);
-            fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[abuf]);
-            abuf ^= 1;
-            if (abuf == 0) aphase ^= 1;
-        }
+        };
+        if (a.small_sums) role(std::true_type{});
+        else role(std::false_type{});
     }
     __syncthreads();
     if (warp == 0) {
@@ -448,11 +517,12 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed2(const __grid_constant__
         uint32_t issued_parity[16];
         bool issued[16];
         for (int s = 0; s < 16; ++s) issued[s] = false;
+        int cur = 0;  // cohort cursor (see SrcBatch::locate)
         for (int r = 0; r < rounds && !*abort_flag; ++r) {
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
             int ci, lu, rt, ctp;
-            const CohortMx& cm = *src.locate(u, ci, lu);
+            const CohortMx& cm = *src.locate(u, ci, lu, cur);
             decode_unit(cm, lu, rt, ctp);
             const bool ex = (rt == (int)mx::EXTRA);
             const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R - cm.off + mx::BK - 1) / mx::BK, cm.n_kc_full);
@@ -488,11 +558,12 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed2(const __grid_constant__
         uint32_t phase = 0;
         int abuf = 0;
         uint32_t aphase = 0;
+        int cur = 0;  // cohort cursor (see SrcBatch::locate)
         for (int r = 0; r < rounds && !*abort_flag; ++r) {
             const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
             if (u >= a.n_units) continue;
             int ci, lu, rt, ctp;
-            const CohortMx& cm = *src.locate(u, ci, lu);
+            const CohortMx& cm = *src.locate(u, ci, lu, cur);
             decode_unit(cm, lu, rt, ctp);
             const bool ex = (rt == (int)mx::EXTRA);
             const int nk = ex ? cm.n_kc_full : min(((rt + 1) * cm.R - cm.off + mx::BK - 1) / mx::BK, cm.n_kc_full);
@@ -531,29 +602,37 @@ __global__ void __launch_bounds__(256, 1) k_block_mixed2(const __grid_constant__
         mbar_wait(done, 0, mx::WAIT_NS);
     } else if (warp >= 4) {
         // ---------------- epilogue (both CTAs): one SNP per thread ----------------
-        const int qd = warp & 3;
-        int abuf = 0;
-        uint32_t aphase = 0;
-        for (int r = 0; r < rounds && !*abort_flag; ++r) {
-            const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
-            if (u >= a.n_units) continue;
-            int ci, lu, rt, ctp;
-            const CohortMx& cm = *src.locate(u, ci, lu);
-            decode_unit(cm, lu, rt, ctp);
-            if (!mbar_wait(&tfull[abuf], aphase, mx::WAIT_NS)) {
-                record_error(a.err, abort_flag, 14);
-                break;
+        // (one copy of the loop per conversion: a branch inside it would keep both live)
+        auto role = [&](auto small) {
+            constexpr bool SMALL = decltype(small)::value;
+            const int qd = warp & 3;
+            int abuf = 0;
+            uint32_t aphase = 0;
+            int cur = 0;  // cohort cursor (see SrcBatch::locate)
+            for (int r = 0; r < rounds && !*abort_flag; ++r) {
+                const int u = r * P + ((r & 1) ? (P - 1 - me) : me);
+                if (u >= a.n_units) continue;
+                int ci, lu, rt, ctp;
+                const CohortMx& cm = *src.locate(u, ci, lu, cur);
+                decode_unit(cm, lu, rt, ctp);
+                if (!mbar_wait(&tfull[abuf], aphase, mx::WAIT_NS)) {
+                    record_error(a.err, abort_flag, 14);
+                    break;
+                }
+                fence_after_sync();
+                const uint32_t tb =
+                    tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
+                const int ct = cm.ct_base + 2 * ctp + (int)rank;
+                epilogue_unit<S, SMALL>(cm, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[abuf]), 0));
+                abuf ^= 1;
+                if (abuf == 0) aphase ^= 1;
             }
-            fence_after_sync();
-            const uint32_t tb = tmem_base + (uint32_t)(abuf * mx::BUF) + ((uint32_t)(qd * 32) << 16);
-            const int ct = cm.ct_base + 2 * ctp + (int)rank;
-            epilogue_unit<S>(cm, a.R_e, tb, rt, (int64_t)ct * mx::BM + qd * 32 + lane);
-            fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&tempty[abuf]), 0));
-            abuf ^= 1;
-            if (abuf == 0) aphase ^= 1;
-        }
+        };
+        if (a.small_sums) role(std::true_type{});
+        else role(std::false_type{});
     }
     __syncthreads();
     cluster_sync();  // no CTA leaves while its peer may still signal it or use its TMEM
@@ -678,6 +757,7 @@ static CohortMx make_cohort(const MixedDev& m, int64_t mb, bool pair, int64_t sn
     c.unit_base = 0;
     c.extra = m.fused ? 0 : 1;
     c.radix = m.radix;
+    c.small_sums = ((int64_t)m.n << m.radix) < (1ll << 22) ? 1 : 0;
     c.R = m.R;
     c.off = m.row_off();
     c.E_w = m.E;
@@ -696,6 +776,7 @@ static MixedArgs make_args(const MixedDev& m, int64_t mb, bool pair, int64_t snp
     if (m.cfg_stages >= 2) a.stages = std::min(a.stages, m.cfg_stages);
     a.n_units = a.c.n_ct * (a.c.n_rt + a.c.extra);
     a.err = m.err;
+    a.small_sums = a.c.small_sums;
     return a;
 }
 
@@ -805,6 +886,15 @@ int64_t mixed_cohort_units(const MixedDev& m, int64_t mb) {
     return (int64_t)c.n_ct * (c.n_rt + c.extra);
 }
 
+int64_t mixed_cohort_work(const MixedDev& m, int64_t mb) {
+    const CohortMx c = make_cohort(m, mb, m.pair);
+    int64_t chunks = 0;  // k-chunks of one SNP tile over its row tiles (as the kernel runs them)
+    for (int rt = 0; rt < c.n_rt; ++rt)
+        chunks += std::min<int64_t>(ceil_div((int64_t)(rt + 1) * c.R - c.off, mx::BK), c.n_kc_full);
+    if (c.extra) chunks += ceil_div((int64_t)c.n_kc_full * m.N_e, mx::NT);
+    return (int64_t)c.n_ct * chunks;
+}
+
 template <int S>
 static cudaError_t batch_prepare_t(int N_e, int stages, bool pair) {
     const size_t smem = smem_bytes(mx::NT, N_e, pair, stages);
@@ -820,7 +910,7 @@ static cudaError_t batch_prepare_t(int N_e, int stages, bool pair) {
 template <int S>
 static cudaError_t batch_launch_t(const CohortMx* tab, const CUtensorMap* maps, int n_cohorts,
                                   int n_units, int R_e, int N_e, int stages, bool pair, int* err,
-                                  int num_sms, cudaStream_t s) {
+                                  bool small_sums, int num_sms, cudaStream_t s) {
     SrcBatch src;
     src.tab = tab;
     src.maps = maps;
@@ -831,6 +921,7 @@ static cudaError_t batch_launch_t(const CohortMx* tab, const CUtensorMap* maps, 
     src.a.stages = stages;
     src.a.n_units = n_units;
     src.a.err = err;
+    src.a.small_sums = small_sums ? 1 : 0;
     const size_t smem = smem_bytes(mx::NT, N_e, pair, stages);
     if (pair) return launch_clusters(k_block_mixed2<S, SrcBatch>, src, smem, n_units, num_sms, s);
     const int grid = std::max(1, std::min(num_sms, n_units));
@@ -848,13 +939,13 @@ cudaError_t mixed_batch_prepare(const MixedDev& m, int stages) {
 
 cudaError_t launch_block_mixed_batch(const CohortMx* tab, const CUtensorMap* maps, int n_cohorts,
                                      int64_t n_units, const MixedDev& m, int stages, int* err,
-                                     int num_sms, cudaStream_t s) {
+                                     bool small_sums, int num_sms, cudaStream_t s) {
     if (n_units <= 0) return cudaSuccess;
     if (n_units > 0x7fffffffLL) return cudaErrorInvalidValue;
 #define GWAS_TRY(SS)                                                                     \
     if (m.S == SS)                                                                       \
         return batch_launch_t<SS>(tab, maps, n_cohorts, (int)n_units, m.R_e, m.N_e, stages, \
-                                  m.pair, err, num_sms, s);
+                                  m.pair, err, small_sums, num_sms, s);
     GWAS_MIXED_LIMBS(GWAS_TRY)
 #undef GWAS_TRY
     return cudaErrorInvalidValue;

@@ -426,57 +426,112 @@ __global__ void __launch_bounds__(256) k_potrf_diag(double* __restrict__ A, int6
 // 64-column blocks (diagonal block in shared memory, the rows below by D_k^T, then the
 // rank-64 update of the panel's remaining columns only); the columns right of the panel
 // get one rank-NB update per panel, so the large trailing GEMMs run with K = 256.
-cudaError_t cholesky_blocked(double* A, int64_t lda, int64_t n, double* Dinv, int* d_info,
-                             cudaStream_t s, int64_t* launches) {
-    constexpr int64_t NB = 4 * T64;
-    int64_t nl = 0;
-    const int smem = POTRF_SMEM;
-    cudaError_t e = cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    for (int64_t p0 = 0; p0 < n; p0 += NB) {
-        const int64_t pend = std::min<int64_t>(n, p0 + NB);  // panel columns [p0, pend)
-        for (int64_t k0 = p0; k0 < pend; k0 += T64) {
-            const int kb = (int)std::min<int64_t>(T64, n - k0);
-            double* Akk = A + k0 + k0 * lda;
-            double* Dk = Dinv + (k0 / T64) * T64 * T64;
-            k_potrf_diag<<<1, 256, smem, s>>>(Akk, lda, kb, k0, Dk, d_info);
-            ++nl;
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            const int64_t below = n - k0 - kb;
-            if (below <= 0) break;
-            double* P = A + (k0 + kb) + k0 * lda;  // rows below the block
-            // L_ik := A_ik L_kk^{-T} = A_ik D_k^T (one column tile: in place is safe)
-            GemmF64 g;
-            g.M = below; g.N = kb; g.K = kb;
-            g.A = P; g.lda = lda; g.B = Dk; g.ldb = T64; g.transB = true;
-            g.C = P; g.ldc = lda;
-            if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
-            ++nl;
-            // the panel's remaining columns [k0 + kb, pend) -= L_below L_(those rows)^T
-            const int64_t w = pend - (k0 + kb);
-            if (w > 0) {
-                GemmF64 u;
-                u.M = below; u.N = w; u.K = kb;
-                u.A = P; u.lda = lda; u.B = P; u.ldb = lda; u.transB = true;
-                u.C = A + (k0 + kb) + (k0 + kb) * lda; u.ldc = lda;
-                u.alpha = -1.0; u.beta = 1.0; u.c_lower = true;
-                if ((e = gemm_f64(u, s)) != cudaSuccess) return e;
-                ++nl;
-            }
-        }
-        // A22 -= L_(rows >= pend, panel) L_(rows >= pend, panel)^T (lower tiles only)
-        const int64_t rest = n - pend;
-        if (rest > 0) {
-            double* Q = A + pend + p0 * lda;
+namespace {
+
+constexpr int64_t CHOL_NB = 4 * T64;  // panel width
+
+// Panel [p0, pend) of the factor, in 64-column blocks: the diagonal block in shared memory
+// (D_k = L_kk^{-1} into Dinv), the rows below it by D_k^T, then the rank-64 update of the
+// panel's remaining columns only.
+cudaError_t factor_panel(double* A, int64_t lda, int64_t n, int64_t p0, int64_t pend, double* Dinv,
+                         int* d_info, cudaStream_t s, int64_t& nl) {
+    cudaError_t e;
+    for (int64_t k0 = p0; k0 < pend; k0 += T64) {
+        const int kb = (int)std::min<int64_t>(T64, n - k0);
+        double* Akk = A + k0 + k0 * lda;
+        double* Dk = Dinv + (k0 / T64) * T64 * T64;
+        k_potrf_diag<<<1, 256, POTRF_SMEM, s>>>(Akk, lda, kb, k0, Dk, d_info);
+        ++nl;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const int64_t below = n - k0 - kb;
+        if (below <= 0) break;
+        double* P = A + (k0 + kb) + k0 * lda;  // rows below the block
+        // L_ik := A_ik L_kk^{-T} = A_ik D_k^T (one column tile: in place is safe)
+        GemmF64 g;
+        g.M = below; g.N = kb; g.K = kb;
+        g.A = P; g.lda = lda; g.B = Dk; g.ldb = T64; g.transB = true;
+        g.C = P; g.ldc = lda;
+        if ((e = gemm_f64(g, s)) != cudaSuccess) return e;
+        ++nl;
+        // the panel's remaining columns [k0 + kb, pend) -= L_below L_(those rows)^T
+        const int64_t w = pend - (k0 + kb);
+        if (w > 0) {
             GemmF64 u;
-            u.M = rest; u.N = rest; u.K = pend - p0;
-            u.A = Q; u.lda = lda; u.B = Q; u.ldb = lda; u.transB = true;
-            u.C = A + pend + pend * lda; u.ldc = lda;
+            u.M = below; u.N = w; u.K = kb;
+            u.A = P; u.lda = lda; u.B = P; u.ldb = lda; u.transB = true;
+            u.C = A + (k0 + kb) + (k0 + kb) * lda; u.ldc = lda;
             u.alpha = -1.0; u.beta = 1.0; u.c_lower = true;
             if ((e = gemm_f64(u, s)) != cudaSuccess) return e;
             ++nl;
         }
     }
+    return cudaSuccess;
+}
+
+// Columns [c0, c1) of the trailing matrix, rows c0 .. n-1 (lower tiles only):
+// A(c0:, c0:c1) -= L(c0:, p0:pend) L(c0:c1, p0:pend)^T. Every 64 x 64 output tile of a
+// column range sits on the same grid from the diagonal and sums over the same k order,
+// so splitting [pend, n) into column ranges leaves each element's arithmetic unchanged.
+cudaError_t trailing_update(double* A, int64_t lda, int64_t n, int64_t p0, int64_t pend,
+                            int64_t c0, int64_t c1, cudaStream_t s, int64_t& nl) {
+    if (c1 <= c0) return cudaSuccess;
+    const double* Q = A + c0 + p0 * lda;
+    GemmF64 u;
+    u.M = n - c0; u.N = c1 - c0; u.K = pend - p0;
+    u.A = Q; u.lda = lda; u.B = Q; u.ldb = lda; u.transB = true;
+    u.C = A + c0 + c0 * lda; u.ldc = lda;
+    u.alpha = -1.0; u.beta = 1.0; u.c_lower = true;
+    ++nl;
+    return gemm_f64(u, s);
+}
+
+}  // namespace
+
+cudaError_t cholesky_blocked(double* A, int64_t lda, int64_t n, double* Dinv, int* d_info,
+                             cudaStream_t s, int64_t* launches, const CholLookahead* la) {
+    int64_t nl = 0;
+    cudaError_t e = cudaFuncSetAttribute(k_potrf_diag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         POTRF_SMEM);
+    if (e != cudaSuccess) return e;
+    if (!la || !la->panel) {
+        for (int64_t p0 = 0; p0 < n; p0 += CHOL_NB) {
+            const int64_t pend = std::min<int64_t>(n, p0 + CHOL_NB);
+            if ((e = factor_panel(A, lda, n, p0, pend, Dinv, d_info, s, nl)) != cudaSuccess) return e;
+            if ((e = trailing_update(A, lda, n, p0, pend, pend, n, s, nl)) != cudaSuccess) return e;
+        }
+        if (launches) *launches += nl;
+        return cudaSuccess;
+    }
+    // Lookahead by one panel. Panel p's trailing update is split at the end of panel p+1:
+    // (a) its columns [pend, pend2) go on the panel stream, right before panel p+1 is
+    // factored there; (b) the columns [pend2, n) go on s. Panel p+1 (and (a)) also need
+    // panel p-1's (b), which updated the same columns, so the panel stream waits for it
+    // first; (b) of panel p then runs on s beside (a) and the factorisation of panel p+1.
+    cudaStream_t sp = la->panel;
+    cudaEvent_t ev_start = la->ev[0], ev_panel = la->ev[1], ev_rest = la->ev[2];
+#define CKL(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
+    CKL(cudaEventRecord(ev_start, s));
+    CKL(cudaStreamWaitEvent(sp, ev_start, 0));
+    bool rest_pending = false;  // a (b) update on s that the panel stream has not waited for
+    for (int64_t p0 = 0; p0 < n; p0 += CHOL_NB) {
+        const int64_t pend = std::min<int64_t>(n, p0 + CHOL_NB);
+        CKL(factor_panel(A, lda, n, p0, pend, Dinv, d_info, sp, nl));
+        if (pend >= n) break;
+        const int64_t pend2 = std::min<int64_t>(n, pend + CHOL_NB);
+        CKL(cudaEventRecord(ev_panel, sp));
+        if (rest_pending) CKL(cudaStreamWaitEvent(sp, ev_rest, 0));  // panel p-1's (b)
+        CKL(cudaStreamWaitEvent(s, ev_panel, 0));
+        rest_pending = false;
+        if (pend2 < n) {
+            CKL(trailing_update(A, lda, n, p0, pend, pend2, n, s, nl));  // (b)
+            CKL(cudaEventRecord(ev_rest, s));
+            rest_pending = true;
+        }
+        CKL(trailing_update(A, lda, n, p0, pend, pend, pend2, sp, nl));  // (a)
+    }
+    CKL(cudaEventRecord(ev_panel, sp));
+    CKL(cudaStreamWaitEvent(s, ev_panel, 0));
+#undef CKL
     if (launches) *launches += nl;
     return cudaSuccess;
 }

@@ -175,6 +175,9 @@ void free_all(gwas_ctx* c) {
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t ev : {c->ev_conv0, c->ev_conv1, c->ev_blk0, c->ev_solve0})
         if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : c->chol.ev)
+        if (ev) cudaEventDestroy(ev);
+    if (c->chol.panel) cudaStreamDestroy(c->chol.panel);
     if (c->s_aux) cudaStreamDestroy(c->s_aux);
     if (c->s_comp) cudaStreamDestroy(c->s_comp);
     if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
@@ -282,6 +285,12 @@ gwas_status gwas_init(int64_t n, int p, int t, const gwas_opts* opts, gwas_ctx**
         CKI(cudaEventCreateWithFlags(&c->ev_d2h[s], cudaEventDisableTiming));
     }
     CKI(cudaStreamCreateWithFlags(&c->s_comp, cudaStreamNonBlocking));
+    {
+        int least = 0, greatest = 0;
+        CKI(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CKI(cudaStreamCreateWithPriority(&c->chol.panel, cudaStreamNonBlocking, greatest));
+        for (cudaEvent_t& ev : c->chol.ev) CKI(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
     if (c->mixed) {
         CKI(cudaStreamCreateWithFlags(&c->s_aux, cudaStreamNonBlocking));
         for (cudaEvent_t* ev : {&c->ev_conv0, &c->ev_conv1, &c->ev_blk0, &c->ev_solve0})
@@ -316,11 +325,19 @@ gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double 
     // Phi (or M) is staged in the W buffer, then M is built into L's buffer.
     CK(cudaMemcpy2DAsync(c->W, ld * sizeof(double), M_or_Phi, n * sizeof(double),
                          n * sizeof(double), n, cudaMemcpyDefault, s));
-    CK(launch_build_M(c->W, ld, c->L, ld, n, is_phi, h, sigma2, s));
-    ++nl;
+    // [X_L | Y] (kept for the REML identities); the inputs are all on the device from here
+    if (!c->XLY) CK(dmalloc(&c->XLY, (size_t)n * (c->q + c->t)));
+    double* XLin = c->XLY;
+    double* Yin = XLin + (size_t)n * c->q;
+    CK(cudaMemcpyAsync(XLin, XL, (size_t)n * c->q * sizeof(double), cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(Yin, Y, (size_t)n * c->t * sizeof(double), cudaMemcpyDefault, s));
     const int init = 0x7fffffff;
     CK(cudaMemcpyAsync(c->d_info, &init, sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cholesky_blocked(c->L, ld, n, c->Dinv, c->d_info, s, &nl));
+    cudaEvent_t fu = pooled_event(c);
+    CK(cudaEventRecord(fu, s));
+    CK(launch_build_M(c->W, ld, c->L, ld, n, is_phi, h, sigma2, s));
+    ++nl;
+    CK(cholesky_blocked(c->L, ld, n, c->Dinv, c->d_info, s, &nl, &c->chol));
     // W := L^{-1}
     CK(cudaMemsetAsync(c->W, 0, (size_t)ld * ld * sizeof(double), s));
     const int64_t half = round_up(ceil_div(n, 2), T64);
@@ -328,12 +345,7 @@ gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double 
     CK(cudaMalloc(&tmp_buf.p, (size_t)half * half * sizeof(double)));
     double* tmp = (double*)tmp_buf.p;
     CK(trtri_lower(c->L, ld, n, c->Dinv, c->W, ld, tmp, s, &nl));
-    // Xbar_L := W X_L, Ybar := W Y ([X_L | Y] is kept for the REML identities)
-    if (!c->XLY) CK(dmalloc(&c->XLY, (size_t)n * (c->q + c->t)));
-    double* XLin = c->XLY;
-    double* Yin = XLin + (size_t)n * c->q;
-    CK(cudaMemcpyAsync(XLin, XL, (size_t)n * c->q * sizeof(double), cudaMemcpyDefault, s));
-    CK(cudaMemcpyAsync(Yin, Y, (size_t)n * c->t * sizeof(double), cudaMemcpyDefault, s));
+    // Xbar_L := W X_L, Ybar := W Y
     {
         GemmF64 a;
         a.M = n; a.N = c->q; a.K = n; a.A = c->W; a.lda = ld; a.a_lower = true;
@@ -395,11 +407,14 @@ gwas_status gwas_factor(gwas_ctx* c, const double* M_or_Phi, int is_phi, double 
     if (probe_st)
         CK(cudaMemcpyAsync(&ones_status, probe_st, 1, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    float ms = 0.f;
+    float ms = 0.f, ms_up = 0.f;
     cudaEventElapsedTime(&ms, f0, f1);
+    cudaEventElapsedTime(&ms_up, f0, fu);
     c->ev_pool.push_back(f0);
     c->ev_pool.push_back(f1);
+    c->ev_pool.push_back(fu);
     c->stats.factor_ms = ms;
+    c->stats.factor_upload_ms = ms_up;
     c->stats.factor_launches = nl;
     c->ones_singular = (ones_status == 1);
     if (info != init) {
@@ -639,10 +654,11 @@ gwas_status gwas_reset_stats(gwas_ctx* c) {
     if (!c) return GWAS_ERR_ARG;
     gwas_stats tmp;
     gwas_status st = gwas_get_stats(c, &tmp);
-    const double fms = c->stats.factor_ms;
+    const double fms = c->stats.factor_ms, fup = c->stats.factor_upload_ms;
     const int64_t fl = c->stats.factor_launches;
     c->stats = gwas_stats{};
     c->stats.factor_ms = fms;
+    c->stats.factor_upload_ms = fup;
     c->stats.factor_launches = fl;
     return st;
 }

@@ -19,8 +19,19 @@ cudaError_t launch_build_M(const double* src, int64_t lds, double* M, int64_t ld
 // (nt blocks of 64 x 64, col-major, zero padded) and the first non-positive pivot
 // (global index) into *d_info (left untouched when the factorisation succeeds).
 // Returns the number of kernels launched through *launches.
+//
+// With a lookahead stream (CholLookahead::panel non-null, created with a higher priority
+// than s), each panel's factorisation and the update of the next panel's columns run on
+// it, beside the update of the columns right of the next panel on s; the same tiles are
+// computed in the same order as without it, so the factor is bitwise the same. s waits
+// for the panel stream before the function returns.
+struct CholLookahead {
+    cudaStream_t panel = nullptr;
+    cudaEvent_t ev[3] = {};  // start, panel factored, trailing update done
+};
 cudaError_t cholesky_blocked(double* A, int64_t lda, int64_t n, double* Dinv, int* d_info,
-                             cudaStream_t s, int64_t* launches);
+                             cudaStream_t s, int64_t* launches,
+                             const CholLookahead* la = nullptr);
 
 // W := L^{-1} (lower triangular, zeros above the diagonal) by the recursive block
 // formula [[L11,0],[L21,L22]]^{-1} = [[W11,0],[-W22 L21 W11, W22]], with the
@@ -104,6 +115,7 @@ struct CohortMx {
     int R;              // rows of L^{-1} per row tile (limb i, l in column i*S + l)
     int off;            // n_rt R - n: row tile rt holds rows rt R - off .. (rt + 1) R - off
     int ct_base;        // first 128-SNP tile of the launch (its SNPs start at 128 ct_base)
+    int small_sums;     // 1: n 2^B < 2^22, so every limb sum in TMEM is below 2^22
     const int* E_w;     // exponent per row tile
     const int* E_e;     // exponent per linear row (fused: per (row tile, linear row))
     double* sq_part;    // [n_rt][ldp]
@@ -181,10 +193,14 @@ cudaError_t launch_snp_solve_mixed(const CohortDev& c, const MixedDev& m, const 
 int mixed_stage_count(const MixedDev& m);
 CohortMx mixed_cohort_entry(const MixedDev& m, int64_t mb, int64_t unit_base);
 int64_t mixed_cohort_units(const MixedDev& m, int64_t mb);
+// Tensor work of a cohort's units in full-width k-chunks (the linear tile at its width).
+int64_t mixed_cohort_work(const MixedDev& m, int64_t mb);
 cudaError_t mixed_batch_prepare(const MixedDev& m, int stages);
+// small_sums: every cohort of the table has CohortMx::small_sums set (the faster exact
+// conversion of the limb sums); otherwise all take the general one.
 cudaError_t launch_block_mixed_batch(const CohortMx* tab, const CUtensorMap* maps, int n_cohorts,
                                      int64_t n_units, const MixedDev& m, int stages, int* err,
-                                     int num_sms, cudaStream_t s);
+                                     bool small_sums, int num_sms, cudaStream_t s);
 
 // ---- batched FP64 path, dosage conversion and p x p solves (batch.cu) ------------------
 

@@ -44,7 +44,7 @@ class gwas_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("trsm_launches", ctypes.c_int64),
                 ("trsm_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64), ("factor_ms", ctypes.c_double),
-                ("factor_launches", ctypes.c_int64)]
+                ("factor_launches", ctypes.c_int64), ("factor_upload_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -163,3 +163,17 @@ def test_oracle_errors_report_a_planted_error():
     e = bench.oracle_errors(L, c, sample)
     assert abs(e["err_b"] - 1e-7) < 1e-9 and abs(e["err_wald"] - 1e-6) < 1e-8
     assert not e["status_match"]
+
+
+def test_factor_record_excludes_the_upload():
+    """The factor's rate is taken over its device time without the host uploads, at
+    2n^3/3 flops, and compared with the probed FP64 fma rate when there is one."""
+    import types
+    st = {"factor_ms": 600.0, "factor_upload_ms": 80.0, "factor_launches": 500}
+    args = types.SimpleNamespace(fp64_probe={"tflops": 1.25})
+    r = bench.factor_record(st, 10000, args)
+    assert r["compute_ms"] == 520.0 and r["upload_ms"] == 80.0 and r["launches"] == 500
+    assert abs(r["fp64_tflops"] - 2e12 / 3 / 0.52 / 1e12) < 1e-12
+    assert abs(r["frac_of_fma_rate"] - r["fp64_tflops"] / 1.25) < 1e-12
+    r = bench.factor_record(st, 10000, types.SimpleNamespace(fp64_probe=None))
+    assert "frac_of_fma_rate" not in r
