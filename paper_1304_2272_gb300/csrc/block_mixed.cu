@@ -130,24 +130,29 @@ __device__ __forceinline__ int limb_int(uint32_t bits) {
     return __float2int_rn(__uint_as_float(bits));
 }
 
-// Adds T_i^2 over the rows of one 16-row group, T_i = sum_l C_il 2^(B (S-1-l)) exact in 64
-// bits (|C_il| < 2^24, so |T_i| < 2^60.01) and its square exact in 128 bits (a tile's sum of
-// squares stays below 2^126).
+// Per-power sums of one 16-row group. With T_i = sum_l C_il 2^(B (S-1-l)),
+// T_i^2 = sum_p P_ip 2^(B (2S-2-p)), P_ip = sum_{l+m=p} C_il C_im: the diagonal products
+// C_il^2 go to dg[l] (power 2l), the cross products C_il C_im (l < m) to cr[l+m-1], each a
+// 32 x 32 -> 64-bit multiply-add (|C_il| < 2^24, so every sum over a tile stays below
+// R 2^49 < 2^57).
 template <int S, bool SMALL>
-__device__ __forceinline__ void sumsq_group(const uint32_t (&v)[S][16], int rows, int B,
-                                            unsigned __int128& acc) {
-    const long long base = 1ll << B;
+__device__ __forceinline__ void sumsq_group(const uint32_t (&v)[S][16], int rows, long long (&dg)[S],
+                                            long long (&cr)[2 * S - 3]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         if (i < rows) {
-            long long T = 0;
+            int C[S];
 #pragma unroll
             for (int l = 0; l < S; ++l) {
                 const int col = i * S + l;
-                T = T * base + (long long)limb_int<SMALL>(v[col / 16][col % 16]);
+                C[l] = limb_int<SMALL>(v[col / 16][col % 16]);
             }
-            const unsigned long long uT = (unsigned long long)(T < 0 ? -T : T);
-            acc += (unsigned __int128)uT * uT;
+#pragma unroll
+            for (int l = 0; l < S; ++l) {
+                dg[l] += (long long)C[l] * C[l];
+#pragma unroll
+                for (int m2 = l + 1; m2 < S; ++m2) cr[l + m2 - 1] += (long long)C[l] * C[m2];
+            }
         }
     }
 }
@@ -165,12 +170,17 @@ __device__ __forceinline__ void sumsq_load(uint32_t tb, int R, int g, uint32_t (
 }
 
 // Sum over the R rows of a row tile of T_i^2, the C_il being the S limb sums of row i in
-// TMEM columns i S + l. Up to 3 limbs the next 16-row group's TMEM loads are in flight
-// while a group is summed.
+// TMEM columns i S + l: the per-power sums of all rows, combined once in 128 bits
+// (mod 2^128; the total is below 2^126, so it is exact). Up to 3 limbs the next 16-row
+// group's TMEM loads are in flight while a group is summed.
 template <int S, bool SMALL>
 __device__ __forceinline__ unsigned __int128 tile_sumsq(uint32_t tb, int R, int B) {
     constexpr int G = (256 / S + 15) / 16;  // 16-row groups of the tallest tile
-    unsigned __int128 acc = 0;
+    long long dg[S], cr[2 * S - 3];
+#pragma unroll
+    for (int l = 0; l < S; ++l) dg[l] = 0;
+#pragma unroll
+    for (int p = 0; p < 2 * S - 3; ++p) cr[p] = 0;
     if constexpr (S <= 3) {
         uint32_t v[2][S][16];
         sumsq_load<S>(tb, R, 0, v[0]);
@@ -179,7 +189,7 @@ __device__ __forceinline__ unsigned __int128 tile_sumsq(uint32_t tb, int R, int 
             if (16 * g < R) {
                 tc::tmem_wait_ld();
                 if (16 * (g + 1) < R) sumsq_load<S>(tb, R, g + 1, v[(g + 1) & 1]);
-                sumsq_group<S, SMALL>(v[g & 1], min(16, R - 16 * g), B, acc);
+                sumsq_group<S, SMALL>(v[g & 1], min(16, R - 16 * g), dg, cr);
             }
         }
     } else {
@@ -188,9 +198,16 @@ __device__ __forceinline__ unsigned __int128 tile_sumsq(uint32_t tb, int R, int 
             uint32_t v[S][16];
             sumsq_load<S>(tb, R, g, v);
             tc::tmem_wait_ld();
-            sumsq_group<S, SMALL>(v, min(16, R - 16 * g), B, acc);
+            sumsq_group<S, SMALL>(v, min(16, R - 16 * g), dg, cr);
         }
     }
+    unsigned __int128 acc = 0;
+#pragma unroll
+    for (int l = 0; l < S; ++l)
+        acc += (unsigned __int128)(__int128)dg[l] << (B * (2 * S - 2 - 2 * l));
+#pragma unroll
+    for (int p = 1; p <= 2 * S - 3; ++p)
+        acc += (unsigned __int128)(__int128)cr[p - 1] << (B * (2 * S - 2 - p) + 1);
     return acc;
 }
 
