@@ -222,13 +222,15 @@ def factor_record(stats: dict, n: int, args) -> dict:
 
 def tile_cfg_fields(tile_cfg) -> dict:
     """The tile_cfg bit fields as the library reads them (a negative value = defaults)."""
-    d = {"stages": 0, "group_mb": 40, "single_cta": False, "pair": False, "fuse": False}
+    d = {"stages": 0, "group_mb": 40, "single_cta": False, "pair": False, "fuse": False,
+         "ztail": False}
     if tile_cfg is not None and tile_cfg >= 0:
         d["stages"] = tile_cfg & 0xF
         d["group_mb"] = ((tile_cfg >> 4) & 0xFF) or 40
         d["single_cta"] = bool((tile_cfg >> 12) & 1)
         d["pair"] = bool((tile_cfg >> 13) & 1)
         d["fuse"] = bool((tile_cfg >> 17) & 1) and not bool((tile_cfg >> 14) & 1)
+        d["ztail"] = bool((tile_cfg >> 21) & 1) and not d["fuse"]
     return d
 
 
@@ -245,7 +247,7 @@ def traffic_for(kernel: str, n: int, m_blk: int, tile_cfg=None):
     nbytes = rec.get("bytes")
     if "bytes_by_group_mb" in rec:
         f = tile_cfg_fields(tile_cfg)
-        if any(f[k] != rec[k] for k in ("single_cta", "fuse")):
+        if any(f[k] != rec.get(k, False) for k in ("single_cta", "fuse", "ztail")):
             return None
         nbytes = rec["bytes_by_group_mb"].get(f["group_mb"])
     path = os.path.join(ROOT, "paper_1304_2272_gb300", "csrc", rec["file"])

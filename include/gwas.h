@@ -87,7 +87,10 @@ typedef struct {
                       default takes 9 bits for n < 32768, 8 for n < 65536, 7 for
                       n < 131072, the most for which the FP32 sums of limb products stay
                       exact); bits 18-20 (batches only) = the number of parts, 1..4, a
-                      mixed batch's cohorts are split into (0 = 4; see gwas_batch_init) */
+                      mixed batch's cohorts are split into (0 = 4; see gwas_batch_init);
+                      bit 21 = the linear rows as R_e = q + t more rows at the end of the
+                      last limb tile, which spans every k (no separate linear tile;
+                      taken when R_e is at most half a tile and bit 17 is not set)      */
     int device;    /* CUDA device ordinal                                             */
     int timing;    /* 1 = record CUDA events around each dominant-kernel launch       */
     int use_graph; /* batches: 1 = capture the batched solve in a CUDA graph and

@@ -212,12 +212,12 @@ __device__ __forceinline__ unsigned __int128 tile_sumsq(uint32_t tb, int R, int 
 }
 
 // The linear reductions of one unit: R_e values T_j = sum_l C_lj 2^(B (S-1-l)) whose limb
-// sums sit in TMEM columns col0 + l R_e + j, written as T_j 2^(E_j - shift0) to
-// lin[(e0 + j) ldp + snp]. The loads of JB linear rows (JB S columns) are issued together
-// and waited for once.
+// sums sit in TMEM columns col0 + j cj + l cl (limb-major: cj = 1, cl = R_e; rows side by
+// side: cj = S, cl = 1), written as T_j 2^(E_j - shift0) to lin[(e0 + j) ldp + snp]. The
+// loads of JB linear rows (JB S columns) are issued together and waited for once.
 template <int S>
-__device__ __forceinline__ void linear_rows(const CohortMx& a, int R_e, uint32_t col0, int64_t e0,
-                                            int64_t snp) {
+__device__ __forceinline__ void linear_rows(const CohortMx& a, int R_e, uint32_t col0, int cj,
+                                            int cl, int64_t e0, int64_t snp) {
     using namespace tc;
     constexpr int JB = 8;
     const int B = a.radix;
@@ -231,7 +231,7 @@ __device__ __forceinline__ void linear_rows(const CohortMx& a, int R_e, uint32_t
         for (int l = 0; l < S; ++l)
 #pragma unroll
             for (int j = 0; j < JB; ++j)
-                if (j < nj) tmem_ld1(col0 + (uint32_t)(l * R_e + j0 + j), x[l][j]);
+                if (j < nj) tmem_ld1(col0 + (uint32_t)((j0 + j) * cj + l * cl), x[l][j]);
         tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < JB; ++j) {
@@ -260,15 +260,20 @@ __device__ __forceinline__ void epilogue_unit(const CohortMx& a, int R_e, uint32
     const int shift0 = (B - 1) + B * (S - 1);
     const int R = a.R;
     if (rt != (int)mx::EXTRA) {
-        const unsigned __int128 acc = tile_sumsq<S, SMALL>(tb, R, B);
+        // with the linear rows at the end of the last row tile, its last R_e rows are Z's
+        const bool zrows = a.ztail && rt == a.n_rt - 1;
+        const int R_w = zrows ? R - R_e : R;
+        const unsigned __int128 acc = tile_sumsq<S, SMALL>(tb, R_w, B);
         const double hi = (double)(unsigned long long)(acc >> 64);
         const double lo = (double)(unsigned long long)acc;
         const double val = ldexp(fma(hi, 18446744073709551616.0, lo), 2 * (a.E_w[rt] - shift0));
         if (snp < a.mb) a.sq_part[(int64_t)rt * a.ldp + snp] = val;
+        if (zrows) linear_rows<S>(a, R_e, tb + (uint32_t)(R_w * S), S, 1, 0, snp);
         // fused linear rows: Z limbs of this tile's k-range, one partial per (rt, j)
-        if (!a.extra) linear_rows<S>(a, R_e, tb + (uint32_t)(R * S), (int64_t)rt * R_e, snp);
+        else if (!a.extra && !a.ztail)
+            linear_rows<S>(a, R_e, tb + (uint32_t)(R * S), 1, R_e, (int64_t)rt * R_e, snp);
     } else {
-        linear_rows<S>(a, R_e, tb, 0, snp);
+        linear_rows<S>(a, R_e, tb, 1, R_e, 0, snp);
     }
 }
 
@@ -731,11 +736,14 @@ cudaError_t mixed_layout(MixedDev& m, int64_t n, int S, int R_e, int64_t m_blk) 
     const int r_fused = (mx::NT - S * R_e) / S;
     m.fused = m.cfg_fuse && r_fused >= 16;
     m.R = m.fused ? r_fused : mx::rows_max(S);
+    // or (tile_cfg bit 21) the linear rows are R_e more rows after row n: they take the
+    // last rows of the last row tile, which spans every k already (at most half a tile)
+    m.ztail = !m.fused && m.cfg_ztail && 2 * R_e <= m.R;
     m.NT = mx::NT;
     m.pair = !m.cfg_single_cta;
-    m.n_rt = (int)ceil_div(n, m.R);
+    m.n_rt = (int)ceil_div(n + (m.ztail ? R_e : 0), m.R);
     m.n_pad = round_up(n, 64);
-    m.rows_total = (int64_t)m.n_rt * m.NT + (m.fused ? 0 : m.N_e);
+    m.rows_total = (int64_t)m.n_rt * m.NT + (m.fused || m.ztail ? 0 : m.N_e);
     m.mb_pad_max = round_up(m_blk, 2 * mx::BM);
     m.ldp = round_up(m_blk, 32);
     return cudaSuccess;
@@ -772,7 +780,8 @@ static CohortMx make_cohort(const MixedDev& m, int64_t mb, bool pair, int64_t sn
     c.mb = mb;
     c.ldp = m.ldp;
     c.unit_base = 0;
-    c.extra = m.fused ? 0 : 1;
+    c.extra = (m.fused || m.ztail) ? 0 : 1;
+    c.ztail = m.ztail ? 1 : 0;
     c.radix = m.radix;
     c.small_sums = ((int64_t)m.n << m.radix) < (1ll << 22) ? 1 : 0;
     c.R = m.R;

@@ -129,6 +129,7 @@ void apply_tile_cfg(MixedDev& m, int tile_cfg) {
     m.cfg_single_cta = false;
     m.cfg_pair = false;
     m.cfg_fuse = false;
+    m.cfg_ztail = false;
     m.cfg_radix = 0;
     if (tile_cfg >= 0) {
         m.cfg_stages = tile_cfg & 0xF;
@@ -139,6 +140,8 @@ void apply_tile_cfg(MixedDev& m, int tile_cfg) {
         // bit 17 fuses the linear rows into the limb tiles; bit 14 (a separate linear
         // tile, the default) takes precedence
         m.cfg_fuse = ((tile_cfg >> 17) & 1) != 0 && ((tile_cfg >> 14) & 1) == 0;
+        // bit 21: the linear rows at the end of the last row tile (unless fused)
+        m.cfg_ztail = ((tile_cfg >> 21) & 1) != 0 && !m.cfg_fuse;
         m.cfg_radix = (tile_cfg >> 15) & 3;
     }
 }
@@ -682,7 +685,8 @@ gwas_status gwas_set_tile_cfg(gwas_ctx* c, int tile_cfg) {
     CK(cudaStreamSynchronize(c->s_comp));
     MixedDev& m = c->mx;
     const int old_R = m.R, old_NT = m.NT, old_radix = m.radix;
-    const bool old_pair = m.pair, old_fused = m.fused;
+    const bool old_pair = m.pair, old_fused = m.fused, old_ztail = m.ztail;
+    const int old_nrt = m.n_rt;
     apply_tile_cfg(m, tile_cfg);
     mixed_layout(m, c->n, m.S, m.R_e, c->opts.m_blk);
     if (!mixed_shape_built(m)) {
@@ -691,7 +695,8 @@ gwas_status gwas_set_tile_cfg(gwas_ctx* c, int tile_cfg) {
         return fail(c, GWAS_ERR_UNSUPPORTED, "gwas_set_tile_cfg: no kernel for that layout");
     }
     c->opts.tile_cfg = tile_cfg;
-    const bool relayout = m.R != old_R || m.NT != old_NT || m.fused != old_fused;
+    const bool relayout = m.R != old_R || m.NT != old_NT || m.fused != old_fused ||
+                          m.ztail != old_ztail || m.n_rt != old_nrt;
     const bool was_factored = c->factored;
     if (relayout || (was_factored && (m.pair != old_pair || m.radix != old_radix))) {
         // the limbs are rebuilt: until that succeeds the context holds no usable factor
@@ -734,7 +739,8 @@ gwas_status gwas_autotune(gwas_ctx* c, const int8_t* X, int64_t mb_max, int reps
     if (c->mixed) {
         // a radix cap set by the caller (tile_cfg bits 15-16) is kept
         const int keep = c->opts.tile_cfg >= 0 ? (c->opts.tile_cfg & (3 << 15)) : 0;
-        for (int variant : {1 << 12, 1 << 13, (1 << 17) | (1 << 12), (1 << 17) | (1 << 13)})
+        for (int variant : {1 << 12, 1 << 13, (1 << 17) | (1 << 12), (1 << 17) | (1 << 13),
+                            (1 << 21) | (1 << 12), (1 << 21) | (1 << 13)})
             for (int group : {40, 80, 160})
                 for (int stages : {0, 4}) cfgs.push_back(keep | variant | (group << 4) | stages);
     } else {

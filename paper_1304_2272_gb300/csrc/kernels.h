@@ -116,6 +116,7 @@ struct CohortMx {
     int off;            // n_rt R - n: row tile rt holds rows rt R - off .. (rt + 1) R - off
     int ct_base;        // first 128-SNP tile of the launch (its SNPs start at 128 ct_base)
     int small_sums;     // 1: n 2^B < 2^22, so every limb sum in TMEM is below 2^22
+    int ztail;          // 1: the R_e linear rows are the last rows of the last row tile
     const int* E_w;     // exponent per row tile
     const int* E_e;     // exponent per linear row (fused: per (row tile, linear row))
     double* sq_part;    // [n_rt][ldp]
@@ -131,6 +132,8 @@ struct MixedDev {
     int NT = 256;               // UMMA N of a row tile: its S R limb rows (row i's limbs
                                 // side by side), fused linear rows, zero rows up to 256
     bool fused = false;         // linear rows ride in the spare N of every row tile
+    bool ztail = false;         // linear rows are R_e extra rows at the end of the last row
+                                // tile (over every k, one exponent each); no linear tile
     bool pair = true;           // CTA-pair kernel (cta_group::2) instead of one CTA per tile
     int n_rt = 0;               // R-row tiles of L^{-1}
     int64_t n_pad = 0;          // n rounded up to 64 (k extent of every BF16 row)
@@ -151,10 +154,12 @@ struct MixedDev {
     bool cfg_single_cta = false;  // force one CTA per 128-SNP tile
     bool cfg_pair = false;        // force CTA pairs
     bool cfg_fuse = false;        // fuse the linear rows into the limb tiles (lower R)
+    bool cfg_ztail = false;       // linear rows at the end of the last row tile (bit 21)
     int cfg_radix = 0;            // bits per limb at most 9 - cfg_radix (tile_cfg bits 15-16)
     int lin_tiles() const { return fused ? n_rt : 1; }
-    // rows of padding before row 0: the row tiles end at row n, so the first is the short one
-    int row_off() const { return (int)((int64_t)n_rt * R - n); }
+    // rows of padding before row 0: the row tiles end at row n (at row n + R_e with the
+    // linear rows as the last rows), so the first is the short one
+    int row_off() const { return (int)((int64_t)n_rt * R - n - (ztail ? R_e : 0)); }
     int n_exp() const { return n_rt + (fused ? n_rt * R_e : R_e); }
     CUtensorMap tmX, tmW, tmE;  // TMA maps of Xb, WL (row tiles), WL (linear tile)
     CUtensorMap tmWh, tmEh;     // the same WL maps with half-height boxes (CTA pairs)

@@ -230,18 +230,21 @@ k_split_w(const double* __restrict__ W, int64_t ldw, int64_t n, int R, int off, 
     }
 }
 
-// Z (n x R_e, column-major) -> limb rows base + l*R_e + j of WL.
+// Z (n x R_e, column-major) -> limb rows base + j*sj + l*sl of WL: a separate linear tile
+// (limb-major, sj = 1, sl = R_e) or the last rows of the last row tile (the limbs of a
+// linear row side by side like those of a row of L^{-1}, sj = S, sl = 1).
 template <int S>
 __global__ void __launch_bounds__(256)
-k_split_z(const double* __restrict__ Z, int64_t n, int R_e, int B, const int* __restrict__ E_e,
-          uint16_t* __restrict__ WL, int64_t n_pad, int64_t base_row) {
+k_split_z(const double* __restrict__ Z, int64_t n, int B, const int* __restrict__ E_e,
+          uint16_t* __restrict__ WL, int64_t n_pad, int64_t base_row, int sj, int sl) {
     const int j = blockIdx.y;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         uint16_t limbs[S];
         split_limbs<S>(Z[k + (int64_t)j * n], E_e[j], B, limbs);
 #pragma unroll
-        for (int l = 0; l < S; ++l) WL[(base_row + (int64_t)l * R_e + j) * n_pad + k] = limbs[l];
+        for (int l = 0; l < S; ++l)
+            WL[(base_row + (int64_t)j * sj + (int64_t)l * sl) * n_pad + k] = limbs[l];
     }
 }
 
@@ -303,14 +306,18 @@ cudaError_t launch_limb_split(MixedDev& m, const double* W, int64_t ldw, const d
     k_exponents<<<(unsigned)ceil_div(m.n_exp(), 128), 128, 0, s>>>(m.bits, m.n_exp(), m.E);
     const dim3 gw((unsigned)ceil_div(n, 32), (unsigned)ceil_div((int64_t)m.n_rt * m.R, 32));
     const dim3 gz(64, (unsigned)m.R_e);
-    const int64_t zbase = (int64_t)m.n_rt * m.NT;
+    // a separate linear tile after the row tiles, or the last R_e rows of the last row tile
+    const int64_t zbase = m.ztail ? (int64_t)(m.n_rt - 1) * m.NT + (int64_t)(m.R - m.R_e) * m.S
+                                  : (int64_t)m.n_rt * m.NT;
+    const int zsj = m.ztail ? m.S : 1, zsl = m.ztail ? 1 : m.R_e;
 #define GWAS_SPLIT(SS)                                                                       \
     k_split_w<SS><<<gw, 256, 0, s>>>(W, ldw, n, m.R, off, m.NT, m.radix, m.E, m.WL, m.n_pad); \
     if (m.fused)                                                                             \
         k_split_zf<SS><<<gz, 256, 0, s>>>(Z, n, m.R, off, m.NT, m.R_e, m.radix, m.E + m.n_rt,   \
                                           m.WL, m.n_pad);                                    \
     else                                                                                     \
-        k_split_z<SS><<<gz, 256, 0, s>>>(Z, n, m.R_e, m.radix, m.E + m.n_rt, m.WL, m.n_pad, zbase);
+        k_split_z<SS><<<gz, 256, 0, s>>>(Z, n, m.radix, m.E + m.n_rt, m.WL, m.n_pad, zbase,     \
+                                         zsj, zsl);
     switch (m.S) {
         case 2: GWAS_SPLIT(2) break;
         case 3: GWAS_SPLIT(3) break;

@@ -26,8 +26,10 @@ def test_set_tile_cfg_resplits_and_keeps_parity(gw):
     ref = G.gls(c.phi, c.h, c.sigma2, c.XL, c.Y, X)
     with gw.GLS(c.n, 4, 1, precision=gw.GWAS_PREC_MIXED, n_limbs=3, m_blk=1024) as e:
         e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
-        # pair <-> single, separate <-> fused linear rows (85 <-> 81 rows per tile)
-        for cfg in (1 << 13, 1 << 12, (1 << 12) | (20 << 4) | 3, (1 << 17) | (1 << 13), -1):
+        # pair <-> single, separate <-> fused linear rows (85 <-> 81 rows per tile) <->
+        # linear rows in the last tile (one more row tile)
+        for cfg in (1 << 13, 1 << 12, (1 << 12) | (20 << 4) | 3, (1 << 17) | (1 << 13),
+                    (1 << 21) | (1 << 13), (1 << 21) | (1 << 12), -1):
             gw.gwas_set_tile_cfg(e.ctx, cfg)
             b, w, s = e.solve(X)
             np.testing.assert_array_equal(s, ref[2])

@@ -69,11 +69,13 @@ def run_batch(gw, cohorts, Xs, precision, solves=1, **opts):
 # mixed batches: the CTA-pair kernel (default) or one CTA per 128-SNP tile (tile_cfg bit 12);
 # a separate linear tile (default) or linear rows fused into the limb tiles (bit 17)
 VARIANTS = {"pair": -1, "single": 1 << 12, "pair_fused": 1 << 17,
-            "single_fused": (1 << 17) | (1 << 12)}
+            "single_fused": (1 << 17) | (1 << 12),
+            # the linear rows as the last rows of the last limb tile (bit 21)
+            "pair_ztail": 1 << 21, "single_ztail": (1 << 21) | (1 << 12)}
 
 
 @pytest.mark.parametrize("precision,variant", [("fp64", "pair"), ("mixed", "pair"),
-                                               ("mixed", "single")])
+                                               ("mixed", "single"), ("mixed", "pair_ztail")])
 @pytest.mark.parametrize("use_graph", [1, 0])
 def test_batch_uneven_cohorts_vs_oracle(gw, precision, variant, use_graph):
     seeds_n = [(1, 129), (2, 300), (3, 64), (4, 1003), (5, 517)]
@@ -95,7 +97,9 @@ def test_batch_uneven_cohorts_vs_oracle(gw, precision, variant, use_graph):
 
 @pytest.mark.parametrize("precision,variant,t", [("fp64", "pair", 2), ("mixed", "pair", 2),
                                                  ("mixed", "single", 3), ("mixed", "pair_fused", 2),
-                                                 ("mixed", "single_fused", 3)])
+                                                 ("mixed", "single_fused", 3),
+                                                 ("mixed", "pair_ztail", 2),
+                                                 ("mixed", "single_ztail", 3)])
 def test_batch_matches_single_cohort_bitwise(gw, precision, variant, t):
     seeds_n = [(11, 250), (12, 700), (13, 90)]
     cohorts, Xs = make_batch(seeds_n, t=t, m_of=lambda k: [333, 129, 64][k])

@@ -13,11 +13,13 @@ def test_tile_cfg_fields_match_the_bit_layout():
     assert bench.tile_cfg_fields(None) == bench.tile_cfg_fields(-1)
     d = bench.tile_cfg_fields(8832)           # pair forced, group 40 MB, stages auto
     assert d == {"stages": 0, "group_mb": 40, "single_cta": False, "pair": True,
-                 "fuse": False}
+                 "fuse": False, "ztail": False}
     d = bench.tile_cfg_fields(4 | (160 << 4) | (1 << 12) | (1 << 17))
     assert d["stages"] == 4 and d["group_mb"] == 160 and d["single_cta"] and d["fuse"]
     assert not bench.tile_cfg_fields((1 << 17) | (1 << 14))["fuse"]   # bit 14 wins
     assert bench.tile_cfg_fields(0)["group_mb"] == 40   # group 0 = the default
+    assert bench.tile_cfg_fields((1 << 21) | (1 << 13))["ztail"]
+    assert not bench.tile_cfg_fields((1 << 21) | (1 << 17))["ztail"]   # fused wins
 
 
 def test_traffic_guard_rejects_other_shapes_and_groupings():

@@ -33,7 +33,9 @@ WALD_TOL = {s: wald_tol(s) for s in (2, 3, 4, 5)}
 # tile_cfg bits: 12 forces one CTA per 128-SNP tile, 13 forces CTA pairs (cta_group::2),
 # 17 fuses the linear rows into the limb tiles (a separate linear tile by default)
 VARIANTS = {"default": -1, "single": 1 << 12, "pair": 1 << 13,
-            "single_fused": (1 << 17) | (1 << 12), "pair_fused": (1 << 17) | (1 << 13)}
+            "single_fused": (1 << 17) | (1 << 12), "pair_fused": (1 << 17) | (1 << 13),
+            # the linear rows as the last rows of the last limb tile (bit 21)
+            "single_ztail": (1 << 21) | (1 << 12), "pair_ztail": (1 << 21) | (1 << 13)}
 
 
 def rel_b(b, ref):
@@ -77,14 +79,16 @@ def oracle(c, X):
     return G.gls(c.phi, c.h, c.sigma2, c.XL, c.Y, X)
 
 
-@pytest.mark.parametrize("variant", ["single_fused", "single", "pair", "pair_fused", "default"])
+@pytest.mark.parametrize("variant", ["single_fused", "single", "pair", "pair_fused", "default",
+                                     "pair_ztail", "single_ztail"])
 def test_mixed_small_first(gwas, variant):
     c = synth.make_cohort(3, 128, n_markers=200)
     X = c.snps(130)
     check(run(gwas, c, X, m_blk=256, tile_cfg=VARIANTS[variant]), oracle(c, X), 3)
 
 
-@pytest.mark.parametrize("variant", ["default", "pair", "single", "pair_fused", "single_fused"])
+@pytest.mark.parametrize("variant", ["default", "pair", "single", "pair_fused", "single_fused",
+                                     "pair_ztail", "single_ztail"])
 def test_mixed_small_workload_full(gwas, variant):
     # n = 1000, p = 4, m = 10,000 (the oracle-sized workload), 3 limbs
     c = synth.make_cohort(0, 1000)
@@ -103,18 +107,18 @@ def tol_bits(bits_per_limb, limbs):
 @pytest.mark.parametrize("limbs", [3, 4, 5])
 def test_smaller_limb_radix(gwas, cap, bits, limbs):
     """8- and 7-bit limbs (the radix taken for n >= 32768 and n >= 65536), forced at
-    n = 1000 through tile_cfg bits 15-16; the fused and separate linear layouts."""
+    n = 1000 through tile_cfg bits 15-16; the separate, fused and last-tile linear layouts."""
     c = synth.make_cohort(0, 1000)
     X = c.snps(3000)
     ref = oracle(c, X)
-    for extra in (0, 1 << 17):
+    for extra in (0, 1 << 17, 1 << 21):
         out = run(gwas, c, X, limbs=limbs, m_blk=1024, tile_cfg=(cap << 15) | extra)
         b, w, s = out
         np.testing.assert_array_equal(s, ref[2])
         ok = ref[2] == 0
         eb = rel_b(b[ok], ref[0][ok])
         ew = wald_err(w[ok], ref[1][ok])
-        print(f"[errors] n=1000 mixed x{limbs} of {bits} bits (fused={bool(extra)}): max rel b "
+        print(f"[errors] n=1000 mixed x{limbs} of {bits} bits (layout bits {extra:#x}): max rel b "
               f"err {eb:.2e}, Wald err {ew:.2e}")
         assert eb <= tol_bits(bits, limbs)
         assert ew <= wald_tol(limbs, bits)
@@ -131,21 +135,22 @@ def test_mixed_more_limbs_full(gwas, limbs, variant):
     print(f"n=1000 mixed x{limbs} ({variant}): max rel b err {eb:.2e}, Wald err {ew:.2e}")
 
 
-@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("layout", ["", "_fused", "_ztail"])
 @pytest.mark.parametrize("limbs", [2, 3, 4, 5])
-def test_pair_and_single_cta_bitwise(gwas, limbs, fused):
+def test_pair_and_single_cta_bitwise(gwas, limbs, layout):
     # both variants use the same tile height and N = 256 tile (limb rows, fused linear
     # rows, zero rows), hence the same limbs and the same partial sums
     c = synth.make_cohort(23, 700, n_markers=700)
     X = c.snps(777)
-    v1, v2 = ("pair_fused", "single_fused") if fused else ("pair", "single")
+    v1, v2 = "pair" + layout, "single" + layout
     b1, w1, _ = run(gwas, c, X, limbs=limbs, m_blk=1024, tile_cfg=VARIANTS[v1])
     b2, w2, _ = run(gwas, c, X, limbs=limbs, m_blk=1024, tile_cfg=VARIANTS[v2])
     np.testing.assert_array_equal(b1, b2)
     np.testing.assert_array_equal(w1, w2)
 
 
-@pytest.mark.parametrize("variant", ["pair", "single", "pair_fused", "single_fused"])
+@pytest.mark.parametrize("variant", ["pair", "single", "pair_fused", "single_fused", "pair_ztail",
+                                     "single_ztail"])
 @pytest.mark.parametrize("limbs", [2, 3, 4, 5])
 @pytest.mark.parametrize("n,m,p,t,mblk", [
     (64, 1, 4, 1, 64), (65, 127, 4, 1, 128), (130, 129, 3, 2, 128), (1003, 300, 4, 3, 512),
@@ -252,14 +257,16 @@ def full_size():
     return c, G.factor(c.phi, c.h, c.sigma2)
 
 
-@pytest.mark.parametrize("limbs", [3, 4, 5])
-def test_mixed_full_size_sampled(gwas, full_size, limbs):
-    """n = 10,000, one block of 16,384 SNPs in the benchmark's launch shape."""
+@pytest.mark.parametrize("limbs,cfg", [(3, -1), (4, -1), (5, -1), (3, (1 << 21) | (1 << 13)),
+                                       (5, (1 << 21) | (1 << 13))])
+def test_mixed_full_size_sampled(gwas, full_size, limbs, cfg):
+    """n = 10,000, one block of 16,384 SNPs in the benchmark's launch shape (the default
+    layout, and the linear rows in the last limb tile)."""
     import torch
     n, mb = 10000, 16384
     c, L = full_size
     Xd = synth.genotypes_torch(5, n, mb, "cuda")
-    e = gwas.GLS(n, 4, 1, m_blk=mb, precision=gwas.GWAS_PREC_MIXED, n_limbs=limbs)
+    e = gwas.GLS(n, 4, 1, m_blk=mb, precision=gwas.GWAS_PREC_MIXED, n_limbs=limbs, tile_cfg=cfg)
     e.factor(c.phi, c.h, c.sigma2, c.XL, c.Y)
     bd = torch.empty((mb, 1, 4), dtype=torch.float64, device="cuda")
     wd = torch.empty((mb, 1), dtype=torch.float64, device="cuda")
@@ -273,5 +280,5 @@ def test_mixed_full_size_sampled(gwas, full_size, limbs):
     ref = G.gls_hoisted(L, c.XL, c.Y, Xs)
     out = (bd.cpu().numpy()[idx], wd.cpu().numpy()[idx], sd.cpu().numpy()[idx])
     eb, ew = check(out, ref, limbs)
-    print(f"n=10000 mixed x{limbs}: max rel b err {eb:.2e}, Wald err {ew:.2e}")
+    print(f"n=10000 mixed x{limbs} (tile_cfg {cfg}): max rel b err {eb:.2e}, Wald err {ew:.2e}")
     e.close()
