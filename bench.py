@@ -190,16 +190,22 @@ TRAFFIC = {
          "bytes": 9495486464 + 60372992}],
     # a mixed block of 16,384 SNPs is two launches of 8,192 (the two halves): bytes per block
     "k_block_mixed<3>": [
-        {"file": "block_mixed.cu", "sha": "dd0df3ef5be84c55", "n": 10000, "m_blk": 16384,
-         "single_cta": False, "fuse": False,
-         "bytes_by_group_mb": {40: 1864541440 + 1865809664 + 10432000 + 7203584,
-                               80: 1991927808 + 1994817280 + 9809920 + 7133696,
-                               160: 3778045184 + 3756617728 + 9096192 + 6043392}},
-        {"file": "block_mixed.cu", "sha": "dd0df3ef5be84c55", "n": 30000, "m_blk": 16384,
-         "single_cta": False, "fuse": False,
-         "bytes_by_group_mb": {40: 55779521024 + 54989144320 + 26972672 + 24396544,
-                               80: 52567564288 + 52031463424 + 27138048 + 23599104,
-                               160: 45582212608 + 49648010752 + 27142912 + 23671808}}],
+        {"file": "block_mixed.cu", "sha": "a98e3058f324fc0e", "n": 10000, "m_blk": 16384,
+         "single_cta": False, "fuse": False, "ztail": False,
+         "bytes_by_group_mb": {40: 1891798016 + 1898073600 + 10515200 + 7256832,
+                               160: 3660850688 + 3656167680 + 9178880 + 6081792}},
+        {"file": "block_mixed.cu", "sha": "a98e3058f324fc0e", "n": 10000, "m_blk": 16384,
+         "single_cta": False, "fuse": False, "ztail": True,
+         "bytes_by_group_mb": {40: 1937885696 + 1941512960 + 10448128 + 7621120,
+                               160: 3591771904 + 3586308352 + 8904704 + 6366720}},
+        {"file": "block_mixed.cu", "sha": "a98e3058f324fc0e", "n": 30000, "m_blk": 16384,
+         "single_cta": False, "fuse": False, "ztail": False,
+         "bytes_by_group_mb": {40: 63709729792 + 64894514944 + 27092480 + 23768576,
+                               160: 44848629760 + 45610755584 + 27181824 + 23899136}},
+        {"file": "block_mixed.cu", "sha": "a98e3058f324fc0e", "n": 30000, "m_blk": 16384,
+         "single_cta": False, "fuse": False, "ztail": True,
+         "bytes_by_group_mb": {40: 60897200384 + 66171474432 + 27252992 + 24198912,
+                               160: 45278907136 + 47682639360 + 27141120 + 23846144}}],
 }
 
 
@@ -241,14 +247,15 @@ MIXED_TOL = {2: 1e-4, 3: 1e-6, 4: 1e-9, 5: 1e-10}
 
 def traffic_for(kernel: str, n: int, m_blk: int, tile_cfg=None):
     recs = [r for r in TRAFFIC.get(kernel, []) if r["n"] == n and r["m_blk"] == m_blk]
+    f = tile_cfg_fields(tile_cfg)
+    # a record per tile layout: the one whose layout flags match tile_cfg's
+    recs = [r for r in recs if "bytes_by_group_mb" not in r or
+            all(f[k] == r.get(k, False) for k in ("single_cta", "fuse", "ztail"))]
     if not recs:
         return None
     rec = recs[0]
     nbytes = rec.get("bytes")
     if "bytes_by_group_mb" in rec:
-        f = tile_cfg_fields(tile_cfg)
-        if any(f[k] != rec.get(k, False) for k in ("single_cta", "fuse", "ztail")):
-            return None
         nbytes = rec["bytes_by_group_mb"].get(f["group_mb"])
     path = os.path.join(ROOT, "paper_1304_2272_gb300", "csrc", rec["file"])
     try:
