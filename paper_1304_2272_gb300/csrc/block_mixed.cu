@@ -7,16 +7,18 @@
 // and every A_l is exact in BF16. A_l x_i then has integer products <= 2^B whose sums
 // stay below 2^24 while n < 2^(24-B), so the FP32 tensor-core accumulation of each limb
 // is exact: B = 9 for n < 32768, 8 for n < 65536, 7 for n < 131072. The epilogue
-// recombines the limbs in 64-bit integers,
+// needs, with the limb sums C_l of a row,
 //     T = sum_l C_l * 2^(B (S-1-l)),   xbar = 2^(E-(B-1)-B(S-1)) * T,
-// and accumulates T^2 exactly in 128-bit integers for S_BRi = Xbar_Ri^T Xbar_Ri. The
-// only rounding left is the limb truncation of W (relative 2^(-BS) of the tile maximum)
-// and one conversion to FP64 per (row tile, SNP).
+// the sum of T^2 over a row tile for S_BRi = Xbar_Ri^T Xbar_Ri: it sums the 32 x 32-bit
+// products C_l C_m per power of 2^B in 64-bit integers and combines them once in 128 bits,
+// exactly. The only rounding left is the limb truncation of W (relative 2^(-BS) of the
+// tile maximum) and one conversion to FP64 per (row tile, SNP).
 //
 // The linear reductions of Algorithm 1, S_BLi = Xbar_Ri^T Xbar_L and bbar_Bi =
 // Xbar_Ri^T ybar, are the same numbers as Z^T x_i with Z = L^{-T} [Xbar_L | Ybar]
-// (= M^{-1} [X_L | Y]); Z is split into limbs the same way and appended as extra UMMA
-// rows, so the tensor cores produce them too.
+// (= M^{-1} [X_L | Y]); Z is split into limbs the same way and rides on the tensor cores
+// too: in a separate linear tile per SNP tile, fused into every row tile on its own
+// k-range, or as the last rows of the last row tile.
 //
 // Kernel structure (one persistent CTA per SM, 8 warps):
 //   warp 0 lane 0: TMA producer (dosage tile 128 SNPs x 64 k, limb tile N x 64 k),
@@ -47,7 +49,8 @@ constexpr int SMEM_BUDGET = 200 * 1024;
 // takes about the same time for any N <= 256, so a tile holds as many rows of L^{-1} as
 // S limbs allow, R = floor(256 / S) (85 for 3 limbs), the S limbs of each row side by
 // side (column i S + l), zero rows up to 256. With the linear rows fused into the tile,
-// R = floor((256 - S R_e) / S).
+// R = floor((256 - S R_e) / S); with them as the last rows of the last tile, the tiles
+// end at row n + R_e.
 constexpr int NT = 256;
 __host__ __device__ constexpr int rows_max(int S) { return NT / S; }
 }  // namespace mx
