@@ -86,8 +86,8 @@ typedef struct {
                       bit 17); bits 15-16 = r caps the bits per limb at 9 - r (the
                       default takes 9 bits for n < 32768, 8 for n < 65536, 7 for
                       n < 131072, the most for which the FP32 sums of limb products stay
-                      exact); bits 18-20 (batches only) = the number of parts, 1..4, a
-                      mixed batch's cohorts are split into (0 = 4; see gwas_batch_init);
+                      exact); bits 18-20 (batches only) = the number of parts, 1..7, a
+                      mixed batch's cohorts are split into (0 = 6; see gwas_batch_init);
                       bit 21 = the linear rows as R_e = q + t more rows at the end of the
                       last limb tile, which spans every k (no separate linear tile;
                       taken when R_e is at most half a tile and bit 17 is not set)      */
@@ -340,7 +340,7 @@ gwas_status gwas_autotune(gwas_ctx* ctx, const int8_t* X, int64_t mb_max, int re
  * largest number of SNPs per cohort in one batched solve. Every cohort takes
  * opts->tile_cfg: GWAS_PREC_MIXED batches run the CTA-pair kernel variant unless bit 12
  * forces one CTA per 128-SNP tile. A mixed batch of several cohorts is solved in parts
- * (contiguous cohort ranges of about equal work, tile_cfg bits 18-20, default 4) on two
+ * (contiguous cohort ranges of about equal work, tile_cfg bits 18-20, default 6) on two
  * streams, each part's dosage conversion beside the previous part's block kernel.
  * Errors as gwas_init. */
 gwas_status gwas_batch_init(int n_cohorts, const int64_t* n, int p, int t, const gwas_opts* opts,

@@ -22,7 +22,7 @@ struct gwas_batch {
     // p x p solves overlap part k's block kernel, and part k's CTAs fill the tail of part
     // k-1's persistent grid.
     cudaStream_t s2 = nullptr;
-    static constexpr int kMaxParts = 4;
+    static constexpr int kMaxParts = 7;
     int n_parts = 1;
     int part_c0[kMaxParts + 1] = {};          // cohorts of part k: [part_c0[k], part_c0[k+1])
     int64_t part_snps[kMaxParts] = {}, part_units[kMaxParts] = {};
@@ -236,10 +236,12 @@ gwas_status gwas_batch_solve_device(gwas_batch* b, const int8_t* const* X, const
             std::vector<int64_t> w(nc);
             int64_t total = 0;
             for (int c = 0; c < nc; ++c) total += (w[c] = mixed_cohort_work(b->ctx[c]->mx, mb[c]));
-            // tile_cfg bits 18-20: the number of parts (0 = four: measured on 48 cohorts of
-            // n ~ U[1000, 8000], 4 parts ran 1475 BF16 TFLOP/s, 3 parts 1413, 2 parts 1358)
+            // tile_cfg bits 18-20: the number of parts (0 = six: measured on 48 cohorts of
+            // n ~ U[1000, 8000] at power-capped clocks, BF16 TFLOP/s per MHz 0.72 with 2
+            // parts, 0.70-0.76 with 3-4 (earlier epilogue), 0.80-0.85 with 4, 0.87 with 6,
+            // 0.84 with 7)
             const int want = b->opts.tile_cfg >= 0 ? (b->opts.tile_cfg >> 18) & 7 : 0;
-            P = std::min(nc, std::min(gwas_batch::kMaxParts, want > 0 ? want : 4));
+            P = std::min(nc, std::min(gwas_batch::kMaxParts, want > 0 ? want : 6));
             int64_t acc = 0;
             int k = 1;
             for (int c = 0; c < nc && k < P; ++c) {
